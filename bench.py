@@ -1,0 +1,400 @@
+#!/usr/bin/env python
+"""Benchmark of the truncated-Newton EOT solver on one GB300.
+
+Workload (a synthetic stand-in for the paper's upsampled-MNIST problems, Sec. 4.1,
+Table 1): a 64 x 64 grid, n = m = 4096, two Gaussian-mixture histograms with 10%
+of the bins zeroed, squared-Euclidean grid cost with max 1 stored as FP32 in HBM
+(64 MiB), gamma annealed from 2^4 to 2^14 (Alg. 1 with adaptive q), mixed
+precision, solved until the marginal L1 error of the output is <= 1e-6.
+
+One step = one full eot_solve (every row of the hot path: exponent formation,
+exp, row and column sweeps, HVP assembly, PCG, Jacobi diagonal, the NewtonSolve
+outer test and the LSE sweeps). value = mean time per solve (time-to-1e-6).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With --impl reference the FP64 numpy oracle is timed on the host cores instead
+(see cpu_sample below); it never touches the GPU.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "time-to-1e-6 marginal L1 error, mixed vs plain FP32 on 1 GB300; P-entries/s"
+GAMMA_I, GAMMA_F, TOL = 16.0, 16384.0, 1e-6
+N = 4096
+WORKLOAD = "grid64x64_sqeuclid_f32_n4096_gamma2^14"
+L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
+
+
+def env_rank():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle as it stands, timed on a bounded sample
+# ---------------------------------------------------------------------------
+
+def cpu_sample(seconds=12.0):
+    """Times the oracle's two primitive costs on the full-size workload with one
+    thread: one O(n^2) log-sum-exp sweep (plan formation + reduction, as in every
+    oracle LSE update) and one CG step on a stored plan (two matrix-vector products,
+    as in the oracle's NewtonSolve). Returns seconds per op."""
+    import numpy as np
+
+    import workloads as W
+    from oracle import eot_oracle as O
+
+    p = W.grid_problem_4096(0, "sqeuclid")
+    C = p["C"].astype(np.float64)
+    g = GAMMA_F
+    u = np.log(p["r"] + 1e-9)
+    v = np.log(p["c"] + 1e-9) - O.lse_c(u[:, None] - g * C)
+    t0 = time.perf_counter()
+    k_lse = 0
+    while time.perf_counter() - t0 < seconds / 2 or k_lse < 2:
+        O.log_row_sum(u, v, g, C)
+        k_lse += 1
+    t_lse = (time.perf_counter() - t0) / k_lse
+    P = O.plan(u, v, g, C)
+    x = np.random.default_rng(0).normal(size=N)
+    t1 = time.perf_counter()
+    k_cg = 0
+    while time.perf_counter() - t1 < seconds / 2 or k_cg < 2:
+        O.F_r_apply(P, 0.9, x)
+        k_cg += 1
+    t_cg = (time.perf_counter() - t1) / k_cg
+    return {"t_lse": t_lse, "t_cg": t_cg, "k_lse": k_lse, "k_cg": k_cg}
+
+
+def run_cpu_sample_subprocess(seconds=12.0):
+    """Runs cpu_sample in a child process pinned to one BLAS/OpenMP thread."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import json, sys; sys.path.insert(0, %r); import bench; "
+            "print(json.dumps(bench.cpu_sample(%r)))" % (ROOT, seconds))
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                         timeout=600)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def oracle_solve_seconds(sample, ops):
+    """Oracle time for a solve with the given op counts: every sweep outside CG is
+    a plan formation + reduction in the oracle; every CG iteration is two
+    matrix-vector products on the stored plan."""
+    other = ops["sweeps_total"] - ops["sweeps_cg"]
+    return other * sample["t_lse"] + ops["cg_iters"] * sample["t_cg"]
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+def traffic_record():
+    """DRAM bytes per launch of the CG sweeps from the committed ncu summary, valid
+    only while the sweep source is unchanged (hash recorded with the numbers)."""
+    path = os.path.join(ROOT, "profiles", "cg_sweeps_grid4096_traffic.json")
+    try:
+        rec = json.load(open(path))
+    except Exception:
+        return None
+    h = hashlib.sha256(open(os.path.join(ROOT, "paper_2504_02067_gb300", "csrc", "sweep.cuh"),
+                            "rb").read()).hexdigest()[:16]
+    return rec if rec.get("sweep_cuh_sha256_16") == h else None
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = env_rank()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_2504_02067_gb300 as E
+    import workloads as W
+
+    E.build()
+    dev = torch.device("cuda", local)
+    p = W.grid_problem_4096(rank, args.cost)
+    C_h = torch.from_numpy(p["C"]).pin_memory()
+    r_h = torch.from_numpy(p["r"]).pin_memory()
+    c_h = torch.from_numpy(p["c"]).pin_memory()
+    C, r, c = C_h.to(dev), r_h.to(dev), c_h.to(dev)
+    h = E.Handle(local, N, N)
+    prm = E.default_params(gamma_i=GAMMA_I, gamma_f=GAMMA_F, tol_final=TOL)
+    prob = E.Problem(C, r, c, precision="mixed")
+    u = torch.empty(N, dtype=torch.float64, device=dev)
+    v = torch.empty(N, dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        h.eot_solve(prob, prm, u, v)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- device-resident timed region ----
+    sampler = ClockSampler(local)
+    barrier()
+    launches0 = h.launches()
+    sampler.start()
+    times, stats = [], []
+    for _ in range(args.steps):
+        flush.zero_()  # evict the 64 MiB cost from L2 between steps (not timed)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = h.eot_solve(prob, prm, u, v)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+        stats.append(st.as_dict())
+    barrier()
+    clocks = sampler.stop()
+    launches = h.launches() - launches0
+    total = sum(times)
+    if world > 1:
+        t = torch.tensor([total], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total = t.item()
+    sec = total / args.steps
+    last = stats[-1]
+    sweeps = last["sweeps_total"]
+    p_entries_per_s = sweeps * N * N / (sum(times) / args.steps)
+
+    # ---- end to end through the public API, host buffers ----
+    u_h = torch.empty(N, dtype=torch.float64).pin_memory()
+    v_h = torch.empty(N, dtype=torch.float64).pin_memory()
+    barrier()
+    e_times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        C.copy_(C_h, non_blocking=True)
+        r.copy_(r_h, non_blocking=True)
+        c.copy_(c_h, non_blocking=True)
+        h.eot_solve(prob, prm, u, v)
+        u_h.copy_(u, non_blocking=True)
+        v_h.copy_(v, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e_times.append(e0.elapsed_time(e1) / 1e3)
+    e2e = sum(e_times) / len(e_times)
+    if world > 1:
+        t = torch.tensor([e2e], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e = t.item()
+
+    # ---- roofline of the dominant kernels (CG column / row halves) ----
+    bytes_per_launch = N * N * 4  # the FP32 cost streamed once per sweep (vectors are O(n))
+    kern = {}
+    for kind, name in ((0, "cg_col_sweep"), (1, "cg_row_sweep")):
+        flushed = []
+        for _ in range(10):
+            flush.zero_()
+            flushed.append(h.eot_sweep_bench(prob, u, v, GAMMA_F, kind, 1))
+        warm = h.eot_sweep_bench(prob, u, v, GAMMA_F, kind, 50)
+        kern[name] = {"ms_hbm": statistics.median(flushed), "ms_l2warm": warm}
+    dom = max(kern, key=lambda k: kern[k]["ms_l2warm"])
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    ach = bytes_per_launch / (kern[dom]["ms_hbm"] * 1e-3) / 1e9
+    tr = traffic_record()
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(ach, 1), "peak": peak,
+                "unit": "GB/s", "frac": round(ach / peak, 4),
+                "traffic": tr["dram_bytes_per_launch"].get(dom) if tr else None,
+                "peak_source": "measured" if peaks else "fallback",
+                "algorithmic_bytes_per_launch": bytes_per_launch,
+                "achieved_l2warm": round(bytes_per_launch / (kern[dom]["ms_l2warm"] * 1e-3) / 1e9, 1),
+                "sweeps_us": {k: {kk: round(vv * 1e3, 2) for kk, vv in d.items()} for k, d in kern.items()}}
+
+    # ---- plain FP32 comparator (same workload, same tolerance) ----
+    plain = None
+    if not args.no_plain:
+        prob_p = E.Problem(C, r, c, precision="plain_fp32")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        try:
+            stp = h.eot_solve(prob_p, prm, u, v).as_dict()
+            torch.cuda.synchronize()
+            plain = {"seconds": time.perf_counter() - t0, "marg_err_l1": stp["marg_err_l1"],
+                     "reached": stp["marg_err_l1"] <= TOL}
+        except E.EotError as ex:
+            torch.cuda.synchronize()
+            plain = {"seconds": time.perf_counter() - t0, "reached": False, "error": str(ex)[:160]}
+
+    result = None
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline and world == 1:
+            s = run_cpu_sample_subprocess(args.cpu_seconds)
+            est = oracle_solve_seconds(s, last)
+            cpu = {"value": round(est, 3), "unit": "s", "cores": 1, "kind": "oracle",
+                   "sample": ("oracle log_row_sum x%d (%.3f s each) and F_r_apply x%d (%.4f s "
+                              "each) at n = 4096, one thread; solve time = %d non-CG sweeps x "
+                              "LSE + %d CG iterations x CG step, counts from this solve"
+                              % (s["k_lse"], s["t_lse"], s["k_cg"], s["t_cg"],
+                                 last["sweeps_total"] - last["sweeps_cg"], last["cg_iters"]))}
+        result = {
+            "metric": METRIC, "value": round(sec, 5), "unit": "s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(sec * 1e3, 3),
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 exp/sums on f64 potentials (mixed)", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": N, "m": N, "gamma_i": GAMMA_I,
+                       "gamma_f": GAMMA_F, "tol": TOL, "cost": args.cost,
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "flushed between steps (512 MiB write)"},
+            "marg_err_l1": last["marg_err_l1"], "reached_tol": last["marg_err_l1"] <= TOL,
+            "p_entries_per_s": round(p_entries_per_s, 1), "sweeps_per_solve": sweeps,
+            "solve_stats": {k: last[k] for k in ("stages", "newton_steps", "cg_iters", "cg_solves",
+                                                 "ls_trials", "sinkhorn_iters", "curvature_stops",
+                                                 "sweeps_cg", "sweeps_total", "final_rho")},
+            "e2e": {"value": round(e2e, 5), "unit": "s",
+                    "h2d_bytes_per_step": int(C_h.numel() * 4 + r_h.numel() * 8 + c_h.numel() * 8),
+                    "d2h_bytes_per_step": int(2 * N * 8)},
+            "gpu_launches": int(launches), "roofline": roofline, "cpu_baseline": cpu,
+            "plain_fp32": plain, "clocks": clocks,
+        }
+        print(json.dumps(result), flush=True)
+    h.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return result
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the oracle on the host cores
+# ---------------------------------------------------------------------------
+
+REFERENCE_OPS = None  # filled from profiles/oracle_ops_grid4096.json when present
+
+
+def run_reference(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return None
+    try:
+        ops = json.load(open(os.path.join(ROOT, "profiles", "oracle_ops_grid4096.json")))
+    except Exception:
+        print(json.dumps({"impl": "reference", "unavailable": "oracle op counts of the workload "
+                          "are not recorded (profiles/oracle_ops_grid4096.json missing)"}))
+        return None
+    per = max(2.0, args.cpu_seconds / 2)
+    vals = []
+    for k in range(args.warmup + args.steps):
+        s = run_cpu_sample_subprocess(per)
+        if k >= args.warmup:
+            vals.append(oracle_solve_seconds(s, ops))
+    v = statistics.mean(vals)
+    out = {"impl": "reference", "metric": METRIC, "value": round(v, 3), "unit": "s",
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": round(v * 1e3, 1), "higher_is_better": False, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "n": N, "m": N, "gamma_i": GAMMA_I,
+                      "gamma_f": GAMMA_F, "tol": TOL, "cost": args.cost},
+           "cpu_baseline": {"value": round(v, 3), "unit": "s", "cores": 1, "kind": "oracle",
+                            "sample": "per step: oracle LSE sweep and CG step timed for %.0f s at "
+                                      "n = 4096, scaled by the oracle's own op counts of this "
+                                      "workload (%s)" % (per, ops.get("source", ""))},
+           "e2e": {"value": round(v, 3), "unit": "s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cost", default="sqeuclid", choices=["sqeuclid", "l1"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,193 @@
+/*
+ * eot.h — C ABI of the GB300 library for entropic-regularised optimal transport
+ * solved by the truncated Newton method of Kemertas, Farahmand and Jepson,
+ * "A Truncated Newton Method for Optimal Transport" (ICLR 2025, arXiv 2504.02067).
+ *
+ * Problem (Sec. 2.1, Eq. sinkhorn-primal): given marginals r in the (n-1)-simplex,
+ * c in the (m-1)-simplex and a cost C with entries in [0, 1], find
+ *     P* = argmin_{P in U(r, c)} <P, C> - H(P) / gamma,
+ * whose form is P(u, v; gamma) = exp(u 1^T + 1 v^T - gamma C) (Eq.
+ * lagrangian-closed-form). gamma is the INVERSE temperature; the potentials u, v
+ * are log-domain (u, not u / gamma). The plan is never stored: every O(n m)
+ * operation re-forms it tile by tile inside a CUDA kernel.
+ *
+ * Conventions for every call below:
+ *  - Pointers marked "device" must be device memory of the handle's GPU;
+ *    pointers marked "host" are host memory. The caller owns every buffer it
+ *    passes; the library never frees or keeps them after the call returns.
+ *  - Dense costs are row-major with leading dimension ldc (elements); n x ldc
+ *    elements must be readable. 16-byte alignment of C with ldc and m multiples
+ *    of 16 bytes / element size enables the vectorised path; otherwise a scalar
+ *    path is used.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Calls are stream-ordered. Calls with host outputs synchronise the stream.
+ *  - Return value: EOT_OK or an error code; the handle keeps a message that
+ *    eot_last_error() returns. No call aborts the process. After
+ *    EOT_ERR_CUDA the handle should be destroyed.
+ *  - Results are bit-reproducible for a fixed handle, problem and stream (all
+ *    reductions have a fixed order; no floating-point atomics).
+ */
+#ifndef EOT_H_
+#define EOT_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  EOT_OK = 0,
+  EOT_ERR_INVALID_ARG = 1,    /* bad pointer, size, kind, precision or parameter */
+  EOT_ERR_NONFINITE = 2,      /* NaN/Inf met in potentials, marginals or CG scalars */
+  EOT_ERR_CG_MAXITER = 3,     /* a linear CG solve hit max_cg iterations (Alg. 2) */
+  EOT_ERR_LINESEARCH = 4,     /* backtracking hit max_ls halvings (Alg. 4 lines 8-13) */
+  EOT_ERR_MAXSTAGES = 5,      /* Alg. 1 did not reach gamma_f within max_stages */
+  EOT_ERR_MAXNEWTON = 6,      /* Alg. 4 did not reach its tolerance within max_newton */
+  EOT_ERR_RANGE = 7,          /* |potential| >= 2^19: outside the mixed-precision split */
+  EOT_ERR_CUDA = 8,           /* a CUDA runtime call failed */
+  EOT_ERR_UNSUPPORTED = 9     /* combination of cost kind and precision not built */
+} eot_status;
+
+typedef enum {
+  EOT_COST_DENSE_F32 = 0,       /* C: float, n x m */
+  EOT_COST_DENSE_F64 = 1,       /* C: double, n x m */
+  EOT_COST_SQEUCLID_POINTS = 2  /* C_ij = s_C |x_i - y_j|^2 formed on the fly from X, Y */
+} eot_cost_kind;
+
+typedef enum {
+  EOT_PREC_FP64 = 0,       /* every operation in FP64 (the paper's setting, Sec. 4) */
+  EOT_PREC_MIXED = 1,      /* FP32 exp and sums on a double-float exponent; FP64
+                              potentials, shifts, CG scalars and combines */
+  EOT_PREC_PLAIN_FP32 = 2  /* potentials rounded to FP32 before the exponent; FP32
+                              exponent and exp, no shift or split */
+} eot_precision;
+
+typedef struct {
+  int32_t kind;        /* eot_cost_kind */
+  int32_t precision;   /* eot_precision: how P is formed. DENSE_F64 needs FP64;
+                          DENSE_F32 and points take MIXED or PLAIN_FP32. */
+  int64_t n, m;        /* rows (len r) and columns (len c); n, m >= 1 */
+  int64_t d;           /* point dimension (points only), 1 <= d <= 64 */
+  int64_t ldc;         /* leading dimension of C in elements (dense only), >= m */
+  const void* C;       /* device: dense cost (float or double per kind) */
+  const float* X;      /* device: n x d row-major points (points only) */
+  const float* Y;      /* device: m x d row-major points (points only) */
+  double cost_scale;   /* points: s_C; <= 0 asks the library for 1 / max_ij |x_i - y_j|^2 */
+  const double* r;     /* device: n target row marginal (solve / newton / backward) */
+  const double* c;     /* device: m target column marginal */
+} eot_problem;
+
+typedef struct {
+  double gamma_i;      /* initial gamma (Alg. 1 line 1); default 2^4 (Table 3 caption) */
+  double gamma_f;      /* final gamma; default 2^12 */
+  double p;            /* eps_d = min(H(r), H(c)) / gamma^p (Alg. 1 line 4); default 1.5 */
+  double q1;           /* initial decay factor q^(1) (Sec. 3.3); default 2 */
+  double w_r;          /* row smoothing weight, w_c = 1/2 - w_r (Sec. 3.4); default 0.45 */
+  double tol_final;    /* target marginal L1 error at gamma_f; the last stage uses
+                          eps_d = min(eps_d, 2 tol_final / 3); default 1e-6 */
+  int32_t max_stages;  /* default 200 */
+  int32_t max_newton;  /* Newton steps per stage; default 200 */
+  int32_t max_cg;      /* CG iterations per linear solve; default min(4n, 2000) when 0 */
+  int32_t max_ls;      /* Armijo halvings per step; default 30 */
+} eot_params;
+
+typedef struct {       /* host-side counters of one eot_solve call */
+  int64_t sweeps_cg;        /* O(nm) sweeps inside linear CG (2 per CG iteration) */
+  int64_t sweeps_newton;    /* other NewtonSolve sweeps (setup, d_v) */
+  int64_t sweeps_linesearch;
+  int64_t sweeps_sinkhorn;  /* LSE sweeps of ChiSinkhorn and the column/row fixes */
+  int64_t sweeps_total;
+  int32_t stages, newton_steps, cg_iters, cg_solves, ls_trials, sinkhorn_iters;
+  int32_t curvature_stops;  /* CG solves stopped because <p, F_r p> <= 0 in finite precision */
+  int32_t reserved;
+  double final_gamma;
+  double final_rho;
+  double grad_l1;           /* ||r~ - r(P)||_1 at the end of the last projection */
+  double marg_err_l1;       /* ||r(P) - r||_1 + ||c(P) - c||_1 of the output (unsmoothed r, c) */
+  double seconds;           /* wall time of the call */
+} eot_stats;
+
+typedef struct eot_handle_s* eot_handle;
+
+/* Create a handle on `device` with workspace for problems up to max_n x max_m
+ * (grown on demand by later calls). Allocates device memory; not stream-ordered. */
+eot_status eot_create(eot_handle* out, int device, int64_t max_n, int64_t max_m);
+/* Free the handle and its workspace. Synchronises the handle's device. */
+eot_status eot_destroy(eot_handle h);
+/* Message of the last error on this handle (never NULL; valid until the next call). */
+const char* eot_last_error(eot_handle h);
+const char* eot_status_string(eot_status s);
+/* Defaults of eot_params listed above. */
+eot_params eot_params_default(void);
+
+/* Marginals of P(u, v; gamma) (Sec. 2, r(P) = P 1, c(P) = P^T 1), by one row and one
+ * column log-sum-exp sweep (stable for any finite u, v).
+ * u: device [n], v: device [m] (FP64). Outputs (device FP64, each nullable):
+ * r_out [n], c_out [m], log_r_out [n], log_c_out [m], total_out [1] = sum_ij P_ij.
+ * Errors: INVALID_ARG, NONFINITE, RANGE, CUDA. */
+eot_status eot_marginals(eot_handle h, const eot_problem* prob, const double* u, const double* v,
+                         double gamma, double* r_out, double* c_out, double* log_r_out,
+                         double* log_c_out, double* total_out, void* stream);
+
+/* Hessian-vector product of the dual g (Eq. hessian; with s = sqrt(rho) the
+ * discounted Hessian of Eq. discounted-hessian):
+ *   out_u = r(P) * du + s P dv,   out_v = s P^T du + c(P) * dv.
+ * One row LSE sweep (row shifts) and one fused two-sided sweep.
+ * u, du, out_u: device [n]; v, dv, out_v: device [m]; r_out, c_out nullable. */
+eot_status eot_hvp(eot_handle h, const eot_problem* prob, const double* u, const double* v,
+                   double gamma, double s, const double* du, const double* dv, double* out_u,
+                   double* out_v, double* r_out, double* c_out, void* stream);
+
+/* NewtonSolve (Alg. 2) at (u, v): anneal rho from rho0, solving F_r(rho) d_u =
+ * -grad_u g with Jacobi-preconditioned CG from 0 to ||res||_1 <= (eta/4)||grad g||_1,
+ * until ||F_r(1) d_u + grad_u g||_1 <= eta ||grad g||_1; then d_v = -P_c d_u (Eq.
+ * bellman2 with Alg. 4 line 7). grad_u g = r(P) - r_target, ||grad g||_1 =
+ * ||grad_u g||_1 (assumes c(P) = c, as Alg. 4 maintains).
+ * r_target: device [n]. du_out: device [n]; dv_out: device [m] (nullable).
+ * rho_out, cg_iters_out: host, nullable (rho of the last CG solve, Appx. B).
+ * Errors: INVALID_ARG, NONFINITE, CG_MAXITER, RANGE, CUDA. Synchronises. */
+eot_status eot_newton_solve(eot_handle h, const eot_problem* prob, const double* u,
+                            const double* v, double gamma, const double* r_target, double eta,
+                            double rho0, int32_t max_cg, double* du_out, double* dv_out,
+                            double* rho_out, int32_t* cg_iters_out, void* stream);
+
+/* Full solve: MDOT (Alg. 1) with adaptive q and asymmetric smoothing, each
+ * stage projected by TruncatedNewtonProject (Alg. 4 with Alg. 2 and Alg. 3).
+ * u: device [n], v: device [m]: outputs (the last projected potentials at gamma_f).
+ * stats: host, nullable. Errors: any. Synchronises. */
+eot_status eot_solve(eot_handle h, const eot_problem* prob, const eot_params* params, double* u,
+                     double* v, eot_stats* stats, void* stream);
+
+/* Gradients of the EOT value F* = <P*, C> - H(P*) / gamma at the potentials (u, v)
+ * (envelope theorem on the Lagrangian, Appx. A; not stated in the paper):
+ *   dC = grad_scale * P                          (dense; device n x m FP32, ld m)
+ *   dX_i = grad_scale * 2 s_C sum_j P_ij (x_i - y_j)  (points; device n x d FP32)
+ *   dY_j = grad_scale * 2 s_C sum_i P_ij (y_j - x_i)  (points; device m x d FP32)
+ *   dr = grad_scale * u / gamma, dc = grad_scale * v / gamma (device FP64)
+ * Each output nullable. s_C is the problem's cost scale, held constant. */
+eot_status eot_backward(eot_handle h, const eot_problem* prob, const double* u, const double* v,
+                        double gamma, double grad_scale, float* dC, float* dX, float* dY,
+                        double* dr, double* dc, void* stream);
+
+/* Measurement aid: times `iters` back-to-back launches of one sweep kernel at (u, v)
+ * with CUDA events recorded on `stream` (after an untimed set-up at the same point):
+ *   kind 0: the CG column half  w = P^T p            (Alg. 2 inner CG, F_r(rho) p)
+ *   kind 1: the CG row half     y = P (w / c(P)), q = r(P) p - rho y, <p, q>
+ *   kind 2: the fused two-sided HVP sweep of eot_hvp
+ *   kind 3: the row log-sum-exp sweep (Alg. 3 / Alg. 4 row updates)
+ * ms_out: host, average milliseconds per launch. Synchronises. */
+eot_status eot_sweep_bench(eot_handle h, const eot_problem* prob, const double* u, const double* v,
+                           double gamma, int32_t kind, int32_t iters, double* ms_out, void* stream);
+
+/* Number of this library's kernel launches issued on the handle so far
+ * (graph-launched kernels counted once per launched node execution estimate:
+ * CG kernels count 4 per CG iteration). For launch accounting in benchmarks. */
+int64_t eot_kernel_launches(eot_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EOT_H_ */

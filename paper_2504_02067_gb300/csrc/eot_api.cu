@@ -1,0 +1,315 @@
+// C ABI of include/eot.h: handle lifecycle, argument checks, dispatch to the
+// FP32 (mixed / plain) and FP64 solver instantiations, error capture.
+#include <cmath>
+#include <cstring>
+
+#include "solver.cuh"
+
+using namespace eot;
+
+namespace eot {
+
+static void free_all(eot_handle h) {
+  free_graphs(h);
+  for (void* p : h->allocs) cudaFree(p);
+  h->allocs.clear();
+  if (h->h_sc) cudaFreeHost(h->h_sc);
+  if (h->h_status) cudaFreeHost(h->h_status);
+  h->h_sc = nullptr;
+  h->h_status = nullptr;
+  h->cap_n = h->cap_m = h->cap_rowpart = 0;
+  h->rowpart = nullptr;
+}
+
+void free_graphs(eot_handle h) {
+  for (auto& kv : h->graphs) {
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+  }
+  h->graphs.clear();
+}
+
+void ensure_capacity(eot_handle h, int64_t n, int64_t m) {
+  if (n <= h->cap_n && m <= h->cap_m) return;
+  EOT_CUDA(cudaDeviceSynchronize());
+  const int64_t N = std::max(n, h->cap_n), Mm = std::max(m, h->cap_m);
+  free_all(h);
+  const int64_t L = std::max(N, Mm);
+  h->max_strips = (Mm + 31) / 32 + 1;
+  h->dot_slots = std::max<int64_t>(std::max<int64_t>(4096, h->max_strips), kVecCtas);
+  EOT_CUDA(cudaHostAlloc((void**)&h->h_sc, (SC_COUNT + 1) * sizeof(double), cudaHostAllocDefault));
+  EOT_CUDA(cudaHostAlloc((void**)&h->h_status, sizeof(int), cudaHostAllocDefault));
+  h->sc = (double*)dev_alloc(h, SC_COUNT * sizeof(double));
+  h->status = (int*)dev_alloc(h, sizeof(int));
+  h->cnt_strip = (int*)dev_alloc(h, h->max_strips * sizeof(int));
+  h->cnt_rowblk = (int*)dev_alloc(h, h->max_rowblk * sizeof(int));
+  h->cnt_dot = (int*)dev_alloc(h, sizeof(int));
+  EOT_CUDA(cudaMemset(h->sc, 0, SC_COUNT * sizeof(double)));
+  EOT_CUDA(cudaMemset(h->status, 0, sizeof(int)));
+  EOT_CUDA(cudaMemset(h->cnt_strip, 0, h->max_strips * sizeof(int)));
+  EOT_CUDA(cudaMemset(h->cnt_rowblk, 0, h->max_rowblk * sizeof(int)));
+  EOT_CUDA(cudaMemset(h->cnt_dot, 0, sizeof(int)));
+  h->colpart = (double*)dev_alloc(h, 2 * h->max_rowblk * Mm * sizeof(double));
+  h->dotpart = (double*)dev_alloc(h, 2 * h->dot_slots * sizeof(double));
+  double** nv[] = {&h->Al, &h->rowfac, &h->rP, &h->logrP, &h->rowmax, &h->rt, &h->logrt,
+                   &h->du, &h->x, &h->res, &h->z, &h->p, &h->q, &h->y, &h->Yx, &h->M,
+                   &h->diag, &h->y0, &h->du0, &h->nt0, &h->nt1, &h->rPs};
+  for (double** p : nv) *p = (double*)dev_alloc(h, N * sizeof(double));
+  double** mv[] = {&h->Bl, &h->colfac, &h->cP, &h->logcP, &h->ct, &h->logct, &h->dv, &h->mt0, &h->mt1};
+  for (double** p : mv) *p = (double*)dev_alloc(h, Mm * sizeof(double));
+  void** ev[] = {&h->Ah, &h->Bh, &h->xw0, &h->xw1, &h->zf, &h->wsq, &h->ewr, &h->ewc};
+  for (void** p : ev) *p = dev_alloc(h, L * sizeof(double));
+  h->cap_n = N;
+  h->cap_m = Mm;
+}
+
+void ensure_rowpart(eot_handle h, int64_t n, int64_t strips) {
+  const int64_t need = 2 * strips * std::max(n, h->cap_n);
+  if (need <= h->cap_rowpart) return;
+  if (h->rowpart) {
+    EOT_CUDA(cudaStreamSynchronize(0));
+    EOT_CUDA(cudaDeviceSynchronize());
+    for (auto it = h->allocs.begin(); it != h->allocs.end(); ++it)
+      if (*it == h->rowpart) {
+        cudaFree(*it);
+        h->allocs.erase(it);
+        break;
+      }
+    free_graphs(h);
+  }
+  h->rowpart = (double*)dev_alloc(h, need * sizeof(double));
+  h->cap_rowpart = need;
+}
+
+}  // namespace eot
+
+namespace {
+
+template <class F>
+eot_status guarded(eot_handle h, F&& f) {
+  if (!h) return EOT_ERR_INVALID_ARG;
+  try {
+    EOT_CUDA(cudaSetDevice(h->device));
+    f();
+    h->err = "no error";
+    return EOT_OK;
+  } catch (const EotError& e) {
+    h->err = e.msg;
+    if (e.st == EOT_ERR_CUDA) return e.st;
+    // reset the tickets so that the next call starts clean
+    if (h->cnt_strip) {
+      cudaDeviceSynchronize();
+      cudaMemset(h->cnt_strip, 0, h->max_strips * sizeof(int));
+      cudaMemset(h->cnt_rowblk, 0, h->max_rowblk * sizeof(int));
+      cudaMemset(h->cnt_dot, 0, sizeof(int));
+    }
+    return e.st;
+  } catch (const std::exception& e) {
+    h->err = e.what();
+    return EOT_ERR_CUDA;
+  }
+}
+
+void check_problem(eot_handle h, const eot_problem* P, bool need_marginals) {
+  if (!P) throw EotError{EOT_ERR_INVALID_ARG, "problem is NULL"};
+  if (P->n < 1 || P->m < 1) throw EotError{EOT_ERR_INVALID_ARG, "n and m must be >= 1"};
+  if (P->n > ((int64_t)1 << 31) || P->m > ((int64_t)1 << 31))
+    throw EotError{EOT_ERR_INVALID_ARG, "n and m must be <= 2^31"};
+  if (need_marginals && (!P->r || !P->c)) throw EotError{EOT_ERR_INVALID_ARG, "r and c are required"};
+  switch (P->kind) {
+    case EOT_COST_DENSE_F32:
+      if (P->precision != EOT_PREC_MIXED && P->precision != EOT_PREC_PLAIN_FP32)
+        throw EotError{EOT_ERR_UNSUPPORTED, "DENSE_F32 takes MIXED or PLAIN_FP32 precision"};
+      break;
+    case EOT_COST_DENSE_F64:
+      if (P->precision != EOT_PREC_FP64)
+        throw EotError{EOT_ERR_UNSUPPORTED, "DENSE_F64 takes FP64 precision"};
+      break;
+    case EOT_COST_SQEUCLID_POINTS:
+      throw EotError{EOT_ERR_UNSUPPORTED, "point costs go through the point-cloud entry points"};
+    default:
+      throw EotError{EOT_ERR_INVALID_ARG, "unknown cost kind"};
+  }
+  if (!P->C) throw EotError{EOT_ERR_INVALID_ARG, "C is NULL"};
+  if (P->ldc < P->m) throw EotError{EOT_ERR_INVALID_ARG, "ldc < m"};
+  ensure_capacity(h, P->n, P->m);
+}
+
+void check_gamma(double g) {
+  if (!(g > 0.0) || !std::isfinite(g) || g >= kSplitLimit)
+    throw EotError{EOT_ERR_INVALID_ARG, "gamma must be finite, > 0 and < 2^19"};
+}
+
+bool is_f64(const eot_problem* P) { return P->kind == EOT_COST_DENSE_F64; }
+
+}  // namespace
+
+extern "C" {
+
+eot_status eot_create(eot_handle* out, int device, int64_t max_n, int64_t max_m) {
+  if (!out || max_n < 1 || max_m < 1) return EOT_ERR_INVALID_ARG;
+  *out = nullptr;
+  eot_handle h = new eot_handle_s();
+  h->device = device;
+  try {
+    EOT_CUDA(cudaSetDevice(device));
+    EOT_CUDA(cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, device));
+    ensure_capacity(h, max_n, max_m);
+  } catch (const EotError& e) {
+    free_all(h);
+    delete h;
+    return e.st;
+  }
+  *out = h;
+  return EOT_OK;
+}
+
+eot_status eot_destroy(eot_handle h) {
+  if (!h) return EOT_ERR_INVALID_ARG;
+  cudaSetDevice(h->device);
+  cudaDeviceSynchronize();
+  free_all(h);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  delete h;
+  return EOT_OK;
+}
+
+const char* eot_last_error(eot_handle h) { return h ? h->err.c_str() : "NULL handle"; }
+
+const char* eot_status_string(eot_status s) {
+  switch (s) {
+    case EOT_OK: return "EOT_OK";
+    case EOT_ERR_INVALID_ARG: return "EOT_ERR_INVALID_ARG";
+    case EOT_ERR_NONFINITE: return "EOT_ERR_NONFINITE";
+    case EOT_ERR_CG_MAXITER: return "EOT_ERR_CG_MAXITER";
+    case EOT_ERR_LINESEARCH: return "EOT_ERR_LINESEARCH";
+    case EOT_ERR_MAXSTAGES: return "EOT_ERR_MAXSTAGES";
+    case EOT_ERR_MAXNEWTON: return "EOT_ERR_MAXNEWTON";
+    case EOT_ERR_RANGE: return "EOT_ERR_RANGE";
+    case EOT_ERR_CUDA: return "EOT_ERR_CUDA";
+    case EOT_ERR_UNSUPPORTED: return "EOT_ERR_UNSUPPORTED";
+  }
+  return "unknown status";
+}
+
+eot_params eot_params_default(void) {
+  eot_params p;
+  p.gamma_i = 16.0;
+  p.gamma_f = 4096.0;
+  p.p = 1.5;
+  p.q1 = 2.0;
+  p.w_r = 0.45;
+  p.tol_final = 1e-6;
+  p.max_stages = 200;
+  p.max_newton = 200;
+  p.max_cg = 0;
+  p.max_ls = 30;
+  return p;
+}
+
+eot_status eot_marginals(eot_handle h, const eot_problem* prob, const double* u, const double* v,
+                         double gamma, double* r_out, double* c_out, double* log_r_out,
+                         double* log_c_out, double* total_out, void* stream) {
+  return guarded(h, [&] {
+    check_problem(h, prob, false);
+    check_gamma(gamma);
+    if (!u || !v) throw EotError{EOT_ERR_INVALID_ARG, "u and v are required"};
+    cudaStream_t st = (cudaStream_t)stream;
+    if (is_f64(prob)) run_marginals<double>(h, prob, u, v, gamma, r_out, c_out, log_r_out, log_c_out, total_out, st);
+    else run_marginals<float>(h, prob, u, v, gamma, r_out, c_out, log_r_out, log_c_out, total_out, st);
+  });
+}
+
+eot_status eot_hvp(eot_handle h, const eot_problem* prob, const double* u, const double* v,
+                   double gamma, double s, const double* du, const double* dv, double* out_u,
+                   double* out_v, double* r_out, double* c_out, void* stream) {
+  return guarded(h, [&] {
+    check_problem(h, prob, false);
+    check_gamma(gamma);
+    if (!u || !v || !du || !dv || !out_u || !out_v)
+      throw EotError{EOT_ERR_INVALID_ARG, "u, v, du, dv, out_u, out_v are required"};
+    if (!std::isfinite(s)) throw EotError{EOT_ERR_INVALID_ARG, "s must be finite"};
+    cudaStream_t st = (cudaStream_t)stream;
+    if (is_f64(prob)) run_hvp<double>(h, prob, u, v, gamma, s, du, dv, out_u, out_v, r_out, c_out, st);
+    else run_hvp<float>(h, prob, u, v, gamma, s, du, dv, out_u, out_v, r_out, c_out, st);
+  });
+}
+
+eot_status eot_newton_solve(eot_handle h, const eot_problem* prob, const double* u,
+                            const double* v, double gamma, const double* r_target, double eta,
+                            double rho0, int32_t max_cg, double* du_out, double* dv_out,
+                            double* rho_out, int32_t* cg_iters_out, void* stream) {
+  return guarded(h, [&] {
+    check_problem(h, prob, false);
+    check_gamma(gamma);
+    if (!u || !v || !r_target || !du_out) throw EotError{EOT_ERR_INVALID_ARG, "u, v, r_target, du_out are required"};
+    if (!(eta > 0.0) || !(rho0 >= 0.0 && rho0 < 1.0))
+      throw EotError{EOT_ERR_INVALID_ARG, "eta must be > 0 and rho0 in [0, 1)"};
+    cudaStream_t st = (cudaStream_t)stream;
+    int it = 0;
+    if (is_f64(prob)) run_newton<double>(h, prob, u, v, gamma, r_target, eta, rho0, max_cg, du_out, dv_out, rho_out, &it, st);
+    else run_newton<float>(h, prob, u, v, gamma, r_target, eta, rho0, max_cg, du_out, dv_out, rho_out, &it, st);
+    if (cg_iters_out) *cg_iters_out = it;
+  });
+}
+
+eot_status eot_solve(eot_handle h, const eot_problem* prob, const eot_params* params, double* u,
+                     double* v, eot_stats* stats, void* stream) {
+  return guarded(h, [&] {
+    check_problem(h, prob, true);
+    if (!u || !v) throw EotError{EOT_ERR_INVALID_ARG, "u and v are required"};
+    eot_params prm = params ? *params : eot_params_default();
+    check_gamma(prm.gamma_f);
+    check_gamma(prm.gamma_i);
+    if (!(prm.p >= 1.0) || !(prm.q1 > 1.0) || !(prm.w_r > 0.25 && prm.w_r < 0.5) ||
+        !(prm.tol_final > 0.0) || prm.max_stages < 1 || prm.max_newton < 1 || prm.max_ls < 1)
+      throw EotError{EOT_ERR_INVALID_ARG, "invalid eot_params"};
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    cudaStream_t st = (cudaStream_t)stream;
+    if (is_f64(prob)) run_solve<double>(h, prob, &prm, u, v, stats, st);
+    else run_solve<float>(h, prob, &prm, u, v, stats, st);
+  });
+}
+
+eot_status eot_backward(eot_handle h, const eot_problem* prob, const double* u, const double* v,
+                        double gamma, double grad_scale, float* dC, float* dX, float* dY,
+                        double* dr, double* dc, void* stream) {
+  return guarded(h, [&] {
+    check_problem(h, prob, false);
+    check_gamma(gamma);
+    if (!u || !v) throw EotError{EOT_ERR_INVALID_ARG, "u and v are required"};
+    if (dX || dY) throw EotError{EOT_ERR_UNSUPPORTED, "dX / dY need a point-cloud problem"};
+    cudaStream_t st = (cudaStream_t)stream;
+    if (dC) {
+      if (is_f64(prob)) run_backward_dense<double>(h, prob, u, v, gamma, grad_scale, dC, st);
+      else run_backward_dense<float>(h, prob, u, v, gamma, grad_scale, dC, st);
+    }
+    const double a = grad_scale / gamma;
+    if (dr) {
+      axpy4_kernel<<<vec_grid(prob->n), kThreads, 0, st>>>(prob->n, dr, 0.0, u, a, nullptr, 0.0, nullptr, 0.0);
+      h->launches++;
+    }
+    if (dc) {
+      axpy4_kernel<<<vec_grid(prob->m), kThreads, 0, st>>>(prob->m, dc, 0.0, v, a, nullptr, 0.0, nullptr, 0.0);
+      h->launches++;
+    }
+    EOT_LAUNCH_CHECK();
+  });
+}
+
+eot_status eot_sweep_bench(eot_handle h, const eot_problem* prob, const double* u, const double* v,
+                           double gamma, int32_t kind, int32_t iters, double* ms_out, void* stream) {
+  return guarded(h, [&] {
+    check_problem(h, prob, false);
+    check_gamma(gamma);
+    if (!u || !v || !ms_out || kind < 0 || kind > 3 || iters < 1)
+      throw EotError{EOT_ERR_INVALID_ARG, "u, v, ms_out required; kind in 0..3; iters >= 1"};
+    cudaStream_t st = (cudaStream_t)stream;
+    *ms_out = is_f64(prob) ? run_sweep_bench<double>(h, prob, u, v, gamma, kind, iters, st)
+                           : run_sweep_bench<float>(h, prob, u, v, gamma, kind, iters, st);
+  });
+}
+
+int64_t eot_kernel_launches(eot_handle h) { return h ? h->launches : 0; }
+
+}  // extern "C"

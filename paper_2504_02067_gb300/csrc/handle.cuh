@@ -1,0 +1,115 @@
+// Handle and workspace of the C ABI (include/eot.h). The handle owns every
+// scratch buffer of the sweeps and of the solver; caller buffers are never kept.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/eot.h"
+#include "kernels.cuh"
+
+struct EotError {
+  eot_status st;
+  std::string msg;
+};
+
+#define EOT_CUDA(call)                                                                   \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      throw EotError{EOT_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
+  } while (0)
+
+#define EOT_LAUNCH_CHECK()                                                               \
+  do {                                                                                   \
+    cudaError_t e_ = cudaGetLastError();                                                 \
+    if (e_ != cudaSuccess)                                                               \
+      throw EotError{EOT_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e_)}; \
+  } while (0)
+
+// captured CG iteration graph, keyed by everything baked into its kernel arguments
+typedef std::tuple<int, int, int, int64_t, int64_t, int64_t, uintptr_t> CgKey;
+struct CgGraph {
+  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph = nullptr;
+  int iters_per_launch = 0;
+};
+
+struct eot_handle_s {
+  int device = 0;
+  int sms = 152;
+  int64_t cap_n = 0, cap_m = 0, cap_rowpart = 0;
+  std::string err = "no error";
+  int64_t launches = 0;
+  std::vector<void*> allocs;
+
+  // scalars and status
+  double* sc = nullptr;     // device [SC_COUNT]
+  double* h_sc = nullptr;   // pinned host [SC_COUNT + 1] (last slot: status as double)
+  int* status = nullptr;    // device
+  int* h_status = nullptr;  // pinned host
+  // sweep scratch
+  int *cnt_strip = nullptr, *cnt_rowblk = nullptr, *cnt_dot = nullptr;
+  double *colpart = nullptr, *rowpart = nullptr, *dotpart = nullptr;
+  int64_t max_strips = 0, max_rowblk = 64, dot_slots = 0;
+  // FP64 n-vectors
+  double *Al = nullptr, *rowfac = nullptr, *rP = nullptr, *logrP = nullptr, *rowmax = nullptr;
+  double *rt = nullptr, *logrt = nullptr, *du = nullptr, *x = nullptr, *res = nullptr;
+  double *z = nullptr, *p = nullptr, *q = nullptr, *y = nullptr, *Yx = nullptr, *M = nullptr;
+  double *diag = nullptr, *y0 = nullptr, *du0 = nullptr, *nt0 = nullptr, *nt1 = nullptr;
+  double* rPs = nullptr;  // row sums of the factorised plan used inside F_r
+  // FP64 m-vectors
+  double *Bl = nullptr, *colfac = nullptr, *cP = nullptr, *logcP = nullptr, *ct = nullptr;
+  double *logct = nullptr, *dv = nullptr, *mt0 = nullptr, *mt1 = nullptr;
+  // element-type vectors (8 bytes per entry, used as float or double)
+  void *Ah = nullptr, *Bh = nullptr, *xw0 = nullptr, *xw1 = nullptr, *zf = nullptr;
+  void *wsq = nullptr, *ewr = nullptr, *ewc = nullptr;
+
+  std::map<CgKey, CgGraph> graphs;
+  cudaStream_t cap_stream = nullptr;
+};
+
+namespace eot {
+
+inline void* dev_alloc(eot_handle h, size_t bytes) {
+  void* p = nullptr;
+  EOT_CUDA(cudaMalloc(&p, bytes < 256 ? 256 : bytes));
+  h->allocs.push_back(p);
+  return p;
+}
+
+void ensure_capacity(eot_handle h, int64_t n, int64_t m);
+void ensure_rowpart(eot_handle h, int64_t n, int64_t strips);
+void free_graphs(eot_handle h);
+
+// sweep geometry
+struct ColGeo {
+  int64_t S;
+  int R, BR;
+};
+inline ColGeo col_geo(eot_handle h, int64_t n, int64_t m, int V) {
+  ColGeo g;
+  g.S = (m + 32 * V - 1) / (32 * V);
+  const int64_t target = 4 * (int64_t)h->sms;
+  int64_t R = (target + g.S - 1) / g.S;
+  int64_t rmax = (n + 31) / 32;
+  if (R > rmax) R = rmax;
+  if (R > h->max_rowblk) R = h->max_rowblk;
+  if (R < 1) R = 1;
+  int64_t BR = (n + R - 1) / R;
+  BR = (BR + 31) / 32 * 32;
+  g.BR = (int)BR;
+  g.R = (int)((n + BR - 1) / BR);
+  return g;
+}
+inline int row_grid(int64_t n) {
+  int64_t g = (n + kWarps - 1) / kWarps;
+  if (g > 4096) g = 4096;
+  return (int)(g < 1 ? 1 : g);
+}
+
+}  // namespace eot

@@ -1,0 +1,512 @@
+// Epilogues of the sweeps and the O(n) kernels of the solver.
+//
+// Factorisation used throughout (see common.cuh):
+//   P_ij = rowfac_i * colfac_j * E_ij,  E_ij = exp(Ah_i + Bh_j - gamma C_ij).
+// Device scalars live in one FP64 array `sc` indexed by the Sc enum, so that
+// captured CUDA graphs stay valid when rho, gamma or tolerances change.
+#pragma once
+#include "sweep.cuh"
+
+namespace eot {
+
+enum Sc : int {
+  SC_RZ = 0, SC_PQ, SC_ALPHA, SC_BETA, SC_RESL1, SC_TOL, SC_RHO, SC_ITERS, SC_ACTIVE, SC_MAXIT,
+  SC_CHECK, SC_GL1, SC_CHI2, SC_LHS, SC_SLOPE, SC_MASS, SC_CHK, SC_GAMMA, SC_AUX0, SC_AUX1,
+  SC_COUNT = 32
+};
+
+// ----------------------------------------------------------------------------
+// epilogues of row sweeps
+// ----------------------------------------------------------------------------
+
+// LSE of a row: lse_i = shift_i + Al_i + M + log S. Dots: with a target rt,
+// ||rt - exp(lse)||_1 and sum rt^2 / exp(lse) (for ||grad g||_1 and chi^2,
+// Alg. 3 / Alg. 4); without a target, sum exp(lse) (total mass).
+struct RowLseEpi {
+  static constexpr int kDot = 2;
+  const double* shift;   // nullable
+  const double* Al;      // nullable
+  double* out_lse;       // nullable
+  double* out_max;       // nullable: shift + Al + M (running max of the row)
+  const double* rt;      // nullable
+  double* sc;
+  int i0, i1;            // scalar slots of the two totals
+  __device__ void row_lse(int64_t i, double M, double S, double* d) {
+    const double off = (shift ? shift[i] : 0.0) + (Al ? Al[i] : 0.0);
+    const double lse = off + M + log(S);
+    if (out_lse) out_lse[i] = lse;
+    if (out_max) out_max[i] = off + M;
+    const double e = exp(lse);
+    if (rt) {
+      d[0] = fabs(rt[i] - e);
+      d[1] = rt[i] * rt[i] / e;
+    } else {
+      d[0] = e;
+      d[1] = 0.0;
+    }
+  }
+  __device__ void finish(const double* t) {
+    sc[i0] = t[0];
+    sc[i1] = rt ? t[1] - 1.0 : t[1];
+  }
+};
+
+// CG row half: y = P (w / c(P)), q = r(P) * p - rho * y, pq = <p, q>, alpha = rz / pq.
+struct CgRowEpi {
+  static constexpr int kDot = 1;
+  const double *rowfac, *rP, *p;
+  double *y, *q, *sc;
+  int* status;
+  __device__ void row(int64_t i, const double* s, double* d) {
+    const double yi = rowfac[i] * s[0];
+    const double qi = rP[i] * p[i] - sc[SC_RHO] * yi;
+    y[i] = yi;
+    q[i] = qi;
+    d[0] = p[i] * qi;
+  }
+  __device__ void finish(const double* t) {
+    sc[SC_PQ] = t[0];
+    if (!(t[0] > 0.0) || !isfinite(t[0])) {
+      atomicOr(status, kStatCurv);
+      sc[SC_ACTIVE] = 0.0;
+      sc[SC_ALPHA] = 0.0;
+    } else {
+      sc[SC_ALPHA] = sc[SC_RZ] / t[0];
+    }
+  }
+};
+
+// Newton-step setup, row half: y0 = P (P^T d_u0 / c(P)) and the Jacobi sums
+// sum_j P_ij^2 / c(P)_j (Lemma condition-number). check = ||y0||_1, which is
+// ||F_r(1) d_u0 + grad_u g||_1 for d_u0 = -D(r(P))^-1 grad_u g (Alg. 2 line 2).
+// The operator F_r uses the row sums rPs of this very factorised plan (so that
+// F_r(1) 1 = 0 holds to summation rounding); grad_u g and d_u0 use r(P) from the
+// row LSE, as Alg. 4 defines them.
+struct SetupRowEpi {
+  static constexpr int kDot = 1;
+  const double *rowfac, *rP, *du0;
+  double *y0, *diag, *rPs, *sc;
+  __device__ void row(int64_t i, const double* s, double* d) {
+    const double f = rowfac[i];
+    const double yy = f * s[0];
+    const double rs = f * s[2];
+    y0[i] = yy;
+    diag[i] = f * f * s[1];
+    rPs[i] = rs;
+    d[0] = fabs((rs - rP[i]) * du0[i] - yy);
+  }
+  __device__ void finish(const double* t) { sc[SC_CHECK] = t[0]; }
+};
+
+// Plain row sums: out_i = rowfac_i * s0 (and * s1).
+struct RowSumEpi {
+  static constexpr int kDot = 0;
+  const double* rowfac;
+  double *o0, *o1;
+  __device__ void row(int64_t i, const double* s, double* d) {
+    const double f = rowfac ? rowfac[i] : 1.0;
+    if (o0) o0[i] = f * s[0];
+    if (o1) o1[i] = f * s[1];
+  }
+  __device__ void finish(const double*) {}
+};
+
+// ----------------------------------------------------------------------------
+// epilogues of column sweeps
+// ----------------------------------------------------------------------------
+
+// CG column half: zf_j = colfac_j * (P^T p)_j / c(P)_j, as the next row weight.
+template <class T>
+struct CgColEpi {
+  static constexpr int kDot = 0;
+  const double *colfac, *cP;
+  T* zf;
+  __device__ void col(int64_t j, const double* s, double* d) {
+    const double f = colfac[j];
+    zf[j] = (T)(f * f * s[0] / cP[j]);
+  }
+  __device__ void finish(const double*) {}
+};
+
+// Newton-step setup, column half: c(P), and the weights of the setup row sweep.
+template <class T>
+struct SetupColEpi {
+  static constexpr int kDot = 0;
+  const double* colfac;
+  double* cP;
+  T *zf, *wsq;
+  __device__ void col(int64_t j, const double* s, double* d) {
+    const double f = colfac[j];
+    const double c = f * s[0];
+    cP[j] = c;
+    zf[j] = (T)(f * f * s[1] / c);
+    wsq[j] = (T)(f * f / c);
+  }
+  __device__ void finish(const double*) {}
+};
+
+// d_v = -P_c d_u = -(P^T d_u) / c(P)  (Alg. 4 line 7).
+struct DvColEpi {
+  static constexpr int kDot = 0;
+  const double *colfac, *cP;
+  double* dv;
+  __device__ void col(int64_t j, const double* s, double* d) { dv[j] = -colfac[j] * s[0] / cP[j]; }
+  __device__ void finish(const double*) {}
+};
+
+// Column LSE: lse_j = Bl_j + M + log S.
+//  mode 0: out_j = base_j + lse_j           (log c(P) given the column shift base)
+//  mode 1: out_j = out_j - lse_j            (column fix, Alg. 4 lines 1 and 15)
+// Dot: sum_j exp(base_j + lse_j) (the total mass, for the Armijo test).
+struct ColLseEpi {
+  static constexpr int kDot = 1;
+  const double* Bl;      // nullable
+  const double* base;    // nullable
+  double* out;
+  int mode;
+  double* sc;
+  int slot;
+  double minus;          // subtracted from the total (1 for the Armijo lhs)
+  __device__ void col_lse(int64_t j, double M, double S, double* d) {
+    const double lse = (Bl ? Bl[j] : 0.0) + M + log(S);
+    const double b = base ? base[j] : 0.0;
+    if (mode == 0) out[j] = b + lse;
+    else out[j] = out[j] - lse;
+    d[0] = exp(b + lse);
+  }
+  __device__ void finish(const double* t) { sc[slot] = t[0] - minus; }
+};
+
+// Column sums: out_j = colfac_j * s0 (and * s1).
+struct ColSumEpi {
+  static constexpr int kDot = 0;
+  const double* colfac;
+  double *o0, *o1;
+  __device__ void col(int64_t j, const double* s, double* d) {
+    const double f = colfac ? colfac[j] : 1.0;
+    if (o0) o0[j] = f * s[0];
+    if (o1) o1[j] = f * s[1];
+  }
+  __device__ void finish(const double*) {}
+};
+
+// Fused two-sided Hessian-vector product (Eq. hessian / discounted-hessian):
+//   out_u = r(P) * du + s P dv,  out_v = s P^T du + c(P) * dv.
+struct HvpEpi {
+  static constexpr int kDot = 0;
+  const double *rowfac, *colfac, *du, *dv;
+  double s;
+  double *out_u, *out_v, *r_out, *c_out;
+  __device__ void col(int64_t j, const double* t, double* d) {
+    const double f = colfac[j];
+    const double c = f * t[0];
+    if (c_out) c_out[j] = c;
+    out_v[j] = s * f * t[1] + c * dv[j];
+  }
+  __device__ void row_part(int64_t i, const double* t) {
+    const double f = rowfac[i];
+    const double r = f * t[0];
+    if (r_out) r_out[i] = r;
+    out_u[i] = r * du[i] + s * f * t[1];
+  }
+  __device__ void finish(const double*) {}
+};
+
+// ----------------------------------------------------------------------------
+// O(n) kernels
+// ----------------------------------------------------------------------------
+
+constexpr int kVecCtas = 64;  // fixed grid of the O(n) kernels (deterministic sums)
+
+inline int vec_grid(int64_t n) {
+  int64_t g = (n + kThreads - 1) / kThreads;
+  return (int)(g < 1 ? 1 : (g > kVecCtas ? kVecCtas : g));
+}
+
+// Split A = x + alpha*y - z into a high part h (multiple of 1/8, exact in T)
+// and a low FP64 part l; optional ew = (T)exp(l), fac = exp(fshift + l).
+// plain != 0: round A to T directly and drop the remainder (plain FP32 path).
+template <class T>
+__global__ void split_kernel(int64_t n, const double* x, const double* y, double alpha,
+                             const double* z, int plain, T* h, double* l, T* ew, double* fac,
+                             const double* fshift, int* status) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double A = x[i];
+    if (y) A += alpha * y[i];
+    if (z) A -= z[i];
+    double hh, ll;
+    if (!isfinite(A)) {
+      atomicOr(status, kStatNonfinite);
+      hh = A;
+      ll = 0.0;
+    } else if (sizeof(T) == 8) {
+      hh = A;
+      ll = 0.0;
+    } else if (plain) {
+      hh = (double)(float)A;
+      ll = 0.0;
+    } else {
+      if (fabs(A) >= kSplitLimit) atomicOr(status, kStatRange);
+      hh = rint(A * 8.0) * kGrid;
+      ll = A - hh;
+    }
+    h[i] = (T)hh;
+    if (l) l[i] = ll;
+    if (ew) ew[i] = (T)exp(ll);
+    if (fac) fac[i] = exp((fshift ? fshift[i] : 0.0) + ll);
+  }
+}
+
+// Deterministic grid reduction of up to two per-thread values: warp sums, then
+// cta_dot_finish (fixed CTA order). Epi::finish receives the totals.
+template <int ND, class Epi>
+__device__ __forceinline__ void vec_finish(double (&v)[2], double* dotpart, int* cnt, Epi& epi) {
+  double wd[ND > 0 ? ND : 1];
+#pragma unroll
+  for (int k = 0; k < ND; ++k) wd[k] = warp_sum(v[k]);
+  cta_dot_finish<ND>(wd, blockIdx.x, gridDim.x, dotpart, cnt, epi);
+}
+
+struct SlotFinish {
+  static constexpr int kDot = 2;
+  double* sc;
+  int s0, s1;  // -1 = unused
+  double add0, add1;
+  __device__ void finish(const double* t) {
+    if (s0 >= 0) sc[s0] = t[0] + add0;
+    if (s1 >= 0) sc[s1] = t[1] + add1;
+  }
+};
+
+struct CgInitFinish {
+  static constexpr int kDot = 2;
+  double* sc;
+  __device__ void finish(const double* t) {
+    sc[SC_RZ] = t[0];
+    sc[SC_RESL1] = t[1];
+    sc[SC_ITERS] = 0.0;
+    sc[SC_BETA] = 0.0;
+    sc[SC_ACTIVE] = (t[1] > sc[SC_TOL] && isfinite(t[0])) ? 1.0 : 0.0;
+  }
+};
+
+struct CgUpdateFinish {
+  static constexpr int kDot = 2;
+  double* sc;
+  int* status;
+  cudaGraphConditionalHandle cond;
+  __device__ void finish(const double* t) {
+    const double rz_new = t[0];
+    sc[SC_BETA] = rz_new / sc[SC_RZ];
+    sc[SC_RZ] = rz_new;
+    sc[SC_RESL1] = t[1];
+    const double it = sc[SC_ITERS] + 1.0;
+    sc[SC_ITERS] = it;
+    bool go = t[1] > sc[SC_TOL] && it < sc[SC_MAXIT] && it < 1.0e6;
+    if (!isfinite(t[0]) || !isfinite(t[1])) {
+      atomicOr(status, kStatCgNan);
+      go = false;
+    }
+    sc[SC_ACTIVE] = go ? 1.0 : 0.0;
+    if (!go && cond) cudaGraphSetConditional(cond, 0);
+  }
+};
+
+// Newton-step preparation: r(P) = exp(log r(P)), d_u0 = r~ / r(P) - 1 (Alg. 2
+// line 1), row weights of the setup column sweep.
+template <class T>
+__global__ void prep_setup_kernel(int64_t n, const double* logrP, const double* rt,
+                                  const double* rowfac, double* rP, double* du0, T* xw0, T* xw1) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double r = exp(logrP[i]);
+    const double d = rt[i] / r - 1.0;
+    rP[i] = r;
+    du0[i] = d;
+    xw0[i] = (T)rowfac[i];
+    xw1[i] = (T)(rowfac[i] * d);
+  }
+}
+
+// PCG start (x = 0): M = diag(F_r(rho)) = r(P) - rho * diag, res = b = r~ - r(P),
+// z = res / M, p = z; rz = <res, z>, ||res||_1.
+// M_ii = r(P)_i (1 - rho mu_i) >= (1 - rho) r(P)_i since mu_i = (P_rc)_ii <= 1
+// (Lemma condition-number); the bound is applied to absorb FP32 summation
+// rounding when mu_i is close to 1.
+template <class T>
+__global__ void cg_init_kernel(int64_t n, const double* rP, const double* rPs, const double* rt,
+                               const double* diag, const double* rowfac, double* M, double* x,
+                               double* res, double* z, double* p, double* Yx, T* xw, double* sc,
+                               double* dotpart, int* cnt) {
+  const double rho = sc[SC_RHO];
+  double v[2] = {0.0, 0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double Mi = fmax(rPs[i] - rho * diag[i], (1.0 - rho) * rPs[i]);
+    const double b = rt[i] - rP[i];
+    const double zi = b / Mi;
+    M[i] = Mi;
+    x[i] = 0.0;
+    res[i] = b;
+    z[i] = zi;
+    p[i] = zi;
+    Yx[i] = 0.0;
+    xw[i] = (T)(rowfac[i] * zi);
+    v[0] += b * zi;
+    v[1] += fabs(b);
+  }
+  CgInitFinish f{sc};
+  vec_finish<2>(v, dotpart, cnt, f);
+}
+
+// PCG step, after q = F_r(rho) p and alpha = rz / <p, q> are known:
+// x += alpha p, res -= alpha q, Yx += alpha y, z = res / M; then beta, the stop test.
+template <class T>
+__global__ void cg_update_kernel(int64_t n, const double* p, const double* q, const double* y,
+                                 const double* M, double* x, double* res, double* Yx, double* z,
+                                 double* sc, double* dotpart, int* cnt, int* status,
+                                 cudaGraphConditionalHandle cond) {
+  if (sc[SC_ACTIVE] == 0.0) {
+    if (cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, 0);
+    return;
+  }
+  const double alpha = sc[SC_ALPHA];
+  double v[2] = {0.0, 0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] += alpha * p[i];
+    const double r = res[i] - alpha * q[i];
+    res[i] = r;
+    Yx[i] += alpha * y[i];
+    const double zi = r / M[i];
+    z[i] = zi;
+    v[0] += r * zi;
+    v[1] += fabs(r);
+  }
+  CgUpdateFinish f{sc, status, cond};
+  vec_finish<2>(v, dotpart, cnt, f);
+}
+
+// p = z + beta p, and the FP32 row weights of the next column sweep.
+template <class T>
+__global__ void cg_pupdate_kernel(int64_t n, const double* z, const double* rowfac, double* p,
+                                  T* xw, const double* sc) {
+  if (sc[SC_ACTIVE] == 0.0) return;
+  const double beta = sc[SC_BETA];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double pi = z[i] + beta * p[i];
+    p[i] = pi;
+    xw[i] = (T)(rowfac[i] * pi);
+  }
+}
+
+// Undiscounted Newton residual of the CG iterate: F_r(1) x + grad_u g
+// = -(res + (1 - rho) Yx), with Yx = P D(c)^-1 P^T x accumulated along the CG
+// steps. chk = ||.||_1 (Alg. 2 line 2).
+static __global__ void cg_check_kernel(int64_t n, const double* res, const double* Yx, double* sc,
+                                double* dotpart, int* cnt) {
+  const double om = 1.0 - sc[SC_RHO];
+  double v[2] = {0.0, 0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    v[0] += fabs(res[i] + om * Yx[i]);
+  SlotFinish f{sc, SC_CHK, -1, 0.0, 0.0};
+  vec_finish<1>(v, dotpart, cnt, f);
+}
+
+// Row weights rowfac * d_u of the d_v sweep and the Armijo slope <-grad_u g, d_u>
+// = <r~ - r(P), d_u>.
+template <class T>
+__global__ void prep_dv_kernel(int64_t n, const double* du, const double* rowfac, const double* rt,
+                               const double* rP, T* xw, double* sc, double* dotpart, int* cnt) {
+  double v[2] = {0.0, 0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    xw[i] = (T)(rowfac[i] * du[i]);
+    v[0] += (rt[i] - rP[i]) * du[i];
+  }
+  SlotFinish f{sc, SC_SLOPE, -1, 0.0, 0.0};
+  vec_finish<1>(v, dotpart, cnt, f);
+}
+
+// y = a*x + b*y + c*z (+ d*w): small FP64 vector updates of the outer loops.
+static __global__ void axpy4_kernel(int64_t n, double* y, double b, const double* x, double a,
+                             const double* z, double c, const double* w, double d) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double t = b == 0.0 ? 0.0 : b * y[i];
+    if (x) t += a * x[i];
+    if (z) t += c * z[i];
+    if (w) t += d * w[i];
+    y[i] = t;
+  }
+}
+
+// Asymmetric smoothing (Sec. 3.4): t = (1 - w eps) r + (w eps / n); log t.
+static __global__ void smooth_kernel(int64_t n, const double* r, double w_eps, double* t, double* logt) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = (1.0 - w_eps) * r[i] + w_eps / (double)n;
+    t[i] = v;
+    logt[i] = log(v);
+  }
+}
+
+// Sums of up to two functions of one vector: kind 0: x log x (entropy terms,
+// 0 log 0 = 0) and x; kind 1: |x - y| and x.
+static __global__ void vec_stats_kernel(int64_t n, const double* x, const double* y, int kind, double* sc,
+                                 int s0, int s1, double* dotpart, int* cnt, int* status) {
+  double v[2] = {0.0, 0.0};
+  bool bad = false;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double a = x[i];
+    if (!isfinite(a)) bad = true;
+    if (kind == 0) {
+      v[0] += a > 0.0 ? a * log(a) : 0.0;
+      v[1] += a;
+      if (a < 0.0) bad = true;
+    } else {
+      v[0] += fabs(a - y[i]);
+      v[1] += a;
+    }
+  }
+  if (bad) atomicOr(status, kStatNonfinite);
+  SlotFinish f{sc, s0, s1, 0.0, 0.0};
+  vec_finish<2>(v, dotpart, cnt, f);
+}
+
+// out[i] = (T)(f[i] * x[i]) (x nullable = 1): FP32 / FP64 sweep weights from FP64 factors.
+template <class T>
+__global__ void weight_kernel(int64_t n, const double* f, const double* x, T* out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (T)(f[i] * (x ? x[i] : 1.0));
+}
+
+// dC_ij = scale * P_ij written densely (ld ldo), P_ij = rowfac_i colfac_j exp(Ah_i + Bh_j - gamma C_ij).
+template <class T>
+__global__ void plan_dense_kernel(int64_t n, int64_t m, const T* C, int64_t ldc, const T* Ah,
+                                  const T* Bh, const double* gamma_dev, const double* rowfac,
+                                  const double* colfac, double scale, float* out, int64_t ldo) {
+  const T g = (T)*gamma_dev;
+  const int64_t total = n * m;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = k / m, j = k - i * m;
+    const T t = fmaT(-g, C[i * ldc + j], Ah[i] + Bh[j]);
+    out[i * ldo + j] = (float)(scale * rowfac[i] * colfac[j] * (double)expT(t));
+  }
+}
+
+static __global__ void exp_kernel(int64_t n, const double* x, double* y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = exp(x[i]);
+}
+
+static __global__ void set_scalar_kernel(double* sc, int slot, double v) { sc[slot] = v; }
+
+}  // namespace eot

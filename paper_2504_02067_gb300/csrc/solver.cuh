@@ -1,0 +1,475 @@
+// Host orchestration of the truncated-Newton EOT solver over the sweep kernels.
+//   Alg. 1 (MDOT, adaptive q, smoothing)  -> run_solve
+//   Alg. 4 (TruncatedNewtonProject)       -> Solver::project
+//   Alg. 3 (ChiSinkhorn)                  -> inside Solver::project
+//   Alg. 2 (NewtonSolve) + Jacobi PCG     -> Solver::newton
+// Control flow stays on the host; every test reads a few FP64 scalars that the
+// kernels reduced on the device. The CG iterations of one linear solve run as a
+// captured CUDA graph of several iterations whose kernels turn into no-ops once
+// the device-side stop flag is cleared (or, optionally, as a graph WHILE node).
+#pragma once
+#include <chrono>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+
+#include "handle.cuh"
+
+namespace eot {
+
+struct SolveCounters {
+  int64_t sweeps_cg = 0, sweeps_newton = 0, sweeps_ls = 0, sweeps_sk = 0, sweeps_other = 0;
+  int64_t cg_iters = 0, cg_solves = 0, newton_steps = 0, ls_trials = 0, sk_iters = 0;
+  int64_t curvature_stops = 0;
+  double rho_last = 0.0;
+};
+
+enum class CgMode { kHost, kBatch, kWhile };
+
+inline CgMode cg_mode_from_env() {
+  const char* e = std::getenv("EOT_CG_GRAPH");
+  if (!e) return CgMode::kBatch;
+  if (!std::strcmp(e, "while")) return CgMode::kWhile;
+  if (!std::strcmp(e, "none")) return CgMode::kHost;
+  return CgMode::kBatch;
+}
+
+template <class T>
+struct Solver {
+  static constexpr int VEC = 16 / (int)sizeof(T);
+  eot_handle h;
+  cudaStream_t st;
+  int64_t n, m, ldc;
+  const T* C;
+  int V;
+  bool plain;
+  int vg_n, vg_m, rg;
+  ColGeo geo;
+  SolveCounters cnt;
+  int64_t* sweep_bucket;
+
+  Solver(eot_handle h_, const eot_problem* P, cudaStream_t s)
+      : h(h_), st(s), n(P->n), m(P->m), ldc(P->ldc), C((const T*)P->C) {
+    plain = P->precision == EOT_PREC_PLAIN_FP32;
+    const bool aligned = ((uintptr_t)C % 16) == 0;
+    V = (aligned && (m % VEC) == 0 && (ldc % VEC) == 0) ? VEC : 1;
+    vg_n = vec_grid(n);
+    vg_m = vec_grid(m);
+    rg = row_grid(n);
+    geo = col_geo(h, n, m, V);
+    sweep_bucket = &cnt.sweeps_other;
+  }
+
+  T* Ah() { return (T*)h->Ah; }
+  T* Bh() { return (T*)h->Bh; }
+  T* xw0() { return (T*)h->xw0; }
+  T* xw1() { return (T*)h->xw1; }
+  T* zf() { return (T*)h->zf; }
+  T* wsq() { return (T*)h->wsq; }
+  T* ewr() { return (T*)h->ewr; }
+  T* ewc() { return (T*)h->ewc; }
+
+  SweepArgs<T> args() const {
+    SweepArgs<T> a{};
+    a.C = C;
+    a.n = n;
+    a.m = m;
+    a.ldc = ldc;
+    a.Ah = (const T*)h->Ah;
+    a.Bh = (const T*)h->Bh;
+    a.gamma = T(0);
+    a.colpart = h->colpart;
+    a.rowpart = h->rowpart;
+    a.cnt_strip = h->cnt_strip;
+    a.cnt_rowblk = h->cnt_rowblk;
+    a.dotpart = h->dotpart;
+    a.cnt_dot = h->cnt_dot;
+    a.rows_per_block = geo.BR;
+    a.nrowblk = geo.R;
+    a.gamma_dev = h->sc + SC_GAMMA;
+    a.active = nullptr;
+    return a;
+  }
+
+  double gamma_host = 0.0;
+  void set_scalar(int slot, double v) {
+    if (slot == SC_GAMMA) gamma_host = v;
+    set_scalar_kernel<<<1, 1, 0, st>>>(h->sc, slot, v);
+    EOT_LAUNCH_CHECK();
+    h->launches++;
+  }
+
+  std::string ctx;  // where the solver is, for error messages
+  const bool trace = std::getenv("EOT_TRACE") != nullptr;
+
+  // Read every device scalar and the status word (synchronises the stream).
+  // Lost CG curvature (kStatCurv) is handled by the caller, not thrown.
+  const double* read() {
+    EOT_CUDA(cudaMemcpyAsync(h->h_sc, h->sc, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, st));
+    EOT_CUDA(cudaMemcpyAsync(h->h_status, h->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    EOT_CUDA(cudaStreamSynchronize(st));
+    const int s = *h->h_status;
+    if (s & kStatNonfinite) throw EotError{EOT_ERR_NONFINITE, "non-finite potential or marginal" + ctx};
+    if (s & kStatCgNan) throw EotError{EOT_ERR_NONFINITE, "non-finite CG residual" + ctx};
+    if (s & kStatRange) throw EotError{EOT_ERR_RANGE, "|potential| >= 2^19 (mixed-precision split)" + ctx};
+    return h->h_sc;
+  }
+  int status_bits() const { return *h->h_status; }
+  void clear_status() { EOT_CUDA(cudaMemsetAsync(h->status, 0, sizeof(int), st)); }
+
+  // ---------------- O(n) helpers ----------------
+  void split_rows(const double* x, const double* y, double alpha, const double* z, double* l,
+                  T* ew, double* fac, const double* fshift) {
+    split_kernel<T><<<vg_n, kThreads, 0, st>>>(n, x, y, alpha, z, plain ? 1 : 0, Ah(), l, ew, fac,
+                                               fshift, h->status);
+    EOT_LAUNCH_CHECK();
+    h->launches++;
+  }
+  void split_cols(const double* x, const double* y, double alpha, const double* z, double* l,
+                  T* ew, double* fac, const double* fshift) {
+    split_kernel<T><<<vg_m, kThreads, 0, st>>>(m, x, y, alpha, z, plain ? 1 : 0, Bh(), l, ew, fac,
+                                               fshift, h->status);
+    EOT_LAUNCH_CHECK();
+    h->launches++;
+  }
+  void axpy(int64_t len, double* y, double b, const double* x, double a, const double* z = nullptr,
+            double c = 0.0, const double* w = nullptr, double d = 0.0) {
+    axpy4_kernel<<<vec_grid(len), kThreads, 0, st>>>(len, y, b, x, a, z, c, w, d);
+    EOT_LAUNCH_CHECK();
+    h->launches++;
+  }
+  void copy(double* dst, const double* src, int64_t len) {
+    EOT_CUDA(cudaMemcpyAsync(dst, src, len * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  }
+
+  // ---------------- sweep launchers ----------------
+  template <int NR, bool LSE, int SQM, class Epi>
+  void row(const SweepArgs<T>& a, const Epi& e) {
+    if (V == VEC) row_sweep_kernel<T, VEC, NR, LSE, SQM, Epi><<<rg, kThreads, 0, st>>>(a, e);
+    else row_sweep_kernel<T, 1, NR, LSE, SQM, Epi><<<rg, kThreads, 0, st>>>(a, e);
+    EOT_LAUNCH_CHECK();
+    h->launches++;
+    (*sweep_bucket)++;
+  }
+  template <int NC, bool LSE, int NR, class Epi>
+  void col(const SweepArgs<T>& a, const Epi& e) {
+    dim3 grid((unsigned)geo.S, (unsigned)geo.R);
+    if (V == VEC) col_sweep_kernel<T, VEC, NC, LSE, NR, Epi><<<grid, kThreads, 0, st>>>(a, e);
+    else col_sweep_kernel<T, 1, NC, LSE, NR, Epi><<<grid, kThreads, 0, st>>>(a, e);
+    EOT_LAUNCH_CHECK();
+    h->launches++;
+    (*sweep_bucket)++;
+  }
+
+  // log r(P) and the running row max at (u, v): A = u - rshift, B = v.
+  // With a target rt, also ||rt - r(P)||_1 -> SC_GL1 and chi^2(rt | r(P)) -> SC_CHI2.
+  void row_lse(const double* u, const double* v, const double* rshift, double* out_lse,
+               double* out_max, const double* rt, int s0 = SC_GL1, int s1 = SC_CHI2) {
+    split_rows(u, nullptr, 0.0, rshift, h->Al, nullptr, nullptr, nullptr);
+    split_cols(v, nullptr, 0.0, nullptr, h->Bl, ewc(), nullptr, nullptr);
+    SweepArgs<T> a = args();
+    a.wc[0] = ewc();
+    RowLseEpi e{rshift, h->Al, out_lse, out_max, rt, h->sc, s0, s1};
+    row<1, true, 0>(a, e);
+  }
+
+  // Column LSE at (u + alpha du, v + alpha dv): B = v + alpha dv - cshift.
+  // mode 0: out = cshift + LSE (log c(P)); mode 1: out -= LSE (column fix).
+  void col_lse(const double* u, const double* du, const double* v, const double* dv, double alpha,
+               const double* cshift, double* out, int mode, int slot, double minus) {
+    split_rows(u, du, alpha, nullptr, h->Al, ewr(), nullptr, nullptr);
+    split_cols(v, dv, alpha, cshift, h->Bl, nullptr, nullptr, nullptr);
+    SweepArgs<T> a = args();
+    a.wr[0] = ewr();
+    ColLseEpi e{h->Bl, mode == 0 ? cshift : nullptr, out, mode, h->sc, slot, minus};
+    col<1, true, 0>(a, e);
+  }
+
+  // ---------------- Alg. 2: NewtonSolve ----------------
+  // At (u, v) with log r(P) and the row maxima from the last row LSE. Targets r~.
+  // Leaves d_u in h->du and d_v = -P_c d_u in h->dv; returns the rho of the last CG
+  // solve (or rho0 when no CG solve ran). Also leaves r(P), c(P) in h->rP, h->cP.
+  double newton(const double* u, const double* v, const double* rt, double gl1, double eta,
+                double rho0, int max_cg, CgMode mode, bool* ran_cg) {
+    int64_t* saved = sweep_bucket;
+    sweep_bucket = &cnt.sweeps_newton;
+    // factorisation P = rowfac * colfac * E with row shift = running row max
+    split_rows(u, nullptr, 0.0, h->rowmax, h->Al, nullptr, h->rowfac, h->rowmax);
+    split_cols(v, nullptr, 0.0, nullptr, h->Bl, ewc(), h->colfac, nullptr);
+    prep_setup_kernel<T><<<vg_n, kThreads, 0, st>>>(n, h->logrP, rt, h->rowfac, h->rP, h->du0,
+                                                    xw0(), xw1());
+    EOT_LAUNCH_CHECK();
+    h->launches++;
+    {
+      SweepArgs<T> a = args();
+      a.wr[0] = xw0();
+      a.wr[1] = xw1();
+      SetupColEpi<T> e{h->colfac, h->cP, zf(), wsq()};
+      col<2, false, 0>(a, e);
+    }
+    {
+      SweepArgs<T> a = args();
+      a.wc[0] = zf();
+      a.wc[1] = wsq();
+      a.wc[2] = ewc();
+      SetupRowEpi e{h->rowfac, h->rP, h->du0, h->y0, h->diag, h->rPs, h->sc};
+      row<3, false, 2>(a, e);
+    }
+    const double check0 = read()[SC_CHECK];
+    double rho = rho0, rho_last = rho0;
+    *ran_cg = false;
+    const double* du_final = h->du0;
+    if (!(check0 <= eta * gl1)) {
+      const double tol = 0.25 * eta * gl1;
+      set_scalar(SC_TOL, tol);
+      set_scalar(SC_MAXIT, (double)max_cg);
+      for (int solve = 0;; ++solve) {
+        set_scalar(SC_RHO, rho);
+        run_cg(mode, max_cg, rt);
+        cg_check_kernel<<<vg_n, kThreads, 0, st>>>(n, h->res, h->Yx, h->sc, h->dotpart, h->cnt_dot);
+        EOT_LAUNCH_CHECK();
+        h->launches++;
+        const double* s = read();
+        const double it = s[SC_ITERS], rl1 = s[SC_RESL1], chk = s[SC_CHK];
+        cnt.cg_iters += (int64_t)it;
+        cnt.sweeps_cg += 2 * (int64_t)it + ((status_bits() & kStatCurv) ? 2 : 0);
+        cnt.cg_solves++;
+        *ran_cg = true;
+        rho_last = rho;
+        if (status_bits() & kStatCurv) {
+          // <p, F_r(rho) p> <= 0 in finite precision: stop CG and keep the iterate,
+          // the truncated-Newton convention; no larger rho can help, so return.
+          cnt.curvature_stops++;
+          clear_status();
+          du_final = it > 0 ? h->x : h->du0;
+          break;
+        }
+        if (rl1 > tol) throw EotError{EOT_ERR_CG_MAXITER, "linear CG reached max_cg" + ctx};
+        du_final = h->x;
+        if (chk <= eta * gl1) break;
+        rho = 1.0 - (1.0 - rho) / 4.0;
+        if (solve > 60) throw EotError{EOT_ERR_CG_MAXITER, "rho annealing did not meet the forcing test" + ctx};
+      }
+    }
+    if (du_final != h->du) copy(h->du, du_final, n);
+    // d_v = -(P^T d_u) / c(P) and the Armijo slope <r~ - r(P), d_u>
+    prep_dv_kernel<T><<<vg_n, kThreads, 0, st>>>(n, h->du, h->rowfac, rt, h->rP, xw0(), h->sc,
+                                                 h->dotpart, h->cnt_dot);
+    EOT_LAUNCH_CHECK();
+    h->launches++;
+    {
+      SweepArgs<T> a = args();
+      a.wr[0] = xw0();
+      DvColEpi e{h->colfac, h->cP, h->dv};
+      col<1, false, 0>(a, e);
+    }
+    sweep_bucket = saved;
+    return rho_last;
+  }
+
+  // One CG iteration's four kernels (column half, row half, update, p update).
+  void cg_iteration(cudaStream_t s, cudaGraphConditionalHandle cond) {
+    {
+      SweepArgs<T> a = args();
+      a.wr[0] = xw0();
+      a.active = h->sc + SC_ACTIVE;
+      CgColEpi<T> e{h->colfac, h->cP, zf()};
+      dim3 grid((unsigned)geo.S, (unsigned)geo.R);
+      if (V == VEC) col_sweep_kernel<T, VEC, 1, false, 0, CgColEpi<T>><<<grid, kThreads, 0, s>>>(a, e);
+      else col_sweep_kernel<T, 1, 1, false, 0, CgColEpi<T>><<<grid, kThreads, 0, s>>>(a, e);
+    }
+    {
+      SweepArgs<T> a = args();
+      a.wc[0] = zf();
+      a.active = h->sc + SC_ACTIVE;
+      CgRowEpi e{h->rowfac, h->rPs, h->p, h->y, h->q, h->sc, h->status};
+      if (V == VEC) row_sweep_kernel<T, VEC, 1, false, false, CgRowEpi><<<rg, kThreads, 0, s>>>(a, e);
+      else row_sweep_kernel<T, 1, 1, false, false, CgRowEpi><<<rg, kThreads, 0, s>>>(a, e);
+    }
+    cg_update_kernel<T><<<vg_n, kThreads, 0, s>>>(n, h->p, h->q, h->y, h->M, h->x, h->res, h->Yx,
+                                                  h->z, h->sc, h->dotpart, h->cnt_dot, h->status,
+                                                  cond);
+    cg_pupdate_kernel<T><<<vg_n, kThreads, 0, s>>>(n, h->z, h->rowfac, h->p, xw0(), h->sc);
+  }
+
+  CgGraph& get_graph(CgMode mode) {
+    const int B = mode == CgMode::kWhile ? 1 : 6;
+    const CgKey key{(int)sizeof(T), V, mode == CgMode::kWhile ? 1 : 0, n, m, ldc, (uintptr_t)C};
+    auto it = h->graphs.find(key);
+    if (it != h->graphs.end()) return it->second;
+    if (h->graphs.size() >= 32) free_graphs(h);
+    CgGraph g;
+    if (!h->cap_stream) EOT_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    if (mode == CgMode::kWhile) {
+      EOT_CUDA(cudaGraphCreate(&g.graph, 0));
+      cudaGraphConditionalHandle cond;
+      EOT_CUDA(cudaGraphConditionalHandleCreate(&cond, g.graph, 1, cudaGraphCondAssignDefault));
+      cudaGraphNodeParams np{};
+      np.type = cudaGraphNodeTypeConditional;
+      np.conditional.handle = cond;
+      np.conditional.type = cudaGraphCondTypeWhile;
+      np.conditional.size = 1;
+      cudaGraphNode_t node;
+      EOT_CUDA(cudaGraphAddNode(&node, g.graph, nullptr, nullptr, 0, &np));
+      cudaGraph_t body = np.conditional.phGraph_out[0];
+      EOT_CUDA(cudaStreamBeginCaptureToGraph(h->cap_stream, body, nullptr, nullptr, 0,
+                                             cudaStreamCaptureModeRelaxed));
+      cg_iteration(h->cap_stream, cond);
+      cudaGraph_t out;
+      EOT_CUDA(cudaStreamEndCapture(h->cap_stream, &out));
+    } else {
+      EOT_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeRelaxed));
+      for (int b = 0; b < B; ++b) cg_iteration(h->cap_stream, 0);
+      EOT_CUDA(cudaStreamEndCapture(h->cap_stream, &g.graph));
+    }
+    EOT_CUDA(cudaGraphInstantiate(&g.exec, g.graph, 0));
+    g.iters_per_launch = B;
+    return h->graphs.emplace(key, g).first->second;
+  }
+
+  // Runs PCG from x = 0 on F_r(rho) until the device stop flag clears.
+  void run_cg(CgMode mode, int max_cg, const double* rt) {
+    cg_init_kernel<T><<<vg_n, kThreads, 0, st>>>(n, h->rP, h->rPs, rt, h->diag, h->rowfac, h->M, h->x,
+                                                 h->res, h->z, h->p, h->Yx, xw0(), h->sc,
+                                                 h->dotpart, h->cnt_dot);
+    EOT_LAUNCH_CHECK();
+    h->launches++;
+    if (mode == CgMode::kHost) {
+      for (int it = 0; it < max_cg; it += 4) {
+        for (int b = 0; b < 4; ++b) cg_iteration(st, 0);
+        EOT_LAUNCH_CHECK();
+        h->launches += 16;
+        if (read()[SC_ACTIVE] == 0.0) break;
+      }
+      return;
+    }
+    CgGraph& g = get_graph(mode);
+    if (mode == CgMode::kWhile) {
+      EOT_CUDA(cudaGraphLaunch(g.exec, st));
+      h->launches += 1;
+      return;
+    }
+    const int maxl = (max_cg + g.iters_per_launch - 1) / g.iters_per_launch + 1;
+    for (int l = 0; l < maxl; ++l) {
+      EOT_CUDA(cudaGraphLaunch(g.exec, st));
+      h->launches += 4 * g.iters_per_launch;
+      if (read()[SC_ACTIVE] == 0.0) break;
+    }
+  }
+
+  // ---------------- Alg. 4: TruncatedNewtonProject ----------------
+  // (u, v) in/out; targets (rt, ct) = smoothed marginals with logs; tolerance eps.
+  // Returns false if the Newton budget ran out. delta_min is reported.
+  bool project(double* u, double* v, double eps, const eot_params& prm, int max_cg, CgMode mode,
+               double* delta_min, double* gl1_out) {
+    double* rt = h->rt;
+    double* logrt = h->logrt;
+    double* logct = h->logct;
+    sweep_bucket = &cnt.sweeps_sk;
+    // line 1: v <- log c~ - LSE_c(u 1^T - gamma C)   (column fix)
+    col_lse(u, nullptr, v, nullptr, 0.0, logct, v, 1, SC_AUX0, 0.0);
+    // line 2: log r(P) <- u + LSE_r(1 v^T - gamma C)
+    row_lse(u, v, logrt, h->logrP, h->rowmax, rt);
+    const double* s = read();
+    double gl1 = s[SC_GL1], chi2 = s[SC_CHI2];
+    if (trace) std::fprintf(stderr, "[eot] stage start gamma %.6g grad %.4e chi2 %.4e eps %.4e\n", gamma_host, gl1, chi2, eps);
+    *delta_min = INFINITY;
+    int steps = 0;
+    bool ok = true;
+    const double eps_chi = std::pow(eps, 0.4);
+    while (gl1 > eps) {
+      ctx = " (gamma " + std::to_string(gamma_host) + ", Newton step " + std::to_string(steps) +
+            ", ||grad g||_1 " + std::to_string(gl1) + ", eps " + std::to_string(eps) + ")";
+      if (steps >= prm.max_newton) {
+        ok = false;
+        break;
+      }
+      // Alg. 3 (ChiSinkhorn): while chi^2(r~ | r(P)) > eps^(2/5)
+      sweep_bucket = &cnt.sweeps_sk;
+      int sk = 0;
+      while (chi2 > eps_chi) {
+        axpy(n, u, 1.0, logrt, 1.0, h->logrP, -1.0);  // u <- u + log r~ - log r(P)
+        col_lse(u, nullptr, v, nullptr, 0.0, logct, v, 1, SC_AUX0, 0.0);
+        row_lse(u, v, logrt, h->logrP, h->rowmax, rt);
+        s = read();
+        gl1 = s[SC_GL1];
+        chi2 = s[SC_CHI2];
+        cnt.sk_iters++;
+        if (++sk > 2000) throw EotError{EOT_ERR_MAXNEWTON, "ChiSinkhorn did not converge"};
+      }
+      if (gl1 <= eps) break;
+      // line 5: forcing parameter
+      const double eta = std::fmax(gl1, 0.8 * eps / gl1);
+      // line 6-7: NewtonSolve and d_v = -P_c d_u
+      bool ran;
+      const double rho0 = std::fmax(0.0, 1.0 - 4.0 * (1.0 - cnt.rho_last));
+      const double rho = newton(u, v, rt, gl1, eta, rho0, max_cg, mode, &ran);
+      if (ran) cnt.rho_last = rho;
+      cnt.newton_steps++;
+      // lines 8-13: backtracking on the simplified Armijo test
+      sweep_bucket = &cnt.sweeps_ls;
+      double alpha = 1.0;
+      int trials = 0;
+      for (;;) {
+        col_lse(u, h->du, v, h->dv, alpha, logct, h->logcP, 0, SC_LHS, 1.0);
+        // A trial point outside the split range (|u + a d_u| >= 2^19) has a plan
+        // whose mass overflows, so it fails the Armijo test: reject it.
+        EOT_CUDA(cudaMemcpyAsync(h->h_status, h->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+        EOT_CUDA(cudaStreamSynchronize(st));
+        const bool out_of_range = (*h->h_status & kStatRange) != 0;
+        if (out_of_range) clear_status();
+        s = read();
+        cnt.ls_trials++;
+        if (!out_of_range && s[SC_LHS] <= 0.99 * alpha * s[SC_SLOPE]) break;
+        if (++trials > prm.max_ls) throw EotError{EOT_ERR_LINESEARCH, "Armijo backtracking exhausted"};
+        alpha *= 0.5;
+      }
+      // lines 14-15: u += a d_u; v += a d_v + log c~ - log c(P(a))
+      axpy(n, u, 1.0, h->du, alpha);
+      axpy(m, v, 1.0, h->dv, alpha, logct, 1.0, h->logcP, -1.0);
+      // line 16: log r(P)
+      sweep_bucket = &cnt.sweeps_ls;
+      row_lse(u, v, logrt, h->logrP, h->rowmax, rt);
+      s = read();
+      const double new_gl1 = s[SC_GL1];
+      chi2 = s[SC_CHI2];
+      const double delta = (gl1 - new_gl1) / ((1.0 - eta) * gl1);
+      if (trace)
+        std::fprintf(stderr, "[eot] gamma %.6g step %d grad %.3e -> %.3e eta %.3e alpha %.4g rho %.9f cg %lld curv %lld sk %lld\n",
+                     gamma_host, steps, gl1, new_gl1, eta, alpha, cnt.rho_last, (long long)cnt.cg_iters,
+                     (long long)cnt.curvature_stops, (long long)cnt.sk_iters);
+      if (delta < *delta_min) *delta_min = delta;
+      gl1 = new_gl1;
+      steps++;
+    }
+    // line 18: u <- u + log r~ - log r(P)
+    axpy(n, u, 1.0, logrt, 1.0, h->logrP, -1.0);
+    *gl1_out = gl1;
+    return ok;
+  }
+};
+
+// ---------------- entry points (instantiated for float and double) ----------------
+template <class T>
+void run_marginals(eot_handle h, const eot_problem* P, const double* u, const double* v,
+                   double gamma, double* r_out, double* c_out, double* lr_out, double* lc_out,
+                   double* total_out, cudaStream_t st);
+template <class T>
+void run_hvp(eot_handle h, const eot_problem* P, const double* u, const double* v, double gamma,
+             double s, const double* du, const double* dv, double* ou, double* ov, double* r_out,
+             double* c_out, cudaStream_t st);
+template <class T>
+void run_newton(eot_handle h, const eot_problem* P, const double* u, const double* v,
+                double gamma, const double* rtarget, double eta, double rho0, int max_cg,
+                double* du_out, double* dv_out, double* rho_out, int* iters_out, cudaStream_t st);
+template <class T>
+void run_solve(eot_handle h, const eot_problem* P, const eot_params* prm, double* u, double* v,
+               eot_stats* stats, cudaStream_t st);
+template <class T>
+double run_sweep_bench(eot_handle h, const eot_problem* P, const double* u, const double* v,
+                       double gamma, int kind, int iters, cudaStream_t st);
+template <class T>
+void run_backward_dense(eot_handle h, const eot_problem* P, const double* u, const double* v,
+                        double gamma, double scale, float* dC, cudaStream_t st);
+
+}  // namespace eot

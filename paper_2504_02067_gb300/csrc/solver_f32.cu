@@ -1,0 +1,18 @@
+// Explicit instantiation of the solver entry points for the float element type.
+#include "solver_impl.cuh"
+
+namespace eot {
+template void run_marginals<float>(eot_handle, const eot_problem*, const double*, const double*, double,
+                                   double*, double*, double*, double*, double*, cudaStream_t);
+template void run_hvp<float>(eot_handle, const eot_problem*, const double*, const double*, double, double,
+                             const double*, const double*, double*, double*, double*, double*, cudaStream_t);
+template void run_newton<float>(eot_handle, const eot_problem*, const double*, const double*, double,
+                                const double*, double, double, int, double*, double*, double*, int*,
+                                cudaStream_t);
+template void run_solve<float>(eot_handle, const eot_problem*, const eot_params*, double*, double*,
+                               eot_stats*, cudaStream_t);
+template void run_backward_dense<float>(eot_handle, const eot_problem*, const double*, const double*,
+                                        double, double, float*, cudaStream_t);
+template double run_sweep_bench<float>(eot_handle, const eot_problem*, const double*, const double*,
+                                      double, int, int, cudaStream_t);
+}  // namespace eot

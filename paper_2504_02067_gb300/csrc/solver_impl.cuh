@@ -1,0 +1,278 @@
+// Definitions of the entry points declared in solver.cuh, instantiated for the
+// FP32 (mixed / plain) and FP64 element types in solver_f32.cu / solver_f64.cu.
+#pragma once
+#include <algorithm>
+
+#include "solver.cuh"
+
+namespace eot {
+
+inline double wall_now() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+template <class T>
+double round_gamma(double g) {
+  // Reading of the paper (Sec. 4 uses FP64 only): the FP32 paths run every
+  // temperature rounded to FP32, so that gamma * C_ij is an exact product in
+  // the FMA; the FP64 path uses gamma as given.
+  return sizeof(T) == 4 ? (double)(float)g : g;
+}
+
+template <class T>
+void run_marginals(eot_handle h, const eot_problem* P, const double* u, const double* v,
+                   double gamma, double* r_out, double* c_out, double* lr_out, double* lc_out,
+                   double* total_out, cudaStream_t st) {
+  Solver<T> S(h, P, st);
+  EOT_CUDA(cudaMemsetAsync(h->status, 0, sizeof(int), st));
+  S.set_scalar(SC_GAMMA, round_gamma<T>(gamma));
+  double* lr = lr_out ? lr_out : h->logrP;
+  double* lc = lc_out ? lc_out : h->logcP;
+  S.row_lse(u, v, nullptr, lr, nullptr, nullptr, SC_MASS, SC_AUX1);
+  S.col_lse(u, nullptr, v, nullptr, 0.0, nullptr, lc, 0, SC_AUX0, 0.0);
+  if (r_out) {
+    exp_kernel<<<S.vg_n, kThreads, 0, st>>>(P->n, lr, r_out);
+    h->launches++;
+  }
+  if (c_out) {
+    exp_kernel<<<S.vg_m, kThreads, 0, st>>>(P->m, lc, c_out);
+    h->launches++;
+  }
+  EOT_LAUNCH_CHECK();
+  if (total_out)
+    EOT_CUDA(cudaMemcpyAsync(total_out, h->sc + SC_MASS, sizeof(double), cudaMemcpyDeviceToDevice, st));
+  S.read();
+}
+
+template <class T>
+void run_hvp(eot_handle h, const eot_problem* P, const double* u, const double* v, double gamma,
+             double s, const double* du, const double* dv, double* ou, double* ov, double* r_out,
+             double* c_out, cudaStream_t st) {
+  Solver<T> S(h, P, st);
+  EOT_CUDA(cudaMemsetAsync(h->status, 0, sizeof(int), st));
+  S.set_scalar(SC_GAMMA, round_gamma<T>(gamma));
+  // row maxima for the factorisation P = rowfac * colfac * E
+  S.row_lse(u, v, nullptr, h->logrP, h->rowmax, nullptr, SC_AUX0, SC_AUX1);
+  S.split_rows(u, nullptr, 0.0, h->rowmax, h->Al, nullptr, h->rowfac, h->rowmax);
+  S.split_cols(v, nullptr, 0.0, nullptr, h->Bl, nullptr, h->colfac, nullptr);
+  weight_kernel<T><<<S.vg_n, kThreads, 0, st>>>(P->n, h->rowfac, nullptr, S.xw0());
+  weight_kernel<T><<<S.vg_n, kThreads, 0, st>>>(P->n, h->rowfac, du, S.xw1());
+  weight_kernel<T><<<S.vg_m, kThreads, 0, st>>>(P->m, h->colfac, nullptr, S.zf());
+  weight_kernel<T><<<S.vg_m, kThreads, 0, st>>>(P->m, h->colfac, dv, S.wsq());
+  EOT_LAUNCH_CHECK();
+  h->launches += 4;
+  ensure_rowpart(h, P->n, S.geo.S);
+  SweepArgs<T> a = S.args();
+  a.wr[0] = S.xw0();
+  a.wr[1] = S.xw1();
+  a.wc[0] = S.zf();
+  a.wc[1] = S.wsq();
+  HvpEpi e{h->rowfac, h->colfac, du, dv, s, ou, ov, r_out, c_out};
+  S.template col<2, false, 2>(a, e);
+  S.read();
+}
+
+template <class T>
+void run_newton(eot_handle h, const eot_problem* P, const double* u, const double* v,
+                double gamma, const double* rtarget, double eta, double rho0, int max_cg,
+                double* du_out, double* dv_out, double* rho_out, int* iters_out, cudaStream_t st) {
+  Solver<T> S(h, P, st);
+  EOT_CUDA(cudaMemsetAsync(h->status, 0, sizeof(int), st));
+  S.set_scalar(SC_GAMMA, round_gamma<T>(gamma));
+  S.row_lse(u, v, nullptr, h->logrP, h->rowmax, rtarget);
+  const double gl1 = S.read()[SC_GL1];
+  if (max_cg <= 0) max_cg = (int)std::min<int64_t>(4 * P->n, 2000);
+  bool ran = false;
+  const double rho = S.newton(u, v, rtarget, gl1, eta, rho0, max_cg, cg_mode_from_env(), &ran);
+  S.copy(du_out, h->du, P->n);
+  if (dv_out) S.copy(dv_out, h->dv, P->m);
+  S.read();
+  if (rho_out) *rho_out = rho;
+  if (iters_out) *iters_out = (int)S.cnt.cg_iters;
+}
+
+template <class T>
+void run_solve(eot_handle h, const eot_problem* P, const eot_params* prm_in, double* u, double* v,
+               eot_stats* stats, cudaStream_t st) {
+  const double t0 = wall_now();
+  const eot_params prm = *prm_in;
+  Solver<T> S(h, P, st);
+  const int64_t n = P->n, m = P->m;
+  const int max_cg = prm.max_cg > 0 ? prm.max_cg : (int)std::min<int64_t>(4 * n, 2000);
+  const CgMode mode = cg_mode_from_env();
+  EOT_CUDA(cudaMemsetAsync(h->status, 0, sizeof(int), st));
+
+  // H(r), H(c) and the masses (Alg. 1 line 4 needs min(H(r), H(c)))
+  vec_stats_kernel<<<S.vg_n, kThreads, 0, st>>>(n, P->r, nullptr, 0, h->sc, SC_AUX0, SC_AUX1,
+                                                 h->dotpart, h->cnt_dot, h->status);
+  EOT_LAUNCH_CHECK();
+  EOT_CUDA(cudaMemcpyAsync(h->h_sc + SC_COUNT - 2, h->sc + SC_AUX0, 2 * sizeof(double),
+                           cudaMemcpyDeviceToHost, st));
+  EOT_CUDA(cudaStreamSynchronize(st));
+  const double Hr = -h->h_sc[SC_COUNT - 2], mr = h->h_sc[SC_COUNT - 1];
+  vec_stats_kernel<<<S.vg_m, kThreads, 0, st>>>(m, P->c, nullptr, 0, h->sc, SC_AUX0, SC_AUX1,
+                                                 h->dotpart, h->cnt_dot, h->status);
+  EOT_LAUNCH_CHECK();
+  h->launches += 2;
+  EOT_CUDA(cudaMemcpyAsync(h->h_sc + SC_COUNT - 2, h->sc + SC_AUX0, 2 * sizeof(double),
+                           cudaMemcpyDeviceToHost, st));
+  EOT_CUDA(cudaMemcpyAsync(h->h_status, h->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  EOT_CUDA(cudaStreamSynchronize(st));
+  const double Hc = -h->h_sc[SC_COUNT - 2], mc = h->h_sc[SC_COUNT - 1];
+  if (*h->h_status != 0 || std::fabs(mr - 1.0) > 1e-6 || std::fabs(mc - 1.0) > 1e-6)
+    throw EotError{EOT_ERR_INVALID_ARG, "r and c must be finite, non-negative and sum to 1"};
+  const double H = std::min(Hr, Hc);
+
+  // Alg. 1
+  const double gamma_f = round_gamma<T>(prm.gamma_f);
+  double gamma = round_gamma<T>(std::min(prm.gamma_i, prm.gamma_f));
+  double gamma_prev = 0.0, q = prm.q1, gl1 = 0.0;
+  const double w_c = 0.5 - prm.w_r;
+  int t = 1;
+  for (;;) {
+    const bool done = gamma == gamma_f;
+    double eps_d = H / std::pow(gamma, prm.p);
+    if (done) eps_d = std::min(eps_d, 2.0 * prm.tol_final / 3.0);
+    smooth_kernel<<<S.vg_n, kThreads, 0, st>>>(n, P->r, prm.w_r * eps_d, h->rt, h->logrt);
+    smooth_kernel<<<S.vg_m, kThreads, 0, st>>>(m, P->c, w_c * eps_d, h->ct, h->logct);
+    EOT_LAUNCH_CHECK();
+    h->launches += 2;
+    if (t == 1) {
+      S.copy(u, h->logrt, n);
+      S.copy(v, h->logct, m);
+      S.copy(h->nt0, h->logrt, n);
+      S.copy(h->mt0, h->logct, m);
+    }
+    S.set_scalar(SC_GAMMA, gamma);
+    double dmin = INFINITY;
+    if (!S.project(u, v, eps_d / 2.0, prm, max_cg, mode, &dmin, &gl1))
+      throw EotError{EOT_ERR_MAXNEWTON, "TruncatedNewtonProject exceeded max_newton"};
+    // AdjustSchedule (Sec. 3.3); a stage without Newton steps has delta_min = +inf
+    if (dmin > 0.95) q = std::min(2.0, q * q);
+    else if (dmin < 0.8) q = std::sqrt(q);
+    const double gamma_next = round_gamma<T>(std::min(q * gamma, gamma_f));
+    if (done) break;
+    if (t >= prm.max_stages) throw EotError{EOT_ERR_MAXSTAGES, "gamma_f not reached within max_stages"};
+    // Alg. 1 line 10: z <- z + ratio (z - z_prev), z_prev <- z
+    const double ratio = (gamma_next - gamma) / (gamma - gamma_prev);
+    S.copy(h->nt1, u, n);
+    S.axpy(n, u, 1.0 + ratio, h->nt0, -ratio);
+    std::swap(h->nt0, h->nt1);
+    S.copy(h->mt1, v, m);
+    S.axpy(m, v, 1.0 + ratio, h->mt0, -ratio);
+    std::swap(h->mt0, h->mt1);
+    gamma_prev = gamma;
+    gamma = gamma_next;
+    ++t;
+  }
+
+  // marginal L1 error of the output against the unsmoothed r, c
+  S.sweep_bucket = &S.cnt.sweeps_other;
+  S.row_lse(u, v, nullptr, h->logrP, nullptr, P->r, SC_GL1, SC_CHI2);
+  S.col_lse(u, nullptr, v, nullptr, 0.0, nullptr, h->logcP, 0, SC_AUX0, 0.0);
+  exp_kernel<<<S.vg_m, kThreads, 0, st>>>(m, h->logcP, h->mt1);
+  vec_stats_kernel<<<S.vg_m, kThreads, 0, st>>>(m, h->mt1, P->c, 1, h->sc, SC_AUX1, -1,
+                                                 h->dotpart, h->cnt_dot, h->status);
+  EOT_LAUNCH_CHECK();
+  h->launches += 2;
+  const double* s = S.read();
+  if (stats) {
+    const SolveCounters& c = S.cnt;
+    stats->sweeps_cg = c.sweeps_cg;
+    stats->sweeps_newton = c.sweeps_newton;
+    stats->sweeps_linesearch = c.sweeps_ls;
+    stats->sweeps_sinkhorn = c.sweeps_sk;
+    stats->sweeps_total = c.sweeps_cg + c.sweeps_newton + c.sweeps_ls + c.sweeps_sk + c.sweeps_other;
+    stats->stages = t;
+    stats->newton_steps = (int32_t)c.newton_steps;
+    stats->cg_iters = (int32_t)c.cg_iters;
+    stats->cg_solves = (int32_t)c.cg_solves;
+    stats->ls_trials = (int32_t)c.ls_trials;
+    stats->sinkhorn_iters = (int32_t)c.sk_iters;
+    stats->curvature_stops = (int32_t)c.curvature_stops;
+    stats->final_gamma = gamma;
+    stats->final_rho = c.rho_last;
+    stats->grad_l1 = gl1;
+    stats->marg_err_l1 = s[SC_GL1] + s[SC_AUX1];
+    stats->seconds = wall_now() - t0;
+  }
+}
+
+template <class T>
+double run_sweep_bench(eot_handle h, const eot_problem* P, const double* u, const double* v,
+                       double gamma, int kind, int iters, cudaStream_t st) {
+  Solver<T> S(h, P, st);
+  EOT_CUDA(cudaMemsetAsync(h->status, 0, sizeof(int), st));
+  S.set_scalar(SC_GAMMA, round_gamma<T>(gamma));
+  // untimed set-up: the Newton-step factorisation and a CG start at rho = 1/2
+  S.row_lse(u, v, nullptr, h->logrP, h->rowmax, nullptr, SC_AUX0, SC_AUX1);
+  exp_kernel<<<S.vg_n, kThreads, 0, st>>>(P->n, h->logrP, h->rt);  // r~ := r(P) (any finite target)
+  EOT_LAUNCH_CHECK();
+  bool ran = false;
+  S.newton(u, v, h->rt, 1.0, 1e300, 0.0, 1, CgMode::kHost, &ran);
+  S.set_scalar(SC_RHO, 0.5);
+  S.set_scalar(SC_TOL, -1.0);
+  S.set_scalar(SC_MAXIT, 1e6);
+  // a positive direction p = rowfac (so <p, F_r p> > 0) and its column-sweep weights
+  weight_kernel<double><<<S.vg_n, kThreads, 0, st>>>(P->n, h->rowfac, nullptr, h->p);
+  weight_kernel<T><<<S.vg_n, kThreads, 0, st>>>(P->n, h->rowfac, h->p, S.xw0());
+  S.set_scalar(SC_RZ, 1.0);
+  EOT_LAUNCH_CHECK();
+  if (kind == 2) {
+    weight_kernel<T><<<S.vg_n, kThreads, 0, st>>>(P->n, h->rowfac, nullptr, S.xw1());
+    weight_kernel<T><<<S.vg_m, kThreads, 0, st>>>(P->m, h->colfac, nullptr, S.wsq());
+    ensure_rowpart(h, P->n, S.geo.S);
+  }
+  cudaEvent_t e0, e1;
+  EOT_CUDA(cudaEventCreate(&e0));
+  EOT_CUDA(cudaEventCreate(&e1));
+  SweepArgs<T> a = S.args();
+  EOT_CUDA(cudaEventRecord(e0, st));
+  for (int k = 0; k < iters; ++k) {
+    if (kind == 0) {
+      a.wr[0] = S.xw0();
+      S.template col<1, false, 0>(a, CgColEpi<T>{h->colfac, h->cP, S.zf()});
+    } else if (kind == 1) {
+      a.wc[0] = S.zf();
+      S.template row<1, false, 0>(a, CgRowEpi{h->rowfac, h->rPs, h->p, h->y, h->q, h->sc, h->status});
+    } else if (kind == 2) {
+      a.wr[0] = S.xw0();
+      a.wr[1] = S.xw1();
+      a.wc[0] = S.zf();
+      a.wc[1] = S.wsq();
+      S.template col<2, false, 2>(a, HvpEpi{h->rowfac, h->colfac, h->x, h->dv, 1.0, h->y, h->mt1, nullptr, nullptr});
+    } else {
+      a.wc[0] = S.ewc();
+      S.template row<1, true, 0>(a, RowLseEpi{nullptr, h->Al, h->y, nullptr, nullptr, h->sc, SC_AUX0, SC_AUX1});
+    }
+  }
+  EOT_CUDA(cudaEventRecord(e1, st));
+  EOT_CUDA(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  EOT_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  S.read();
+  return (double)ms / (iters > 0 ? iters : 1);
+}
+
+template <class T>
+void run_backward_dense(eot_handle h, const eot_problem* P, const double* u, const double* v,
+                        double gamma, double scale, float* dC, cudaStream_t st) {
+  Solver<T> S(h, P, st);
+  EOT_CUDA(cudaMemsetAsync(h->status, 0, sizeof(int), st));
+  S.set_scalar(SC_GAMMA, round_gamma<T>(gamma));
+  S.row_lse(u, v, nullptr, h->logrP, h->rowmax, nullptr, SC_AUX0, SC_AUX1);
+  S.split_rows(u, nullptr, 0.0, h->rowmax, h->Al, nullptr, h->rowfac, h->rowmax);
+  S.split_cols(v, nullptr, 0.0, nullptr, h->Bl, nullptr, h->colfac, nullptr);
+  int64_t blocks = (P->n * P->m + kThreads - 1) / kThreads;
+  if (blocks > 16 * (int64_t)h->sms * 8) blocks = 16 * (int64_t)h->sms * 8;
+  plan_dense_kernel<T><<<(unsigned)blocks, kThreads, 0, st>>>(P->n, P->m, S.C, P->ldc, S.Ah(), S.Bh(),
+                                                              h->sc + SC_GAMMA, h->rowfac, h->colfac,
+                                                              scale, dC, P->m);
+  EOT_LAUNCH_CHECK();
+  h->launches++;
+  S.read();
+}
+
+}  // namespace eot

@@ -1,0 +1,202 @@
+"""GPU parity of the dense-cost path against the FP64 oracle, through the C ABI.
+
+Tolerances (the benchmark spec): marginal L1 <= 1e-6, relative transport cost <= 1e-6;
+the FP64 path is held to ~1e-12 on single sweeps. Inputs are seeded and come
+from workloads/ or the oracle, never from the CUDA path."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import eot_oracle as O
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def H():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2504_02067_gb300 import Handle, build
+    build()
+    h = Handle(0, 64, 64)
+    yield h
+    h.close()
+
+
+def t(x, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(x)).to(device=DEV, dtype=dtype)
+
+
+def near_feasible(seed, n, m, gamma, C64):
+    """u, v with sum P = 1 and c(P) = c (oracle column fix), r, c Dirichlet."""
+    rng = np.random.default_rng(seed)
+    r = rng.dirichlet(np.ones(n)) * 0.999 + 0.001 / n
+    c = rng.dirichlet(np.ones(m)) * 0.999 + 0.001 / m
+    u = np.log(r) + rng.normal(0, 0.3, n) + 5.0 * gamma / 4096
+    v = np.log(c) - O.lse_c(u[:, None] - gamma * C64)
+    return u, v, r, c
+
+
+SIZES = [(1, 1), (7, 5), (31, 129), (128, 128), (300, 517), (784, 784), (1000, 1024)]
+
+
+def make_dense(seed, n, m, f32):
+    rng = np.random.default_rng(seed)
+    C = rng.uniform(0, 1, size=(n, m))
+    if f32:
+        C = C.astype(np.float32)
+    return C
+
+
+@pytest.mark.parametrize("n,m", SIZES)
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_marginals(H, n, m, prec):
+    from paper_2504_02067_gb300 import Problem
+    f32 = prec == "mixed"
+    C = make_dense(n * 7 + m, n, m, f32)
+    gamma = float(np.float32(2.0 ** 10)) if f32 else 2.0 ** 10
+    C64 = C.astype(np.float64)
+    u, v, _, _ = near_feasible(n + m, n, m, gamma, C64)
+    prob = Problem(t(C, torch.float32 if f32 else torch.float64), precision=prec)
+    r, c, lr, lc, tot = H.marginals(prob, t(u), t(v), gamma)
+    P = O.plan(u, v, gamma, C64)
+    rr, cr = O.row_sum(P), O.col_sum(P)
+    er = np.abs(r.cpu().numpy() - rr).sum()
+    ec = np.abs(c.cpu().numpy() - cr).sum()
+    tol = 1e-6 if f32 else 1e-12
+    assert er <= tol and ec <= tol, (er, ec)
+    np.testing.assert_allclose(lr.cpu().numpy(), np.log(rr), atol=50 * tol)
+    assert abs(tot.item() - P.sum()) <= tol
+
+
+@pytest.mark.parametrize("n,m", [(7, 5), (128, 128), (300, 517), (1000, 1024)])
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_hvp_and_null_vector(H, n, m, prec):
+    from paper_2504_02067_gb300 import Problem
+    f32 = prec == "mixed"
+    C = make_dense(3 * n + m, n, m, f32)
+    C64 = C.astype(np.float64)
+    gamma = float(np.float32(2.0 ** 12)) if f32 else 2.0 ** 12
+    u, v, _, _ = near_feasible(n * m, n, m, gamma, C64)
+    rng = np.random.default_rng(5)
+    du, dv = rng.normal(size=n), rng.normal(size=m)
+    prob = Problem(t(C, torch.float32 if f32 else torch.float64), precision=prec)
+    tol = 1e-6 if f32 else 1e-12
+    for s in (1.0, math.sqrt(0.75)):
+        ou, ov, r, c = H.hvp(prob, t(u), t(v), gamma, s, t(du), t(dv))
+        ru, rv, rr, cr = O.hvp(u, v, gamma, C64, du, dv, s)
+        ref = np.concatenate([ru, rv])
+        got = np.concatenate([ou.cpu().numpy(), ov.cpu().numpy()])
+        assert np.abs(got - ref).sum() <= tol * np.abs(ref).sum(), np.abs(got - ref).sum()
+        assert np.abs(r.cpu().numpy() - rr).sum() <= tol
+    # K1: the Hessian (s = 1) annihilates (1, -1)  (Sec. 2.1 footnote)
+    ou, ov, r, c = H.hvp(prob, t(u), t(v), gamma, 1.0, t(np.ones(n)), t(-np.ones(m)))
+    assert (ou.abs().sum() + ov.abs().sum()).item() <= 2 * tol
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_newton_solve_matches_oracle(H, prec):
+    """Alg. 2 on the GPU vs the oracle at the same (u, v): same rho sequence end,
+    CG iteration count within one, direction within tolerance."""
+    from paper_2504_02067_gb300 import Problem
+    f32 = prec == "mixed"
+    n = m = 256
+    rng = np.random.default_rng(11)
+    C = rng.uniform(0, 1, size=(n, m))
+    if f32:
+        C = C.astype(np.float32)
+    C64 = C.astype(np.float64)
+    gamma = 64.0
+    u, v, r, c = near_feasible(12, n, m, gamma, C64)
+    P = O.plan(u, v, gamma, C64)
+    rP = O.row_sum(P)
+    rt = rP * (1 + 0.02 * rng.normal(size=n))
+    rt /= rt.sum()
+    gu = rP - rt
+    gl1 = np.abs(gu).sum()
+    eta = max(gl1, 0.8 * 1e-4 / gl1)
+    ref = O.newton_solve(P, gu, gl1, eta, 0.0)
+    prob = Problem(t(C, torch.float32 if f32 else torch.float64), precision=prec)
+    du, dv, rho, it = H.newton_solve(prob, t(u), t(v), gamma, t(rt), eta, 0.0)
+    du = du.cpu().numpy()
+    assert rho == pytest.approx(ref.rho)
+    assert abs(it - ref.cg_iters) <= 1 + ref.cg_solves
+    tol = 1e-5 if f32 else 1e-9
+    assert np.abs(du - ref.d_u).sum() <= tol * np.abs(ref.d_u).sum()
+    np.testing.assert_allclose(dv.cpu().numpy(), -(P.T @ ref.d_u) / O.col_sum(P),
+                               atol=tol * np.abs(ref.d_u).max())
+    # the forcing test of Alg. 2 holds for the GPU direction, checked in FP64
+    assert np.abs(O.F_r_apply(P, 1.0, du) + gu).sum() <= eta * gl1 * (1 + 1e-6)
+
+
+def test_solve_small_fp64_matches_oracle(H):
+    from paper_2504_02067_gb300 import Problem, default_params
+    rng = np.random.default_rng(21)
+    n, m = 60, 50
+    C = rng.uniform(0, 1, size=(n, m))
+    r, c = rng.dirichlet(np.ones(n)), rng.dirichlet(np.ones(m))
+    ref = O.mdot(C, r, c, gamma_i=16.0, gamma_f=1024.0, tol_final=1e-9)
+    prob = Problem(t(C), t(r), t(c))
+    u, v, st = H.solve(prob, default_params(gamma_i=16.0, gamma_f=1024.0, tol_final=1e-9))
+    u, v = u.cpu().numpy(), v.cpu().numpy()
+    assert O.marginal_l1_error(u, v, 1024.0, C, r, c) <= 1e-9
+    assert st["marg_err_l1"] <= 1e-9
+    c_gpu = O.transport_cost(u, v, 1024.0, C)
+    c_ref = O.transport_cost(ref.u, ref.v, 1024.0, C)
+    assert abs(c_gpu - c_ref) <= 1e-6 * c_ref
+    assert st["stages"] == ref.stages
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_solve_grid784_fp64(H, seed):
+    """28 x 28 grid, float64 cost, gamma_f = 2^12, to marginal L1 <= 1e-6 (oracle-checked)."""
+    from paper_2504_02067_gb300 import Problem, default_params
+    p = W.grid_problem_784(seed)
+    prob = Problem(t(p["C"]), t(p["r"]), t(p["c"]))
+    u, v, st = H.solve(prob, default_params(gamma_i=16.0, gamma_f=4096.0))
+    u, v = u.cpu().numpy(), v.cpu().numpy()
+    err = O.marginal_l1_error(u, v, 4096.0, p["C"], p["r"], p["c"])
+    assert err <= 1e-6, err
+    assert abs(st["marg_err_l1"] - err) <= 1e-9
+
+
+@pytest.mark.parametrize("kind", ["sqeuclid", "l1"])
+def test_solve_grid4096_mixed(H, kind):
+    """64 x 64 grid, float32 cost in HBM, gamma_f = 2^14, mixed precision, to marginal
+    L1 <= 1e-6 as evaluated by the FP64 oracle on the float32 cost."""
+    from paper_2504_02067_gb300 import Problem, default_params
+    p = W.grid_problem_4096(0, kind)
+    prob = Problem(t(p["C"], torch.float32), t(p["r"]), t(p["c"]))
+    u, v, st = H.solve(prob, default_params(gamma_i=16.0, gamma_f=16384.0))
+    u, v = u.cpu().numpy(), v.cpu().numpy()
+    g = float(np.float32(16384.0))
+    err = O.marginal_l1_error(u, v, g, p["C"].astype(np.float64), p["r"], p["c"])
+    assert err <= 1e-6, (err, st)
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+@pytest.mark.parametrize("kappa", [0.0, 700.0, -3.0e4, 2.0e5])
+def test_marginals_large_potentials_gauge(H, prec, kappa):
+    """Potentials of magnitude ~gamma from a zero-bin grid problem, shifted along the
+    gauge direction (u + k, v - k), which leaves P unchanged (Sec. 2.1 footnote):
+    the LSE sweeps must return the oracle's marginals of the unshifted point."""
+    from paper_2504_02067_gb300 import Problem
+    p = W.grid_problem_4096(3, "sqeuclid", side=32)
+    C = p["C"] if prec == "mixed" else p["C"].astype(np.float64)
+    C64 = C.astype(np.float64)
+    gamma = 4096.0
+    r, c = p["r"] * 0.999 + 0.001 / 1024, p["c"] * 0.999 + 0.001 / 1024
+    u, v = O.sinkhorn_log(C64, r, c, gamma, tol=1e-30, max_iter=25)
+    assert np.abs(u).max() > 100
+    P = O.plan(u, v, gamma, C64)
+    prob = Problem(t(C, torch.float32 if prec == "mixed" else torch.float64), precision=prec)
+    rr, cc, lr, lc, tot = H.marginals(prob, t(u + kappa), t(v - kappa), gamma)
+    tol = 1e-6 if prec == "mixed" else 1e-11
+    assert np.abs(rr.cpu().numpy() - O.row_sum(P)).sum() <= tol
+    assert np.abs(cc.cpu().numpy() - O.col_sum(P)).sum() <= tol
+    assert abs(tot.item() - P.sum()) <= tol
