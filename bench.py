@@ -377,6 +377,32 @@ def run_reference(args):
     return out
 
 
+def run_profile_sweep(args):
+    """A few launches of one sweep kernel on the full-size workload (for ncu):
+    the set-up launches come first (one row LSE, the Newton-step column and row
+    sweeps, the d_v column sweep), then `args.profile_iters` timed launches."""
+    import numpy as np
+    import torch
+
+    import paper_2504_02067_gb300 as E
+    import workloads as W
+
+    E.build()
+    dev = torch.device("cuda", 0)
+    p = W.grid_problem_4096(0, args.cost)
+    C = torch.from_numpy(p["C"]).to(dev)
+    r = torch.from_numpy(p["r"]).to(dev)
+    c = torch.from_numpy(p["c"]).to(dev)
+    h = E.Handle(0, N, N)
+    prob = E.Problem(C, r, c, precision="mixed")
+    rng = np.random.default_rng(0)
+    u = torch.from_numpy(np.log(p["r"] + 1e-6) + rng.normal(0, 1, N)).to(dev)
+    v = torch.from_numpy(np.log(p["c"] + 1e-6)).to(dev)
+    ms = h.eot_sweep_bench(prob, u, v, GAMMA_F, args.profile_sweep, args.profile_iters)
+    print(json.dumps({"kind": args.profile_sweep, "iters": args.profile_iters, "ms_per_launch": ms}))
+    h.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -387,7 +413,13 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--profile-sweep", type=int, default=-1,
+                    help="run only eot_sweep_bench of this kind (0 CG column, 1 CG row, 2 HVP, 3 row LSE)")
+    ap.add_argument("--profile-iters", type=int, default=3)
     args = ap.parse_args()
+    if args.profile_sweep >= 0:
+        run_profile_sweep(args)
+        return
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":

@@ -16,6 +16,7 @@ namespace eot {
 
 constexpr int kWarps = 8;            // warps per CTA of every sweep kernel
 constexpr int kThreads = kWarps * 32;
+constexpr int kColCtasPerSm = 2;     // resident column-sweep CTAs per SM (register bound)
 constexpr double kGrid = 0.125;      // split grid of the high parts
 constexpr double kSplitLimit = 524288.0;  // |A|, |B| < 2^19 keeps Ah + Bh exact in FP32
 constexpr float kLog2e = 1.4426950408889634f;
@@ -30,6 +31,13 @@ enum : int {
   kStatCurv = 8,        // CG: <p, F_r(rho) p> <= 0 or non-finite (loss of precision)
   kStatCgNan = 16       // CG: non-finite residual or preconditioned residual
 };
+
+// Programmatic dependent launch (sm_90+): a kernel launched with programmatic
+// stream serialisation may start while its predecessor drains. Everything that
+// reads data written by earlier kernels, or writes anything, comes after
+// pdl_wait(); only loads of the immutable cost matrix may precede it.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 __device__ __forceinline__ float ex2_approx(float x) {
   float y;
@@ -48,17 +56,31 @@ __device__ __forceinline__ double fmaT(double a, double b, double c) { return fm
 __device__ __forceinline__ float ceil_grid(float x) { return ceilf(x * 8.0f) * 0.125f; }
 __device__ __forceinline__ double ceil_grid(double x) { return ceil(x * 8.0) * 0.125; }
 
-// streaming 16-byte loads of the cost matrix that do not allocate in L1
-__device__ __forceinline__ void ld_stream(const float* p, float (&c)[4]) {
-  asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
-               : "=f"(c[0]), "=f"(c[1]), "=f"(c[2]), "=f"(c[3]) : "l"(p));
+// L2 policy for cost loads: with keep != 0 the cost's lines are marked
+// evict-last, so that a cost that fits in L2 stays resident across the many
+// sweeps of a solve (l2_demote_kernel resets the priority at the end).
+__device__ __forceinline__ uint64_t cost_policy(int keep) {
+  uint64_t pol;
+  if (keep) asm volatile("createpolicy.fractional.L2::evict_last.L2::evict_unchanged.b64 %0, 1.0;" : "=l"(pol));
+  else asm volatile("createpolicy.fractional.L2::evict_normal.L2::evict_unchanged.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
 }
-__device__ __forceinline__ void ld_stream(const double* p, double (&c)[2]) {
-  asm volatile("ld.global.nc.L1::no_allocate.v2.f64 {%0,%1}, [%2];"
-               : "=d"(c[0]), "=d"(c[1]) : "l"(p));
+
+// streaming 16-byte loads of the cost matrix: no L1 allocation, L2 policy `pol`
+__device__ __forceinline__ void ld_stream(const float* p, float (&c)[4], uint64_t pol) {
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.f32 {%0,%1,%2,%3}, [%4], %5;"
+               : "=f"(c[0]), "=f"(c[1]), "=f"(c[2]), "=f"(c[3]) : "l"(p), "l"(pol));
 }
-__device__ __forceinline__ void ld_stream(const float* p, float (&c)[1]) { c[0] = __ldg(p); }
-__device__ __forceinline__ void ld_stream(const double* p, double (&c)[1]) { c[0] = __ldg(p); }
+__device__ __forceinline__ void ld_stream(const double* p, double (&c)[2], uint64_t pol) {
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.f64 {%0,%1}, [%2], %3;"
+               : "=d"(c[0]), "=d"(c[1]) : "l"(p), "l"(pol));
+}
+__device__ __forceinline__ void ld_stream(const float* p, float (&c)[1], uint64_t pol) {
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(c[0]) : "l"(p), "l"(pol));
+}
+__device__ __forceinline__ void ld_stream(const double* p, double (&c)[1], uint64_t pol) {
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(c[0]) : "l"(p), "l"(pol));
+}
 
 // read-only vector loads of V consecutive elements (aligned when V > 1)
 template <int V, class T>
@@ -75,6 +97,31 @@ __device__ __forceinline__ void ld_vec(const T* p, T (&c)[V]) {
   }
 }
 
+// Compensated (Neumaier) accumulation s + c += x. In FP32 it keeps the running
+// sums of the sweeps accurate to about one rounding without FP64 instructions in
+// the inner loops (the FP64 pipe of this GPU is narrow); in FP64 it is a plain add.
+__device__ __forceinline__ void kadd(float& s, float& c, float x) {
+  const float t = s + x;
+  c += (fabsf(s) >= fabsf(x)) ? ((s - t) + x) : ((x - t) + s);
+  s = t;
+}
+__device__ __forceinline__ void kadd(double& s, double& c, double x) { s += x; }
+
+// V consecutive elements from shared memory (16-byte aligned when V > 1)
+template <int V, class T>
+__device__ __forceinline__ void ld_vec_smem(const T* p, T (&c)[V]) {
+  if constexpr (V == 4 && sizeof(T) == 4) {
+    const float4 x = *reinterpret_cast<const float4*>(p);
+    c[0] = x.x; c[1] = x.y; c[2] = x.z; c[3] = x.w;
+  } else if constexpr (V == 2 && sizeof(T) == 8) {
+    const double2 x = *reinterpret_cast<const double2*>(p);
+    c[0] = x.x; c[1] = x.y;
+  } else {
+#pragma unroll
+    for (int e = 0; e < V; ++e) c[e] = p[e];
+  }
+}
+
 __device__ __forceinline__ double warp_sum(double x) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
@@ -85,19 +132,33 @@ __device__ __forceinline__ double warp_sum(double x) {
 struct LsePair {
   double m, s;
 };
+// Combine two pairs. The scaling factor exp(m - M) is formed in the element type
+// T: one FP32 rounding is far below the FP32 path's own error, and it keeps the
+// FP64 pipe free; the FP64 path scales in FP64.
+template <class T = double>
 __device__ __forceinline__ LsePair lse_combine(LsePair a, LsePair b) {
   if (b.s == 0.0) return a;
   if (a.s == 0.0) return b;
-  double M = fmax(a.m, b.m);
-  return {M, a.s * exp(a.m - M) + b.s * exp(b.m - M)};
+  const double M = fmax(a.m, b.m);
+  return {M, a.s * (double)expT((T)(a.m - M)) + b.s * (double)expT((T)(b.m - M))};
 }
+template <class T = double>
 __device__ __forceinline__ LsePair warp_lse(LsePair p) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     LsePair q{__shfl_xor_sync(0xffffffffu, p.m, o), __shfl_xor_sync(0xffffffffu, p.s, o)};
-    p = lse_combine(p, q);
+    p = lse_combine<T>(p, q);
   }
   return p;
 }
+
+__device__ __forceinline__ float warp_sum_f(float x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+// warp sum in the element type (FP32 path: FP32 shuffles and adds)
+__device__ __forceinline__ double warp_sum_t(float x) { return (double)warp_sum_f(x); }
+__device__ __forceinline__ double warp_sum_t(double x) { return warp_sum(x); }
 
 }  // namespace eot

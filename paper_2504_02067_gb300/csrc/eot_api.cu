@@ -36,7 +36,7 @@ void ensure_capacity(eot_handle h, int64_t n, int64_t m) {
   free_all(h);
   const int64_t L = std::max(N, Mm);
   h->max_strips = (Mm + 31) / 32 + 1;
-  h->dot_slots = std::max<int64_t>(std::max<int64_t>(4096, h->max_strips), kVecCtas);
+  h->dot_slots = std::max<int64_t>(std::max<int64_t>((N + kWarps - 1) / kWarps + 1, h->max_strips), kVecCtas);
   EOT_CUDA(cudaHostAlloc((void**)&h->h_sc, (SC_COUNT + 1) * sizeof(double), cudaHostAllocDefault));
   EOT_CUDA(cudaHostAlloc((void**)&h->h_status, sizeof(int), cudaHostAllocDefault));
   h->sc = (double*)dev_alloc(h, SC_COUNT * sizeof(double));
@@ -154,6 +154,9 @@ eot_status eot_create(eot_handle* out, int device, int64_t max_n, int64_t max_m)
   try {
     EOT_CUDA(cudaSetDevice(device));
     EOT_CUDA(cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, device));
+    int l2 = 0;
+    EOT_CUDA(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, device));
+    h->l2_bytes = l2;
     ensure_capacity(h, max_n, max_m);
   } catch (const EotError& e) {
     free_all(h);
@@ -286,11 +289,11 @@ eot_status eot_backward(eot_handle h, const eot_problem* prob, const double* u, 
     }
     const double a = grad_scale / gamma;
     if (dr) {
-      axpy4_kernel<<<vec_grid(prob->n), kThreads, 0, st>>>(prob->n, dr, 0.0, u, a, nullptr, 0.0, nullptr, 0.0);
+      launch_k(axpy4_kernel, dim3(vec_grid(prob->n)), dim3(kThreads), st, prob->n, dr, 0.0, u, a, nullptr, 0.0, nullptr, 0.0);
       h->launches++;
     }
     if (dc) {
-      axpy4_kernel<<<vec_grid(prob->m), kThreads, 0, st>>>(prob->m, dc, 0.0, v, a, nullptr, 0.0, nullptr, 0.0);
+      launch_k(axpy4_kernel, dim3(vec_grid(prob->m)), dim3(kThreads), st, prob->m, dc, 0.0, v, a, nullptr, 0.0, nullptr, 0.0);
       h->launches++;
     }
     EOT_LAUNCH_CHECK();

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 
 #include <cstdio>
+#include <cstdlib>
+#include <utility>
 #include <map>
 #include <string>
 #include <tuple>
@@ -42,6 +44,7 @@ struct CgGraph {
 struct eot_handle_s {
   int device = 0;
   int sms = 152;
+  int64_t l2_bytes = 0;
   int64_t cap_n = 0, cap_m = 0, cap_rowpart = 0;
   std::string err = "no error";
   int64_t launches = 0;
@@ -75,6 +78,34 @@ struct eot_handle_s {
 
 namespace eot {
 
+// Kernel launch with programmatic stream serialisation (PDL): the kernel may
+// begin while its predecessor in the stream drains; every kernel of this
+// library calls pdl_wait() before touching data of earlier kernels.
+// EOT_PDL=0 in the environment turns the attribute off.
+inline bool pdl_enabled() {
+  static const bool on = [] {
+    const char* e = std::getenv("EOT_PDL");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
+template <typename... KArgs, typename... Args>
+inline void launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t st, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl_enabled() ? 1 : 0;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+  if (e != cudaSuccess)
+    throw EotError{EOT_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e)};
+}
+
 inline void* dev_alloc(eot_handle h, size_t bytes) {
   void* p = nullptr;
   EOT_CUDA(cudaMalloc(&p, bytes < 256 ? 256 : bytes));
@@ -94,8 +125,9 @@ struct ColGeo {
 inline ColGeo col_geo(eot_handle h, int64_t n, int64_t m, int V) {
   ColGeo g;
   g.S = (m + 32 * V - 1) / (32 * V);
-  const int64_t target = 4 * (int64_t)h->sms;
-  int64_t R = (target + g.S - 1) / g.S;
+  // one wave: S * R <= resident CTAs
+  const int64_t target = (int64_t)kColCtasPerSm * h->sms;
+  int64_t R = target / g.S;
   int64_t rmax = (n + 31) / 32;
   if (R > rmax) R = rmax;
   if (R > h->max_rowblk) R = h->max_rowblk;
@@ -106,9 +138,9 @@ inline ColGeo col_geo(eot_handle h, int64_t n, int64_t m, int V) {
   g.R = (int)((n + BR - 1) / BR);
   return g;
 }
+// one row per warp: ceil(n / 8) CTAs
 inline int row_grid(int64_t n) {
   int64_t g = (n + kWarps - 1) / kWarps;
-  if (g > 4096) g = 4096;
   return (int)(g < 1 ? 1 : g);
 }
 

@@ -60,6 +60,18 @@ struct Solver {
     sweep_bucket = &cnt.sweeps_other;
   }
 
+  // Keep the cost resident in L2 across the sweeps of one call when it fits in
+  // 60% of L2 (evict-last loads); release() demotes it again.
+  bool keep_l2 = false;
+  void retain_cost() { keep_l2 = (double)n * (double)ldc * sizeof(T) <= 0.6 * (double)h->l2_bytes; }
+  void release_cost() {
+    if (!keep_l2) return;
+    const int64_t bytes = n * ldc * (int64_t)sizeof(T);
+    launch_k(l2_demote_kernel, dim3(4 * h->sms), dim3(kThreads), st, (const char*)C, bytes);
+    h->launches++;
+    keep_l2 = false;
+  }
+
   T* Ah() { return (T*)h->Ah; }
   T* Bh() { return (T*)h->Bh; }
   T* xw0() { return (T*)h->xw0; }
@@ -88,13 +100,14 @@ struct Solver {
     a.nrowblk = geo.R;
     a.gamma_dev = h->sc + SC_GAMMA;
     a.active = nullptr;
+    a.keep_l2 = keep_l2 ? 1 : 0;
     return a;
   }
 
   double gamma_host = 0.0;
   void set_scalar(int slot, double v) {
     if (slot == SC_GAMMA) gamma_host = v;
-    set_scalar_kernel<<<1, 1, 0, st>>>(h->sc, slot, v);
+    launch_k(set_scalar_kernel, dim3(1), dim3(1), st, h->sc, slot, v);
     EOT_LAUNCH_CHECK();
     h->launches++;
   }
@@ -120,21 +133,21 @@ struct Solver {
   // ---------------- O(n) helpers ----------------
   void split_rows(const double* x, const double* y, double alpha, const double* z, double* l,
                   T* ew, double* fac, const double* fshift) {
-    split_kernel<T><<<vg_n, kThreads, 0, st>>>(n, x, y, alpha, z, plain ? 1 : 0, Ah(), l, ew, fac,
+    launch_k(split_kernel<T>, dim3(vg_n), dim3(kThreads), st, n, x, y, alpha, z, plain ? 1 : 0, Ah(), l, ew, fac,
                                                fshift, h->status);
     EOT_LAUNCH_CHECK();
     h->launches++;
   }
   void split_cols(const double* x, const double* y, double alpha, const double* z, double* l,
                   T* ew, double* fac, const double* fshift) {
-    split_kernel<T><<<vg_m, kThreads, 0, st>>>(m, x, y, alpha, z, plain ? 1 : 0, Bh(), l, ew, fac,
+    launch_k(split_kernel<T>, dim3(vg_m), dim3(kThreads), st, m, x, y, alpha, z, plain ? 1 : 0, Bh(), l, ew, fac,
                                                fshift, h->status);
     EOT_LAUNCH_CHECK();
     h->launches++;
   }
   void axpy(int64_t len, double* y, double b, const double* x, double a, const double* z = nullptr,
             double c = 0.0, const double* w = nullptr, double d = 0.0) {
-    axpy4_kernel<<<vec_grid(len), kThreads, 0, st>>>(len, y, b, x, a, z, c, w, d);
+    launch_k(axpy4_kernel, dim3(vec_grid(len)), dim3(kThreads), st, len, y, b, x, a, z, c, w, d);
     EOT_LAUNCH_CHECK();
     h->launches++;
   }
@@ -145,8 +158,8 @@ struct Solver {
   // ---------------- sweep launchers ----------------
   template <int NR, bool LSE, int SQM, class Epi>
   void row(const SweepArgs<T>& a, const Epi& e) {
-    if (V == VEC) row_sweep_kernel<T, VEC, NR, LSE, SQM, Epi><<<rg, kThreads, 0, st>>>(a, e);
-    else row_sweep_kernel<T, 1, NR, LSE, SQM, Epi><<<rg, kThreads, 0, st>>>(a, e);
+    if (V == VEC) launch_k(row_sweep_kernel<T, VEC, NR, LSE, SQM, Epi>, dim3(rg), dim3(kThreads), st, a, e);
+    else launch_k(row_sweep_kernel<T, 1, NR, LSE, SQM, Epi>, dim3(rg), dim3(kThreads), st, a, e);
     EOT_LAUNCH_CHECK();
     h->launches++;
     (*sweep_bucket)++;
@@ -154,8 +167,8 @@ struct Solver {
   template <int NC, bool LSE, int NR, class Epi>
   void col(const SweepArgs<T>& a, const Epi& e) {
     dim3 grid((unsigned)geo.S, (unsigned)geo.R);
-    if (V == VEC) col_sweep_kernel<T, VEC, NC, LSE, NR, Epi><<<grid, kThreads, 0, st>>>(a, e);
-    else col_sweep_kernel<T, 1, NC, LSE, NR, Epi><<<grid, kThreads, 0, st>>>(a, e);
+    if (V == VEC) launch_k(col_sweep_kernel<T, VEC, NC, LSE, NR, Epi>, dim3(grid), dim3(kThreads), st, a, e);
+    else launch_k(col_sweep_kernel<T, 1, NC, LSE, NR, Epi>, dim3(grid), dim3(kThreads), st, a, e);
     EOT_LAUNCH_CHECK();
     h->launches++;
     (*sweep_bucket)++;
@@ -196,7 +209,7 @@ struct Solver {
     // factorisation P = rowfac * colfac * E with row shift = running row max
     split_rows(u, nullptr, 0.0, h->rowmax, h->Al, nullptr, h->rowfac, h->rowmax);
     split_cols(v, nullptr, 0.0, nullptr, h->Bl, ewc(), h->colfac, nullptr);
-    prep_setup_kernel<T><<<vg_n, kThreads, 0, st>>>(n, h->logrP, rt, h->rowfac, h->rP, h->du0,
+    launch_k(prep_setup_kernel<T>, dim3(vg_n), dim3(kThreads), st, n, h->logrP, rt, h->rowfac, h->rP, h->du0,
                                                     xw0(), xw1());
     EOT_LAUNCH_CHECK();
     h->launches++;
@@ -226,7 +239,7 @@ struct Solver {
       for (int solve = 0;; ++solve) {
         set_scalar(SC_RHO, rho);
         run_cg(mode, max_cg, rt);
-        cg_check_kernel<<<vg_n, kThreads, 0, st>>>(n, h->res, h->Yx, h->sc, h->dotpart, h->cnt_dot);
+        launch_k(cg_check_kernel, dim3(vg_n), dim3(kThreads), st, n, h->res, h->Yx, h->sc, h->dotpart, h->cnt_dot);
         EOT_LAUNCH_CHECK();
         h->launches++;
         const double* s = read();
@@ -253,7 +266,7 @@ struct Solver {
     }
     if (du_final != h->du) copy(h->du, du_final, n);
     // d_v = -(P^T d_u) / c(P) and the Armijo slope <r~ - r(P), d_u>
-    prep_dv_kernel<T><<<vg_n, kThreads, 0, st>>>(n, h->du, h->rowfac, rt, h->rP, xw0(), h->sc,
+    launch_k(prep_dv_kernel<T>, dim3(vg_n), dim3(kThreads), st, n, h->du, h->rowfac, rt, h->rP, xw0(), h->sc,
                                                  h->dotpart, h->cnt_dot);
     EOT_LAUNCH_CHECK();
     h->launches++;
@@ -275,21 +288,21 @@ struct Solver {
       a.active = h->sc + SC_ACTIVE;
       CgColEpi<T> e{h->colfac, h->cP, zf()};
       dim3 grid((unsigned)geo.S, (unsigned)geo.R);
-      if (V == VEC) col_sweep_kernel<T, VEC, 1, false, 0, CgColEpi<T>><<<grid, kThreads, 0, s>>>(a, e);
-      else col_sweep_kernel<T, 1, 1, false, 0, CgColEpi<T>><<<grid, kThreads, 0, s>>>(a, e);
+      if (V == VEC) launch_k(col_sweep_kernel<T, VEC, 1, false, 0, CgColEpi<T>>, dim3(grid), dim3(kThreads), s, a, e);
+      else launch_k(col_sweep_kernel<T, 1, 1, false, 0, CgColEpi<T>>, dim3(grid), dim3(kThreads), s, a, e);
     }
     {
       SweepArgs<T> a = args();
       a.wc[0] = zf();
       a.active = h->sc + SC_ACTIVE;
       CgRowEpi e{h->rowfac, h->rPs, h->p, h->y, h->q, h->sc, h->status};
-      if (V == VEC) row_sweep_kernel<T, VEC, 1, false, false, CgRowEpi><<<rg, kThreads, 0, s>>>(a, e);
-      else row_sweep_kernel<T, 1, 1, false, false, CgRowEpi><<<rg, kThreads, 0, s>>>(a, e);
+      if (V == VEC) launch_k(row_sweep_kernel<T, VEC, 1, false, false, CgRowEpi>, dim3(rg), dim3(kThreads), s, a, e);
+      else launch_k(row_sweep_kernel<T, 1, 1, false, false, CgRowEpi>, dim3(rg), dim3(kThreads), s, a, e);
     }
-    cg_update_kernel<T><<<vg_n, kThreads, 0, s>>>(n, h->p, h->q, h->y, h->M, h->x, h->res, h->Yx,
+    launch_k(cg_update_kernel<T>, dim3(vg_n), dim3(kThreads), s, n, h->p, h->q, h->y, h->M, h->x, h->res, h->Yx,
                                                   h->z, h->sc, h->dotpart, h->cnt_dot, h->status,
                                                   cond);
-    cg_pupdate_kernel<T><<<vg_n, kThreads, 0, s>>>(n, h->z, h->rowfac, h->p, xw0(), h->sc);
+    launch_k(cg_pupdate_kernel<T>, dim3(vg_n), dim3(kThreads), s, n, h->z, h->rowfac, h->p, xw0(), h->sc);
   }
 
   CgGraph& get_graph(CgMode mode) {
@@ -329,7 +342,7 @@ struct Solver {
 
   // Runs PCG from x = 0 on F_r(rho) until the device stop flag clears.
   void run_cg(CgMode mode, int max_cg, const double* rt) {
-    cg_init_kernel<T><<<vg_n, kThreads, 0, st>>>(n, h->rP, h->rPs, rt, h->diag, h->rowfac, h->M, h->x,
+    launch_k(cg_init_kernel<T>, dim3(vg_n), dim3(kThreads), st, n, h->rP, h->rPs, rt, h->diag, h->rowfac, h->M, h->x,
                                                  h->res, h->z, h->p, h->Yx, xw0(), h->sc,
                                                  h->dotpart, h->cnt_dot);
     EOT_LAUNCH_CHECK();

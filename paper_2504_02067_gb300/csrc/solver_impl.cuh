@@ -31,11 +31,11 @@ void run_marginals(eot_handle h, const eot_problem* P, const double* u, const do
   S.row_lse(u, v, nullptr, lr, nullptr, nullptr, SC_MASS, SC_AUX1);
   S.col_lse(u, nullptr, v, nullptr, 0.0, nullptr, lc, 0, SC_AUX0, 0.0);
   if (r_out) {
-    exp_kernel<<<S.vg_n, kThreads, 0, st>>>(P->n, lr, r_out);
+    launch_k(exp_kernel, dim3(S.vg_n), dim3(kThreads), st, P->n, lr, r_out);
     h->launches++;
   }
   if (c_out) {
-    exp_kernel<<<S.vg_m, kThreads, 0, st>>>(P->m, lc, c_out);
+    launch_k(exp_kernel, dim3(S.vg_m), dim3(kThreads), st, P->m, lc, c_out);
     h->launches++;
   }
   EOT_LAUNCH_CHECK();
@@ -55,10 +55,10 @@ void run_hvp(eot_handle h, const eot_problem* P, const double* u, const double* 
   S.row_lse(u, v, nullptr, h->logrP, h->rowmax, nullptr, SC_AUX0, SC_AUX1);
   S.split_rows(u, nullptr, 0.0, h->rowmax, h->Al, nullptr, h->rowfac, h->rowmax);
   S.split_cols(v, nullptr, 0.0, nullptr, h->Bl, nullptr, h->colfac, nullptr);
-  weight_kernel<T><<<S.vg_n, kThreads, 0, st>>>(P->n, h->rowfac, nullptr, S.xw0());
-  weight_kernel<T><<<S.vg_n, kThreads, 0, st>>>(P->n, h->rowfac, du, S.xw1());
-  weight_kernel<T><<<S.vg_m, kThreads, 0, st>>>(P->m, h->colfac, nullptr, S.zf());
-  weight_kernel<T><<<S.vg_m, kThreads, 0, st>>>(P->m, h->colfac, dv, S.wsq());
+  launch_k(weight_kernel<T>, dim3(S.vg_n), dim3(kThreads), st, P->n, h->rowfac, nullptr, S.xw0());
+  launch_k(weight_kernel<T>, dim3(S.vg_n), dim3(kThreads), st, P->n, h->rowfac, du, S.xw1());
+  launch_k(weight_kernel<T>, dim3(S.vg_m), dim3(kThreads), st, P->m, h->colfac, nullptr, S.zf());
+  launch_k(weight_kernel<T>, dim3(S.vg_m), dim3(kThreads), st, P->m, h->colfac, dv, S.wsq());
   EOT_LAUNCH_CHECK();
   h->launches += 4;
   ensure_rowpart(h, P->n, S.geo.S);
@@ -101,16 +101,26 @@ void run_solve(eot_handle h, const eot_problem* P, const eot_params* prm_in, dou
   const int max_cg = prm.max_cg > 0 ? prm.max_cg : (int)std::min<int64_t>(4 * n, 2000);
   const CgMode mode = cg_mode_from_env();
   EOT_CUDA(cudaMemsetAsync(h->status, 0, sizeof(int), st));
+  S.retain_cost();
+  struct Release {  // demote the cost's L2 lines on every exit path
+    Solver<T>& s;
+    ~Release() {
+      try {
+        s.release_cost();
+      } catch (...) {
+      }
+    }
+  } release_guard{S};
 
   // H(r), H(c) and the masses (Alg. 1 line 4 needs min(H(r), H(c)))
-  vec_stats_kernel<<<S.vg_n, kThreads, 0, st>>>(n, P->r, nullptr, 0, h->sc, SC_AUX0, SC_AUX1,
+  launch_k(vec_stats_kernel, dim3(S.vg_n), dim3(kThreads), st, n, P->r, nullptr, 0, h->sc, SC_AUX0, SC_AUX1,
                                                  h->dotpart, h->cnt_dot, h->status);
   EOT_LAUNCH_CHECK();
   EOT_CUDA(cudaMemcpyAsync(h->h_sc + SC_COUNT - 2, h->sc + SC_AUX0, 2 * sizeof(double),
                            cudaMemcpyDeviceToHost, st));
   EOT_CUDA(cudaStreamSynchronize(st));
   const double Hr = -h->h_sc[SC_COUNT - 2], mr = h->h_sc[SC_COUNT - 1];
-  vec_stats_kernel<<<S.vg_m, kThreads, 0, st>>>(m, P->c, nullptr, 0, h->sc, SC_AUX0, SC_AUX1,
+  launch_k(vec_stats_kernel, dim3(S.vg_m), dim3(kThreads), st, m, P->c, nullptr, 0, h->sc, SC_AUX0, SC_AUX1,
                                                  h->dotpart, h->cnt_dot, h->status);
   EOT_LAUNCH_CHECK();
   h->launches += 2;
@@ -133,8 +143,8 @@ void run_solve(eot_handle h, const eot_problem* P, const eot_params* prm_in, dou
     const bool done = gamma == gamma_f;
     double eps_d = H / std::pow(gamma, prm.p);
     if (done) eps_d = std::min(eps_d, 2.0 * prm.tol_final / 3.0);
-    smooth_kernel<<<S.vg_n, kThreads, 0, st>>>(n, P->r, prm.w_r * eps_d, h->rt, h->logrt);
-    smooth_kernel<<<S.vg_m, kThreads, 0, st>>>(m, P->c, w_c * eps_d, h->ct, h->logct);
+    launch_k(smooth_kernel, dim3(S.vg_n), dim3(kThreads), st, n, P->r, prm.w_r * eps_d, h->rt, h->logrt);
+    launch_k(smooth_kernel, dim3(S.vg_m), dim3(kThreads), st, m, P->c, w_c * eps_d, h->ct, h->logct);
     EOT_LAUNCH_CHECK();
     h->launches += 2;
     if (t == 1) {
@@ -170,11 +180,12 @@ void run_solve(eot_handle h, const eot_problem* P, const eot_params* prm_in, dou
   S.sweep_bucket = &S.cnt.sweeps_other;
   S.row_lse(u, v, nullptr, h->logrP, nullptr, P->r, SC_GL1, SC_CHI2);
   S.col_lse(u, nullptr, v, nullptr, 0.0, nullptr, h->logcP, 0, SC_AUX0, 0.0);
-  exp_kernel<<<S.vg_m, kThreads, 0, st>>>(m, h->logcP, h->mt1);
-  vec_stats_kernel<<<S.vg_m, kThreads, 0, st>>>(m, h->mt1, P->c, 1, h->sc, SC_AUX1, -1,
+  launch_k(exp_kernel, dim3(S.vg_m), dim3(kThreads), st, m, h->logcP, h->mt1);
+  launch_k(vec_stats_kernel, dim3(S.vg_m), dim3(kThreads), st, m, h->mt1, P->c, 1, h->sc, SC_AUX1, -1,
                                                  h->dotpart, h->cnt_dot, h->status);
   EOT_LAUNCH_CHECK();
   h->launches += 2;
+  S.release_cost();
   const double* s = S.read();
   if (stats) {
     const SolveCounters& c = S.cnt;
@@ -203,10 +214,11 @@ double run_sweep_bench(eot_handle h, const eot_problem* P, const double* u, cons
                        double gamma, int kind, int iters, cudaStream_t st) {
   Solver<T> S(h, P, st);
   EOT_CUDA(cudaMemsetAsync(h->status, 0, sizeof(int), st));
+  S.retain_cost();
   S.set_scalar(SC_GAMMA, round_gamma<T>(gamma));
   // untimed set-up: the Newton-step factorisation and a CG start at rho = 1/2
   S.row_lse(u, v, nullptr, h->logrP, h->rowmax, nullptr, SC_AUX0, SC_AUX1);
-  exp_kernel<<<S.vg_n, kThreads, 0, st>>>(P->n, h->logrP, h->rt);  // r~ := r(P) (any finite target)
+  launch_k(exp_kernel, dim3(S.vg_n), dim3(kThreads), st, P->n, h->logrP, h->rt);  // r~ := r(P) (any finite target)
   EOT_LAUNCH_CHECK();
   bool ran = false;
   S.newton(u, v, h->rt, 1.0, 1e300, 0.0, 1, CgMode::kHost, &ran);
@@ -214,13 +226,13 @@ double run_sweep_bench(eot_handle h, const eot_problem* P, const double* u, cons
   S.set_scalar(SC_TOL, -1.0);
   S.set_scalar(SC_MAXIT, 1e6);
   // a positive direction p = rowfac (so <p, F_r p> > 0) and its column-sweep weights
-  weight_kernel<double><<<S.vg_n, kThreads, 0, st>>>(P->n, h->rowfac, nullptr, h->p);
-  weight_kernel<T><<<S.vg_n, kThreads, 0, st>>>(P->n, h->rowfac, h->p, S.xw0());
+  launch_k(weight_kernel<double>, dim3(S.vg_n), dim3(kThreads), st, P->n, h->rowfac, nullptr, h->p);
+  launch_k(weight_kernel<T>, dim3(S.vg_n), dim3(kThreads), st, P->n, h->rowfac, h->p, S.xw0());
   S.set_scalar(SC_RZ, 1.0);
   EOT_LAUNCH_CHECK();
   if (kind == 2) {
-    weight_kernel<T><<<S.vg_n, kThreads, 0, st>>>(P->n, h->rowfac, nullptr, S.xw1());
-    weight_kernel<T><<<S.vg_m, kThreads, 0, st>>>(P->m, h->colfac, nullptr, S.wsq());
+    launch_k(weight_kernel<T>, dim3(S.vg_n), dim3(kThreads), st, P->n, h->rowfac, nullptr, S.xw1());
+    launch_k(weight_kernel<T>, dim3(S.vg_m), dim3(kThreads), st, P->m, h->colfac, nullptr, S.wsq());
     ensure_rowpart(h, P->n, S.geo.S);
   }
   cudaEvent_t e0, e1;
@@ -247,6 +259,7 @@ double run_sweep_bench(eot_handle h, const eot_problem* P, const double* u, cons
     }
   }
   EOT_CUDA(cudaEventRecord(e1, st));
+  S.release_cost();
   EOT_CUDA(cudaEventSynchronize(e1));
   float ms = 0.f;
   EOT_CUDA(cudaEventElapsedTime(&ms, e0, e1));
@@ -267,7 +280,7 @@ void run_backward_dense(eot_handle h, const eot_problem* P, const double* u, con
   S.split_cols(v, nullptr, 0.0, nullptr, h->Bl, nullptr, h->colfac, nullptr);
   int64_t blocks = (P->n * P->m + kThreads - 1) / kThreads;
   if (blocks > 16 * (int64_t)h->sms * 8) blocks = 16 * (int64_t)h->sms * 8;
-  plan_dense_kernel<T><<<(unsigned)blocks, kThreads, 0, st>>>(P->n, P->m, S.C, P->ldc, S.Ah(), S.Bh(),
+  launch_k(plan_dense_kernel<T>, dim3((unsigned)blocks), dim3(kThreads), st, P->n, P->m, S.C, P->ldc, S.Ah(), S.Bh(),
                                                               h->sc + SC_GAMMA, h->rowfac, h->colfac,
                                                               scale, dC, P->m);
   EOT_LAUNCH_CHECK();

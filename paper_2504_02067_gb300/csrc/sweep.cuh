@@ -40,6 +40,7 @@ struct SweepArgs {
   int nrowblk;          // R  (column sweep)
   const double* gamma_dev;  // nullable: read gamma here (keeps captured graphs valid)
   const double* active;     // nullable: the kernel does nothing while *active == 0
+  int keep_l2;              // mark the cost's L2 lines evict-last (cost fits in L2)
 };
 
 template <int N>
@@ -75,17 +76,35 @@ __device__ __forceinline__ void cta_dot_finish(double (&wd)[ND > 0 ? ND : 1], in
       last = (atomicAdd(cnt, 1) == (int)nparts - 1);
     }
     __syncthreads();
-    if (last && threadIdx.x == 0) {
+    if (last) {
+      // all threads of the last CTA add the partials: fixed assignment and a
+      // fixed reduction tree, so the totals are bit-reproducible
       __threadfence();
-      DotArr<ND> tot;
+      double v[ND];
 #pragma unroll
-      for (int k = 0; k < ND; ++k) tot.v[k] = 0.0;
-      for (int64_t p = 0; p < nparts; ++p) {
+      for (int k = 0; k < ND; ++k) v[k] = 0.0;
+      for (int64_t p = threadIdx.x; p < nparts; p += kThreads) {
 #pragma unroll
-        for (int k = 0; k < ND; ++k) tot.v[k] += __ldcg(dotpart + p * 2 + k);
+        for (int k = 0; k < ND; ++k) v[k] += __ldcg(dotpart + p * 2 + k);
       }
-      *cnt = 0;
-      epi.finish(tot.v);
+#pragma unroll
+      for (int k = 0; k < ND; ++k) v[k] = warp_sum(v[k]);
+      __syncthreads();
+      if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < ND; ++k) sd[warp][k] = v[k];
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        DotArr<ND> tot;
+#pragma unroll
+        for (int k = 0; k < ND; ++k) {
+          tot.v[k] = 0.0;
+          for (int w = 0; w < kWarps; ++w) tot.v[k] += sd[w][k];
+        }
+        *cnt = 0;
+        epi.finish(tot.v);
+      }
     }
   }
 }
@@ -93,61 +112,167 @@ __device__ __forceinline__ void cta_dot_finish(double (&wd)[ND > 0 ? ND : 1], in
 // ----------------------------------------------------------------------------
 // Row sweep: out_i = reduce_j E_ij * wc_k[j] (NR = 1..3 reductions; bit k of SQM
 // makes reduction k use E_ij^2), or the online LSE of (t_ij + log wc_0[j]).
+// One row per warp, 8 rows per CTA. The column vectors (Bh and the weights) are
+// staged in shared memory tile by tile and shared by the CTA's 8 rows. Each lane
+// streams its part of the row in batches of U 16-byte loads, software-pipelined
+// over two register buffers: the loads of batch k+1 are in flight while batch k
+// is reduced.
 // ----------------------------------------------------------------------------
+template <class T, int V, int U>
+__device__ __forceinline__ void row_load(const T* crow, int j0, int tw, T (&c)[U][V], uint64_t pol) {
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int jl = j0 + u * 32 * V;
+    if (jl < tw) ld_stream(crow + jl, c[u], pol);
+  }
+}
+
+template <class T, int V, int U, int NR, int SQM, int NV, int TW>
+__device__ __forceinline__ void row_reduce_sum(const T (&c)[U][V], int j0, int tw, T ah, T g,
+                                               const T (&sv)[NV][TW], T (&S)[NR], T (&Cc)[NR]) {
+  T acc[NR];
+#pragma unroll
+  for (int k = 0; k < NR; ++k) acc[k] = T(0);
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int jl = j0 + u * 32 * V;
+    if (jl >= tw) continue;
+    T b[V], w[NR][V];
+    ld_vec_smem<V>(&sv[0][jl], b);
+#pragma unroll
+    for (int k = 0; k < NR; ++k) ld_vec_smem<V>(&sv[1 + k][jl], w[k]);
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+      const T x = expT(fmaT(-g, c[u][e], ah + b[e]));
+#pragma unroll
+      for (int k = 0; k < NR; ++k) {
+        if ((SQM >> k) & 1) acc[k] = fmaT(x * x, w[k][e], acc[k]);
+        else acc[k] = fmaT(x, w[k][e], acc[k]);
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < NR; ++k) kadd(S[k], Cc[k], acc[k]);
+}
+
+// Online LSE of t + log w over one batch. The running max mx lives on the 1/8
+// grid so that am = ah - mx is exact. One max test per 16-byte chunk: if the
+// chunk holds a t above theta, mx is raised once and the chunk's t are formed
+// again against the new mx (at most 4 raises; a non-finite t leaves a
+// non-finite sum).
+template <class T, int V, int U, int NV, int TW>
+__device__ __forceinline__ void row_reduce_lse(const T (&c)[U][V], int j0, int tw, T ah, T g,
+                                               const T (&sv)[NV][TW], T& mx, T& am, T& S, T& Cc) {
+  T acc = T(0);
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int jl = j0 + u * 32 * V;
+    if (jl >= tw) continue;
+    T b[V], w[V], t[V];
+    ld_vec_smem<V>(&sv[0][jl], b);
+    ld_vec_smem<V>(&sv[1][jl], w);
+    T tmax = T(-3.0e38);
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+      t[e] = fmaT(-g, c[u][e], am + b[e]);
+      tmax = fmax(tmax, t[e]);
+    }
+    for (int k = 0; k < 4 && tmax > T(kTheta); ++k) {
+      const T dlt = ceil_grid(tmax);
+      mx += dlt;
+      am = ah - mx;
+      const T f = expT(-dlt);
+      acc *= f;
+      S *= f;
+      Cc *= f;
+      tmax = T(-3.0e38);
+#pragma unroll
+      for (int e = 0; e < V; ++e) {
+        t[e] = fmaT(-g, c[u][e], am + b[e]);
+        tmax = fmax(tmax, t[e]);
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < V; ++e) acc = fmaT(expT(t[e]), w[e], acc);
+  }
+  kadd(S, Cc, acc);
+}
+
 template <class T, int V, int NR, bool LSE, int SQM, class Epi>
-__global__ void __launch_bounds__(kThreads) row_sweep_kernel(SweepArgs<T> a, Epi epi) {
-  constexpr int U = 4;  // chunks per lane in flight
+__global__ void __launch_bounds__(kThreads, 4) row_sweep_kernel(SweepArgs<T> a, Epi epi) {
+  constexpr int U = 4;                               // chunks per batch (two batches in flight)
+  constexpr int NV = 1 + (LSE ? 1 : NR);             // staged column vectors
+  constexpr int TW = (sizeof(T) == 4 ? 8192 : 4096) / NV;  // tile width (<= 32 KB smem)
   constexpr int ND = Epi::kDot;
+  constexpr int NA = LSE ? 1 : NR;
+  constexpr int STEP = 32 * V * U;
+  __shared__ __align__(16) T sv[NV][TW];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t i = (int64_t)blockIdx.x * kWarps + warp;
+  const bool rv = i < a.n;
+  const T* crow = a.C + (rv ? i : 0) * a.ldc;
+  // the first batch of the (immutable) cost row is in flight before the wait
+  const uint64_t pol = cost_policy(a.keep_l2);
+  T cA[U][V], cB[U][V];
+  const int tw0 = (int)min((int64_t)TW, a.m);
+  if (rv && lane * V < tw0) row_load<T, V, U>(crow, lane * V, tw0, cA, pol);
+  pdl_wait();
   if (a.active && *a.active == 0.0) return;
   double wd[ND > 0 ? ND : 1];
 #pragma unroll
   for (int k = 0; k < (ND > 0 ? ND : 1); ++k) wd[k] = 0.0;
   const T g = a.gamma_dev ? (T)*a.gamma_dev : a.gamma;
-  const int64_t wstride = (int64_t)gridDim.x * kWarps;
-  for (int64_t i = (int64_t)blockIdx.x * kWarps + warp; i < a.n; i += wstride) {
-    const T* crow = a.C + i * a.ldc;
-    const T ah = a.Ah[i];
+  const T ah = rv ? a.Ah[i] : T(0);
+  T S[NA], Cc[NA];
+#pragma unroll
+  for (int k = 0; k < NA; ++k) { S[k] = T(0); Cc[k] = T(0); }
+  T mx = T(0), am = ah;
+  bool mx_set = false;
+
+  for (int64_t t0 = 0; t0 < a.m; t0 += TW) {
+    const int tw = (int)min((int64_t)TW, a.m - t0);
+    __syncthreads();
+    for (int q = threadIdx.x; q < tw; q += kThreads) {
+      sv[0][q] = a.Bh[t0 + q];
+#pragma unroll
+      for (int k = 0; k < NV - 1; ++k) sv[1 + k][q] = a.wc[k][t0 + q];
+    }
+    __syncthreads();
+    if (!rv) continue;
+    const T* ct = crow + t0;
+    int j0 = lane * V;
+    if (j0 >= tw) continue;
+    if (t0 > 0) row_load<T, V, U>(ct, j0, tw, cA, pol);  // tile 0 was prefetched
+    if constexpr (LSE) {
+      if (!mx_set) {
+        // start the running max at the lane's first element, so that the
+        // dominant terms cannot underflow against a far-away start value
+        const T b0 = sv[0][j0];
+        mx = ceil_grid(fmaT(-g, cA[0][0], ah + b0));
+        am = ah - mx;
+        mx_set = true;
+      }
+    }
+    for (;;) {
+      const int j1 = j0 + STEP;
+      if (j1 < tw) row_load<T, V, U>(ct, j1, tw, cB, pol);
+      if constexpr (!LSE) row_reduce_sum<T, V, U, NR, SQM, NV, TW>(cA, j0, tw, ah, g, sv, S, Cc);
+      else row_reduce_lse<T, V, U, NV, TW>(cA, j0, tw, ah, g, sv, mx, am, S[0], Cc[0]);
+      if (j1 >= tw) break;
+      const int j2 = j1 + STEP;
+      if (j2 < tw) row_load<T, V, U>(ct, j2, tw, cA, pol);
+      if constexpr (!LSE) row_reduce_sum<T, V, U, NR, SQM, NV, TW>(cB, j1, tw, ah, g, sv, S, Cc);
+      else row_reduce_lse<T, V, U, NV, TW>(cB, j1, tw, ah, g, sv, mx, am, S[0], Cc[0]);
+      if (j2 >= tw) break;
+      j0 = j2;
+    }
+  }
+  pdl_trigger();
+  if (rv) {
     if constexpr (!LSE) {
       double tot[NR];
 #pragma unroll
-      for (int k = 0; k < NR; ++k) tot[k] = 0.0;
-      for (int64_t j0 = (int64_t)lane * V; j0 < a.m; j0 += 32 * V * U) {
-        T c[U][V], b[U][V], w[NR][U][V];
-        bool ok[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const int64_t j = j0 + (int64_t)u * 32 * V;
-          ok[u] = j < a.m;
-          if (ok[u]) {
-            ld_stream(crow + j, c[u]);
-            ld_vec<V>(a.Bh + j, b[u]);
-#pragma unroll
-            for (int k = 0; k < NR; ++k) ld_vec<V>(a.wc[k] + j, w[k][u]);
-          }
-        }
-        T acc[NR];
-#pragma unroll
-        for (int k = 0; k < NR; ++k) acc[k] = T(0);
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          if (!ok[u]) continue;
-#pragma unroll
-          for (int e = 0; e < V; ++e) {
-            const T t = fmaT(-g, c[u][e], ah + b[u][e]);
-            const T x = expT(t);
-#pragma unroll
-            for (int k = 0; k < NR; ++k) {
-              if ((SQM >> k) & 1) acc[k] = fmaT(x * x, w[k][u][e], acc[k]);
-              else acc[k] = fmaT(x, w[k][u][e], acc[k]);
-            }
-          }
-        }
-#pragma unroll
-        for (int k = 0; k < NR; ++k) tot[k] += (double)acc[k];
-      }
-#pragma unroll
-      for (int k = 0; k < NR; ++k) tot[k] = warp_sum(tot[k]);
+      for (int k = 0; k < NR; ++k) tot[k] = warp_sum((double)S[k] + (double)Cc[k]);
       if (lane == 0) {
         DotArr<ND> d;
         epi.row(i, tot, d.v);  // tot: [NR] sums
@@ -155,54 +280,8 @@ __global__ void __launch_bounds__(kThreads) row_sweep_kernel(SweepArgs<T> a, Epi
         for (int k = 0; k < ND; ++k) wd[k] += d.v[k];
       }
     } else {
-      // online log-sum-exp of t_ij + log w_j with a lazily moved running max mx.
-      // mx starts at 0 (so am = ah is exact) and stays on the 1/8 grid; it moves
-      // up when t > theta, and onto the element while nothing is accumulated yet
-      // (t < -kLow), so that no dominant term can underflow.
-      T mx = T(0);
-      T am = ah;
-      T s = T(0);
-      double S = 0.0;           // flushed part of s, relative to mx
-      for (int64_t j0 = (int64_t)lane * V; j0 < a.m; j0 += 32 * V * U) {
-        T c[U][V], b[U][V], w0[U][V];
-        bool ok[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const int64_t j = j0 + (int64_t)u * 32 * V;
-          ok[u] = j < a.m;
-          if (ok[u]) {
-            ld_stream(crow + j, c[u]);
-            ld_vec<V>(a.Bh + j, b[u]);
-            ld_vec<V>(a.wc[0] + j, w0[u]);
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          if (!ok[u]) continue;
-#pragma unroll
-          for (int e = 0; e < V; ++e) {
-            T t = fmaT(-g, c[u][e], am + b[u][e]);
-            // move the running max; at most 4 steps (a non-finite or huge t
-            // leaves the loop unchanged and shows up as a non-finite sum)
-            for (int k = 0; k < 4 && (t > T(kTheta) || (t < T(-kLow) && s == T(0) && S == 0.0)); ++k) {
-              const T dlt = ceil_grid(t);
-              mx += dlt;
-              am = ah - mx;
-              if (dlt > T(0)) {
-                const T f = expT(-dlt);
-                s *= f;
-                S *= (double)f;
-              }
-              t = fmaT(-g, c[u][e], am + b[u][e]);
-            }
-            s = fmaT(expT(t), w0[u][e], s);
-          }
-        }
-        S += (double)s;
-        s = T(0);
-      }
-      LsePair p{(double)mx, S};
-      p = warp_lse(p);
+      LsePair p{(double)mx, (double)S[0] + (double)Cc[0]};
+      p = warp_lse<T>(p);
       if (lane == 0) {
         DotArr<ND> d;
         epi.row_lse(i, p.m, p.s, d.v);
@@ -221,8 +300,8 @@ __global__ void __launch_bounds__(kThreads) row_sweep_kernel(SweepArgs<T> a, Epi
 // grid = (S strips of 32*V columns, R row blocks of BR rows).
 // ----------------------------------------------------------------------------
 template <class T, int V, int NC, bool LSE, int NR, class Epi>
-__global__ void __launch_bounds__(kThreads) col_sweep_kernel(SweepArgs<T> a, Epi epi) {
-  constexpr int U = 4;  // rows per warp in flight
+__global__ void __launch_bounds__(kThreads, kColCtasPerSm) col_sweep_kernel(SweepArgs<T> a, Epi epi) {
+  constexpr int U = 4;  // rows per batch (two batches in flight)
   constexpr int SW = 32 * V;
   constexpr int ND = Epi::kDot;
   constexpr int NP = LSE ? 2 : NC;  // partial arrays
@@ -235,6 +314,15 @@ __global__ void __launch_bounds__(kThreads) col_sweep_kernel(SweepArgs<T> a, Epi
   const bool jv = j < a.m;
   const int64_t r0 = (int64_t)rb * a.rows_per_block;
   const int64_t r1 = min(a.n, r0 + (int64_t)a.rows_per_block);
+  // the first batch of (immutable) cost rows is in flight before the wait
+  const uint64_t pol = cost_policy(a.keep_l2);
+  T cA[U][V], cB[U][V];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int64_t i = r0 + warp + (int64_t)u * kWarps;
+    if (i < r1 && jv) ld_stream(a.C + i * a.ldc + j, cA[u], pol);
+  }
+  pdl_wait();
   if (a.active && *a.active == 0.0) return;
   const T g = a.gamma_dev ? (T)*a.gamma_dev : a.gamma;
 
@@ -246,78 +334,95 @@ __global__ void __launch_bounds__(kThreads) col_sweep_kernel(SweepArgs<T> a, Epi
     if constexpr (NR > 0) ld_vec<V>(a.wc[0] + j, wcv[0]);
     if constexpr (NR > 1) ld_vec<V>(a.wc[1] + j, wcv[1]);
   }
-  double tot[NP][V];
+  T tot[NP][V], cmp[NP][V];  // compensated running sums
 #pragma unroll
   for (int k = 0; k < NP; ++k)
 #pragma unroll
-    for (int e = 0; e < V; ++e) tot[k][e] = 0.0;
-  // LSE state per column: running max mx (on the grid, starting at 0) and bm = Bh - mx
+    for (int e = 0; e < V; ++e) { tot[k][e] = T(0); cmp[k][e] = T(0); }
+  // LSE state per column: running max mx (on the grid) and bm = Bh - mx
   T mx[V], bm[V];
-  if constexpr (LSE) {
 #pragma unroll
-    for (int e = 0; e < V; ++e) { mx[e] = T(0); bm[e] = b[e]; }
-  }
+  for (int e = 0; e < V; ++e) { mx[e] = T(0); bm[e] = b[e]; }
 
-  for (int64_t i0 = r0 + warp; i0 < r1; i0 += (int64_t)kWarps * U) {
-    T c[U][V], ah[U], x0[U], x1[U];
-    bool ok[U];
+  // rows of this warp in batches of U, software-pipelined over two buffers
+  T hA[U], hB[U], xA[2][U], xB[2][U];
+  auto load_vec = [&](int64_t i0, T (&hh)[U], T (&xx)[2][U]) {
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int64_t i = i0 + (int64_t)u * kWarps;
-      ok[u] = i < r1;
-      if (ok[u]) {
-        ah[u] = a.Ah[i];
-        x0[u] = a.wr[0][i];
-        if constexpr (NC > 1) x1[u] = a.wr[1][i];
-        if (jv) ld_stream(a.C + i * a.ldc + j, c[u]);
-        else {
-#pragma unroll
-          for (int e = 0; e < V; ++e) c[u][e] = T(0);
-        }
+      if (i < r1) {
+        hh[u] = a.Ah[i];
+        xx[0][u] = a.wr[0][i];
+        if constexpr (NC > 1) xx[1][u] = a.wr[1][i];
       }
     }
+  };
+  auto load = [&](int64_t i0, T (&c)[U][V], T (&hh)[U], T (&xx)[2][U]) {
+    load_vec(i0, hh, xx);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = i0 + (int64_t)u * kWarps;
+      if (i < r1 && jv) ld_stream(a.C + i * a.ldc + j, c[u], pol);
+    }
+  };
+  auto reduce = [&](int64_t i0, const T (&c)[U][V], const T (&hh)[U], const T (&xx)[2][U]) {
     T acc[NP][V];
 #pragma unroll
     for (int k = 0; k < NP; ++k)
 #pragma unroll
       for (int e = 0; e < V; ++e) acc[k][e] = T(0);
+    if constexpr (LSE) {
+      // per column: form the batch's t, raise the running max once if a t
+      // exceeds theta (then form them again; at most 4 raises), accumulate
+      if (jv) {
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+          T t[U];
+          T tmax = T(-3.0e38);
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            t[u] = fmaT(-g, c[u][e], hh[u] + bm[e]);
+            if (i0 + (int64_t)u * kWarps < r1) tmax = fmax(tmax, t[u]);
+          }
+          for (int k = 0; k < 4 && tmax > T(kTheta); ++k) {
+            const T dlt = ceil_grid(tmax);
+            mx[e] += dlt;
+            bm[e] = b[e] - mx[e];
+            const T f = expT(-dlt);
+            tot[1][e] *= f;
+            cmp[1][e] *= f;
+            tmax = T(-3.0e38);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+              t[u] = fmaT(-g, c[u][e], hh[u] + bm[e]);
+              if (i0 + (int64_t)u * kWarps < r1) tmax = fmax(tmax, t[u]);
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < U; ++u)
+            if (i0 + (int64_t)u * kWarps < r1) acc[1][e] = fmaT(expT(t[u]), xx[0][u], acc[1][e]);
+        }
+      }
+    } else {
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      if (!ok[u]) continue;
+      if (i0 + (int64_t)u * kWarps >= r1) continue;
       T racc0 = T(0), racc1 = T(0);
 #pragma unroll
       for (int e = 0; e < V; ++e) {
         if constexpr (!LSE) {
-          const T t = fmaT(-g, c[u][e], ah[u] + b[e]);
+          const T t = fmaT(-g, c[u][e], hh[u] + b[e]);
           const T x = jv ? expT(t) : T(0);
-          acc[0][e] = fmaT(x, x0[u], acc[0][e]);
-          if constexpr (NC > 1) acc[1][e] = fmaT(x, x1[u], acc[1][e]);
+          acc[0][e] = fmaT(x, xx[0][u], acc[0][e]);
+          if constexpr (NC > 1) acc[1][e] = fmaT(x, xx[1][u], acc[1][e]);
           if constexpr (NR > 0) racc0 = fmaT(x, wcv[0][e], racc0);
           if constexpr (NR > 1) racc1 = fmaT(x, wcv[1][e], racc1);
-        } else {
-          if (jv) {
-            T t = fmaT(-g, c[u][e], ah[u] + bm[e]);
-            // bounded, as in the row sweep
-            for (int k = 0; k < 4 && (t > T(kTheta) ||
-                                      (t < T(-kLow) && acc[1][e] == T(0) && tot[1][e] == 0.0)); ++k) {
-              const T dlt = ceil_grid(t);
-              mx[e] += dlt;
-              bm[e] = b[e] - mx[e];
-              if (dlt > T(0)) {
-                const T f = expT(-dlt);
-                acc[1][e] *= f;  // unflushed part
-                tot[1][e] *= (double)f;
-              }
-              t = fmaT(-g, c[u][e], ah[u] + bm[e]);
-            }
-            acc[1][e] = fmaT(expT(t), x0[u], acc[1][e]);
-          }
         }
       }
       if constexpr (NR > 0) {
-        double rs0 = warp_sum((double)racc0);
+        const double rs0 = warp_sum_t(racc0);
         double rs1 = 0.0;
-        if constexpr (NR > 1) rs1 = warp_sum((double)racc1);
+        if constexpr (NR > 1) rs1 = warp_sum_t(racc1);
         if (lane == 0) {
           const int64_t i = i0 + (int64_t)u * kWarps;
           a.rowpart[(0 * S + strip) * a.n + i] = rs0;
@@ -325,19 +430,47 @@ __global__ void __launch_bounds__(kThreads) col_sweep_kernel(SweepArgs<T> a, Epi
         }
       }
     }
+    }
 #pragma unroll
     for (int k = 0; k < NP; ++k)
 #pragma unroll
-      for (int e = 0; e < V; ++e) tot[k][e] += (double)acc[k][e];
+      for (int e = 0; e < V; ++e) kadd(tot[k][e], cmp[k][e], acc[k][e]);
+  };
+  constexpr int64_t BSTEP = (int64_t)kWarps * U;
+  int64_t i0 = r0 + warp;
+  if (i0 < r1) {
+    load_vec(i0, hA, xA);  // the cost rows of this batch were prefetched
+    if constexpr (LSE) {
+      // start each column's running max at its first element
+      if (jv) {
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+          mx[e] = ceil_grid(fmaT(-g, cA[0][e], hA[0] + b[e]));
+          bm[e] = b[e] - mx[e];
+        }
+      }
+    }
+    for (;;) {
+      const int64_t i1 = i0 + BSTEP;
+      if (i1 < r1) load(i1, cB, hB, xB);
+      reduce(i0, cA, hA, xA);
+      if (i1 >= r1) break;
+      const int64_t i2 = i1 + BSTEP;
+      if (i2 < r1) load(i2, cA, hA, xA);
+      reduce(i1, cB, hB, xB);
+      if (i2 >= r1) break;
+      i0 = i2;
+    }
   }
 
+  pdl_trigger();
   // ---- combine the 8 warps of this CTA in FP64 and write the [R][m] partials ----
   __shared__ double sred[NP][kWarps][SW];
   __shared__ double smax[LSE ? kWarps : 1][LSE ? SW : 1];
 #pragma unroll
   for (int k = 0; k < NP; ++k)
 #pragma unroll
-    for (int e = 0; e < V; ++e) sred[k][warp][lane * V + e] = tot[k][e];
+    for (int e = 0; e < V; ++e) sred[k][warp][lane * V + e] = (double)tot[k][e] + (double)cmp[k][e];
   if constexpr (LSE) {
 #pragma unroll
     for (int e = 0; e < V; ++e) smax[warp][lane * V + e] = (double)mx[e];
@@ -355,7 +488,7 @@ __global__ void __launch_bounds__(kThreads) col_sweep_kernel(SweepArgs<T> a, Epi
       }
     } else {
       LsePair p{0.0, 0.0};
-      for (int w = 0; w < kWarps; ++w) p = lse_combine(p, LsePair{smax[w][cc], sred[1][w][cc]});
+      for (int w = 0; w < kWarps; ++w) p = lse_combine<T>(p, LsePair{smax[w][cc], sred[1][w][cc]});
       a.colpart[((int64_t)0 * R + rb) * a.m + jj] = p.m;
       a.colpart[((int64_t)1 * R + rb) * a.m + jj] = p.s;
     }
@@ -391,8 +524,8 @@ __global__ void __launch_bounds__(kThreads) col_sweep_kernel(SweepArgs<T> a, Epi
       } else {
         LsePair p{0.0, 0.0};
         for (int r = 0; r < R; ++r)
-          p = lse_combine(p, LsePair{__ldcg(a.colpart + (int64_t)r * a.m + jj),
-                                     __ldcg(a.colpart + ((int64_t)R + r) * a.m + jj)});
+          p = lse_combine<T>(p, LsePair{__ldcg(a.colpart + (int64_t)r * a.m + jj),
+                                        __ldcg(a.colpart + ((int64_t)R + r) * a.m + jj)});
         epi.col_lse(jj, p.m, p.s, d.v);
       }
 #pragma unroll
