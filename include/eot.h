@@ -181,6 +181,24 @@ eot_status eot_backward(eot_handle h, const eot_problem* prob, const double* u, 
 eot_status eot_sweep_bench(eot_handle h, const eot_problem* prob, const double* u, const double* v,
                            double gamma, int32_t kind, int32_t iters, double* ms_out, void* stream);
 
+/* The marginals of eot_marginals without a handle and without allocating any
+ * device memory, for callers that cannot allocate (their allocator or memory
+ * budget belongs to another component, or an allocation would synchronise the
+ * device at the wrong moment). The paper has no counterpart; this is a library
+ * facility. The scratch space is a fixed array of about 3 MB in the library,
+ * held by every GPU that loads the library until the process exits.
+ * n and m must be <= 16384 (EOT_ERR_INVALID_ARG otherwise). DENSE_F32 (MIXED or
+ * PLAIN_FP32) and DENSE_F64 (FP64) costs; u, v, r_out [n], c_out [m] are device
+ * FP64 buffers owned by the caller; status_out (device int, nullable) receives
+ * the kernels' status bits (0 = fine; non-finite or out-of-range potentials set
+ * bits and give non-finite outputs). Asynchronous on `stream`; no host readback.
+ * The first call on a device looks up the scratch array's address, so make it
+ * before any stream capture. All calls on a device share the array: calls that
+ * overlap on the GPU race, and the caller must order them. */
+eot_status eot_marginals_noalloc(const eot_problem* prob, const double* u, const double* v,
+                                 double gamma, double* r_out, double* c_out, int32_t* status_out,
+                                 void* stream);
+
 /* Number of this library's kernel launches issued on the handle so far
  * (graph-launched kernels counted once per launched node execution estimate:
  * CG kernels count 4 per CG iteration). For launch accounting in benchmarks. */

@@ -56,7 +56,7 @@ class EotStats(ctypes.Structure):
 
 EXPORTS = ["eot_create", "eot_destroy", "eot_last_error", "eot_status_string",
            "eot_params_default", "eot_marginals", "eot_hvp", "eot_newton_solve", "eot_solve",
-           "eot_backward", "eot_sweep_bench", "eot_kernel_launches"]
+           "eot_backward", "eot_sweep_bench", "eot_marginals_noalloc", "eot_kernel_launches"]
 
 _LIB = None
 
@@ -87,6 +87,8 @@ def load_library(path=None):
     L.eot_solve.argtypes = [vp, P, ctypes.POINTER(EotParams), vp, vp, ctypes.POINTER(EotStats), vp]
     L.eot_backward.argtypes = [vp, P, vp, vp, dbl, dbl, vp, vp, vp, vp, vp, vp]
     L.eot_sweep_bench.argtypes = [vp, P, vp, vp, dbl, i32, i32, ctypes.POINTER(dbl), vp]
+    L.eot_marginals_noalloc.argtypes = [P, vp, vp, dbl, vp, vp, vp, vp]
+    L.eot_marginals_noalloc.restype = ctypes.c_int
     L.eot_kernel_launches.argtypes = [vp]
     L.eot_kernel_launches.restype = i64
     for f in ("eot_create", "eot_destroy", "eot_marginals", "eot_hvp", "eot_newton_solve",
@@ -257,3 +259,12 @@ def default_params(**overrides):
     for k, val in overrides.items():
         setattr(p, k, val)
     return p
+
+
+def eot_marginals_noalloc(prob, u, v, gamma, r_out, c_out, status_out=None, stream=None):
+    """eot_marginals_noalloc of include/eot.h: marginals into caller-provided
+    tensors, no handle, no device allocation by the library."""
+    st = load_library().eot_marginals_noalloc(prob.ref(), _p(u), _p(v), float(gamma), _p(r_out),
+                                              _p(c_out), _p(status_out), _stream(stream))
+    if st != EOT_OK:
+        raise EotError(st, "eot_marginals_noalloc failed")
