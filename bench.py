@@ -159,9 +159,16 @@ def measured_peaks():
 def traffic_record():
     """DRAM bytes per launch of the CG sweeps from the committed ncu summary, valid
     only while the sweep source is unchanged (hash recorded with the numbers)."""
-    path = os.path.join(ROOT, "profiles", "cg_sweeps_grid4096_traffic.json")
+    path = os.path.join(ROOT, "profiles", "cg_sweeps_grid4096_traffic.txt")
     try:
-        rec = json.load(open(path))
+        rec = {"dram_bytes_per_launch": {}}
+        for line in open(path):
+            parts = line.split()
+            if len(parts) == 2 and not line.startswith("#"):
+                if parts[0] == "sweep_cuh_sha256_16":
+                    rec[parts[0]] = parts[1]
+                else:
+                    rec["dram_bytes_per_launch"][parts[0]] = int(parts[1])
     except Exception:
         return None
     h = hashlib.sha256(open(os.path.join(ROOT, "paper_2504_02067_gb300", "csrc", "sweep.cuh"),
