@@ -348,19 +348,26 @@ def run_ours(args):
 # reference arm: the oracle on the host cores
 # ---------------------------------------------------------------------------
 
-REFERENCE_OPS = None  # filled from profiles/oracle_ops_grid4096.json when present
+def oracle_ops_of_workload():
+    """The oracle's own operation counts on this workload, from its recorded run
+    (tests/golden/grid4096_oracle_trace.json). In the oracle every stage makes a
+    column and a row LSE update, every Newton step forms the plan once and makes a
+    row LSE update, every line-search trial a column LSE, every ChiSinkhorn
+    iteration two LSE updates; the outer tests of NewtonSolve and d_v are
+    matrix-vector products on the stored plan, as are the CG steps."""
+    tr = json.load(open(os.path.join(ROOT, "tests", "golden", "grid4096_oracle_trace.json")))
+    t = tr["sqeuclid"]
+    lse_like = 2 * t["stages"] + 2 * t["newton_steps"] + t["ls_trials"] + 2 * t["sinkhorn_iters"]
+    cg_like = t["cg_iters"] + 2 * t["newton_steps"]
+    return {"sweeps_total": lse_like + cg_like, "sweeps_cg": cg_like, "cg_iters": cg_like,
+            "source": "tests/golden/grid4096_oracle_trace.json"}
 
 
 def run_reference(args):
     rank, world, _ = env_rank()
     if rank != 0:
         return None
-    try:
-        ops = json.load(open(os.path.join(ROOT, "profiles", "oracle_ops_grid4096.json")))
-    except Exception:
-        print(json.dumps({"impl": "reference", "unavailable": "oracle op counts of the workload "
-                          "are not recorded (profiles/oracle_ops_grid4096.json missing)"}))
-        return None
+    ops = oracle_ops_of_workload()
     per = max(2.0, args.cpu_seconds / 2)
     vals = []
     for k in range(args.warmup + args.steps):
