@@ -42,12 +42,15 @@ void ensure_capacity(eot_handle h, int64_t n, int64_t m) {
   h->sc = (double*)dev_alloc(h, SC_COUNT * sizeof(double));
   h->status = (int*)dev_alloc(h, sizeof(int));
   h->cnt_strip = (int*)dev_alloc(h, h->max_strips * sizeof(int));
-  h->cnt_rowblk = (int*)dev_alloc(h, h->max_rowblk * sizeof(int));
+  h->rowblk_slots = std::max<int64_t>(h->max_rowblk, L / 256 + 2);
+  h->cnt_rowblk = (int*)dev_alloc(h, h->rowblk_slots * sizeof(int));
+  h->maxbuf_len = L / 256 + 8 * (int64_t)h->sms + 64;
+  h->maxbuf = (double*)dev_alloc(h, h->maxbuf_len * sizeof(double));
   h->cnt_dot = (int*)dev_alloc(h, sizeof(int));
   EOT_CUDA(cudaMemset(h->sc, 0, SC_COUNT * sizeof(double)));
   EOT_CUDA(cudaMemset(h->status, 0, sizeof(int)));
   EOT_CUDA(cudaMemset(h->cnt_strip, 0, h->max_strips * sizeof(int)));
-  EOT_CUDA(cudaMemset(h->cnt_rowblk, 0, h->max_rowblk * sizeof(int)));
+  EOT_CUDA(cudaMemset(h->cnt_rowblk, 0, h->rowblk_slots * sizeof(int)));
   EOT_CUDA(cudaMemset(h->cnt_dot, 0, sizeof(int)));
   h->colpart = (double*)dev_alloc(h, 2 * h->max_rowblk * Mm * sizeof(double));
   h->dotpart = (double*)dev_alloc(h, 2 * h->dot_slots * sizeof(double));
@@ -64,7 +67,10 @@ void ensure_capacity(eot_handle h, int64_t n, int64_t m) {
 }
 
 void ensure_rowpart(eot_handle h, int64_t n, int64_t strips) {
-  const int64_t need = 2 * strips * std::max(n, h->cap_n);
+  ensure_rowpart_elems(h, 2 * strips * std::max(n, h->cap_n));
+}
+
+void ensure_rowpart_elems(eot_handle h, int64_t need) {
   if (need <= h->cap_rowpart) return;
   if (h->rowpart) {
     EOT_CUDA(cudaStreamSynchronize(0));
@@ -100,7 +106,7 @@ eot_status guarded(eot_handle h, F&& f) {
     if (h->cnt_strip) {
       cudaDeviceSynchronize();
       cudaMemset(h->cnt_strip, 0, h->max_strips * sizeof(int));
-      cudaMemset(h->cnt_rowblk, 0, h->max_rowblk * sizeof(int));
+      cudaMemset(h->cnt_rowblk, 0, h->rowblk_slots * sizeof(int));
       cudaMemset(h->cnt_dot, 0, sizeof(int));
     }
     return e.st;
@@ -126,7 +132,14 @@ void check_problem(eot_handle h, const eot_problem* P, bool need_marginals) {
         throw EotError{EOT_ERR_UNSUPPORTED, "DENSE_F64 takes FP64 precision"};
       break;
     case EOT_COST_SQEUCLID_POINTS:
-      throw EotError{EOT_ERR_UNSUPPORTED, "point costs go through the point-cloud entry points"};
+      if (!P->X || !P->Y) throw EotError{EOT_ERR_INVALID_ARG, "X and Y are required for point costs"};
+      if (P->d < 1 || P->d > 64) throw EotError{EOT_ERR_INVALID_ARG, "point dimension d must be in [1, 64]"};
+      if (P->precision < EOT_PREC_FP64 || P->precision > EOT_PREC_PLAIN_FP32)
+        throw EotError{EOT_ERR_INVALID_ARG, "unknown precision"};
+      if (!(P->cost_scale >= 0.0) || !std::isfinite(P->cost_scale))
+        throw EotError{EOT_ERR_INVALID_ARG, "cost_scale must be finite (<= 0 asks for 1 / max cost)"};
+      ensure_capacity(h, P->n, P->m);
+      return;
     default:
       throw EotError{EOT_ERR_INVALID_ARG, "unknown cost kind"};
   }
@@ -140,7 +153,10 @@ void check_gamma(double g) {
     throw EotError{EOT_ERR_INVALID_ARG, "gamma must be finite, > 0 and < 2^19"};
 }
 
-bool is_f64(const eot_problem* P) { return P->kind == EOT_COST_DENSE_F64; }
+bool is_f64(const eot_problem* P) {
+  return P->kind == EOT_COST_DENSE_F64 ||
+         (P->kind == EOT_COST_SQEUCLID_POINTS && P->precision == EOT_PREC_FP64);
+}
 
 }  // namespace
 

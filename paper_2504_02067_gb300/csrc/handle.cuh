@@ -58,7 +58,9 @@ struct eot_handle_s {
   // sweep scratch
   int *cnt_strip = nullptr, *cnt_rowblk = nullptr, *cnt_dot = nullptr;
   double *colpart = nullptr, *rowpart = nullptr, *dotpart = nullptr;
-  int64_t max_strips = 0, max_rowblk = 64, dot_slots = 0;
+  int64_t max_strips = 0, max_rowblk = 64, dot_slots = 0, rowblk_slots = 0;
+  double* maxbuf = nullptr;  // per-CTA candidates of the point-cost maximum
+  int64_t maxbuf_len = 0;
   // FP64 n-vectors
   double *Al = nullptr, *rowfac = nullptr, *rP = nullptr, *logrP = nullptr, *rowmax = nullptr;
   double *rt = nullptr, *logrt = nullptr, *du = nullptr, *x = nullptr, *res = nullptr;
@@ -115,6 +117,7 @@ inline void* dev_alloc(eot_handle h, size_t bytes) {
 
 void ensure_capacity(eot_handle h, int64_t n, int64_t m);
 void ensure_rowpart(eot_handle h, int64_t n, int64_t strips);
+void ensure_rowpart_elems(eot_handle h, int64_t elems);
 void free_graphs(eot_handle h);
 
 // sweep geometry

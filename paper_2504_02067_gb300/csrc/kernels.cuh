@@ -513,6 +513,18 @@ __global__ void plan_dense_kernel(int64_t n, int64_t m, const T* C, int64_t ldc,
   }
 }
 
+// out = f * d + s * g for one side of the two-sweep Hessian-vector product;
+// f (a marginal) is also copied to fout when given.
+static __global__ void hvp_assemble_kernel(int64_t n, const double* f, const double* g,
+                                           const double* d, double s, double* out, double* fout) {
+  pdl_wait();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    out[i] = f[i] * d[i] + s * g[i];
+    if (fout) fout[i] = f[i];
+  }
+}
+
 // Resets the L2 eviction priority of a cost marked evict-last by the sweeps
 // (one applypriority per 128-byte line, all lines inside the cost's rows), so
 // that later traffic evicts it normally.

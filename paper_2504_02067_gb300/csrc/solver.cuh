@@ -12,8 +12,10 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <vector>
 
 #include "handle.cuh"
+#include "sweep_pts.cuh"
 
 namespace eot {
 
@@ -48,11 +50,31 @@ struct Solver {
   SolveCounters cnt;
   int64_t* sweep_bucket;
 
+  // point-cloud cost (C == nullptr): C_ij = sC |x_i - y_j|^2
+  bool points = false;
+  const float *X = nullptr, *Y = nullptr;
+  int d = 0;
+  double sC = 0.0;
+
   Solver(eot_handle h_, const eot_problem* P, cudaStream_t s)
       : h(h_), st(s), n(P->n), m(P->m), ldc(P->ldc), C((const T*)P->C) {
     plain = P->precision == EOT_PREC_PLAIN_FP32;
-    const bool aligned = ((uintptr_t)C % 16) == 0;
-    V = (aligned && (m % VEC) == 0 && (ldc % VEC) == 0) ? VEC : 1;
+    points = P->kind == EOT_COST_SQEUCLID_POINTS;
+    if (points) {
+      C = nullptr;
+      ldc = m;
+      X = P->X;
+      Y = P->Y;
+      d = (int)P->d;
+      V = 1;
+      // partial buffers of both orientations, before any graph capture
+      ensure_rowpart_elems(h, 2 * pts_geo(true).S * n);
+      ensure_rowpart_elems(h, 2 * pts_geo(false).S * m);
+      sC = P->cost_scale > 0.0 ? P->cost_scale : max_cost_scale();
+    } else {
+      const bool aligned = ((uintptr_t)C % 16) == 0;
+      V = (aligned && (m % VEC) == 0 && (ldc % VEC) == 0) ? VEC : 1;
+    }
     vg_n = vec_grid(n);
     vg_m = vec_grid(m);
     rg = row_grid(n);
@@ -60,10 +82,51 @@ struct Solver {
     sweep_bucket = &cnt.sweeps_other;
   }
 
+  // ---- point-cloud geometry: own blocks of 256 RO elements x S chunks ----
+  struct PtsGeo {
+    int64_t B, S, chunk;
+  };
+  static int pts_ro(int d) { return d <= 4 ? 4 : (d <= 16 ? 2 : 1); }
+  PtsGeo pts_geo(bool rows) const {
+    const int64_t n_own = rows ? n : m, n_oth = rows ? m : n;
+    PtsGeo g;
+    g.B = (n_own + (int64_t)kThreads * pts_ro(d) - 1) / ((int64_t)kThreads * pts_ro(d));
+    int64_t S = (2 * (int64_t)h->sms + g.B - 1) / g.B;
+    S = std::max<int64_t>(1, std::min<int64_t>(S, (n_oth + 31) / 32));
+    g.chunk = ((n_oth + S - 1) / S + 31) / 32 * 32;
+    g.S = (n_oth + g.chunk - 1) / g.chunk;
+    return g;
+  }
+  // s_C = 1 / max_ij |x_i - y_j|^2 (cost normalised to max 1, Sec. 4.1): FP32 scan,
+  // FP64 re-evaluation of each thread's arg-max pair, maximum on the host.
+  double max_cost_scale() {
+    const int64_t B = (n + kThreads - 1) / kThreads;
+    int64_t S = std::max<int64_t>(1, (2 * (int64_t)h->sms + B - 1) / B);
+    S = std::min<int64_t>(S, (m + 255) / 256);
+    const int64_t chunk = (m + S - 1) / S;
+    S = (m + chunk - 1) / chunk;
+    if (B * S > h->maxbuf_len) throw EotError{EOT_ERR_INVALID_ARG, "cost-max buffer too small"};
+    const dim3 grid((unsigned)B, (unsigned)S);
+    if (d <= 4) launch_k(pts_maxdist_kernel<4>, grid, dim3(kThreads), st, X, Y, n, m, d, chunk, h->maxbuf);
+    else if (d <= 16) launch_k(pts_maxdist_kernel<16>, grid, dim3(kThreads), st, X, Y, n, m, d, chunk, h->maxbuf);
+    else launch_k(pts_maxdist_kernel<64>, grid, dim3(kThreads), st, X, Y, n, m, d, chunk, h->maxbuf);
+    h->launches++;
+    std::vector<double> v((size_t)(B * S));
+    EOT_CUDA(cudaMemcpyAsync(v.data(), h->maxbuf, v.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    EOT_CUDA(cudaStreamSynchronize(st));
+    double mx = 0.0;
+    for (double x : v) mx = std::max(mx, x);
+    if (!(mx > 0.0) || !std::isfinite(mx))
+      throw EotError{EOT_ERR_INVALID_ARG, "point costs: all points coincide or are not finite"};
+    return 1.0 / mx;
+  }
+
   // Keep the cost resident in L2 across the sweeps of one call when it fits in
   // 60% of L2 (evict-last loads); release() demotes it again.
   bool keep_l2 = false;
-  void retain_cost() { keep_l2 = (double)n * (double)ldc * sizeof(T) <= 0.6 * (double)h->l2_bytes; }
+  void retain_cost() {
+    keep_l2 = !points && (double)n * (double)ldc * sizeof(T) <= 0.6 * (double)h->l2_bytes;
+  }
   void release_cost() {
     if (!keep_l2) return;
     const int64_t bytes = n * ldc * (int64_t)sizeof(T);
@@ -101,6 +164,11 @@ struct Solver {
     a.gamma_dev = h->sc + SC_GAMMA;
     a.active = nullptr;
     a.keep_l2 = keep_l2 ? 1 : 0;
+    a.X = X;
+    a.Y = Y;
+    a.d = d;
+    a.sC = sC;
+    a.chunk = 0;
     return a;
   }
 
@@ -156,19 +224,54 @@ struct Solver {
   }
 
   // ---------------- sweep launchers ----------------
+  // point sweep: own side = rows (ROWS) or columns, dispatched on d
+  template <int NR, bool LSE, int SQM, bool ROWS, class Epi>
+  void launch_pts(cudaStream_t s, SweepArgs<T> a, const Epi& e) {
+    const PtsGeo g = pts_geo(ROWS);
+    a.chunk = g.chunk;
+    const dim3 grid((unsigned)g.B, (unsigned)g.S);
+    // the FP32 mixed path forms D compensated; plain FP32 and FP64 use the
+    // direct sum of squares
+    constexpr bool F32 = sizeof(T) == 4;
+    const bool precise = F32 && !plain;
+    if (d <= 4) {
+      if (precise) launch_k(pts_sweep_kernel<T, 4, 4, NR, LSE, SQM, ROWS, F32, Epi>, grid, dim3(kThreads), s, a, e);
+      else launch_k(pts_sweep_kernel<T, 4, 4, NR, LSE, SQM, ROWS, false, Epi>, grid, dim3(kThreads), s, a, e);
+    } else if (d <= 16) {
+      if (precise) launch_k(pts_sweep_kernel<T, 16, 2, NR, LSE, SQM, ROWS, F32, Epi>, grid, dim3(kThreads), s, a, e);
+      else launch_k(pts_sweep_kernel<T, 16, 2, NR, LSE, SQM, ROWS, false, Epi>, grid, dim3(kThreads), s, a, e);
+    } else {
+      if (precise) launch_k(pts_sweep_kernel<T, 64, 1, NR, LSE, SQM, ROWS, F32, Epi>, grid, dim3(kThreads), s, a, e);
+      else launch_k(pts_sweep_kernel<T, 64, 1, NR, LSE, SQM, ROWS, false, Epi>, grid, dim3(kThreads), s, a, e);
+    }
+  }
+  template <int NR, bool LSE, int SQM, class Epi>
+  void launch_row(cudaStream_t s, const SweepArgs<T>& a, const Epi& e) {
+    if (points) launch_pts<NR, LSE, SQM, true>(s, a, e);
+    else if (V == VEC) launch_k(row_sweep_kernel<T, VEC, NR, LSE, SQM, Epi>, dim3(rg), dim3(kThreads), s, a, e);
+    else launch_k(row_sweep_kernel<T, 1, NR, LSE, SQM, Epi>, dim3(rg), dim3(kThreads), s, a, e);
+  }
+  template <int NC, bool LSE, int NR, class Epi>
+  void launch_col(cudaStream_t s, const SweepArgs<T>& a, const Epi& e) {
+    if (points) {
+      if constexpr (NR == 0) launch_pts<NC, LSE, 0, false>(s, a, e);
+      else throw EotError{EOT_ERR_UNSUPPORTED, "fused two-sided sweep needs a dense cost"};
+      return;
+    }
+    const dim3 grid((unsigned)geo.S, (unsigned)geo.R);
+    if (V == VEC) launch_k(col_sweep_kernel<T, VEC, NC, LSE, NR, Epi>, grid, dim3(kThreads), s, a, e);
+    else launch_k(col_sweep_kernel<T, 1, NC, LSE, NR, Epi>, grid, dim3(kThreads), s, a, e);
+  }
   template <int NR, bool LSE, int SQM, class Epi>
   void row(const SweepArgs<T>& a, const Epi& e) {
-    if (V == VEC) launch_k(row_sweep_kernel<T, VEC, NR, LSE, SQM, Epi>, dim3(rg), dim3(kThreads), st, a, e);
-    else launch_k(row_sweep_kernel<T, 1, NR, LSE, SQM, Epi>, dim3(rg), dim3(kThreads), st, a, e);
+    launch_row<NR, LSE, SQM>(st, a, e);
     EOT_LAUNCH_CHECK();
     h->launches++;
     (*sweep_bucket)++;
   }
   template <int NC, bool LSE, int NR, class Epi>
   void col(const SweepArgs<T>& a, const Epi& e) {
-    dim3 grid((unsigned)geo.S, (unsigned)geo.R);
-    if (V == VEC) launch_k(col_sweep_kernel<T, VEC, NC, LSE, NR, Epi>, dim3(grid), dim3(kThreads), st, a, e);
-    else launch_k(col_sweep_kernel<T, 1, NC, LSE, NR, Epi>, dim3(grid), dim3(kThreads), st, a, e);
+    launch_col<NC, LSE, NR>(st, a, e);
     EOT_LAUNCH_CHECK();
     h->launches++;
     (*sweep_bucket)++;
@@ -287,17 +390,14 @@ struct Solver {
       a.wr[0] = xw0();
       a.active = h->sc + SC_ACTIVE;
       CgColEpi<T> e{h->colfac, h->cP, zf()};
-      dim3 grid((unsigned)geo.S, (unsigned)geo.R);
-      if (V == VEC) launch_k(col_sweep_kernel<T, VEC, 1, false, 0, CgColEpi<T>>, dim3(grid), dim3(kThreads), s, a, e);
-      else launch_k(col_sweep_kernel<T, 1, 1, false, 0, CgColEpi<T>>, dim3(grid), dim3(kThreads), s, a, e);
+      launch_col<1, false, 0>(s, a, e);
     }
     {
       SweepArgs<T> a = args();
       a.wc[0] = zf();
       a.active = h->sc + SC_ACTIVE;
       CgRowEpi e{h->rowfac, h->rPs, h->p, h->y, h->q, h->sc, h->status};
-      if (V == VEC) launch_k(row_sweep_kernel<T, VEC, 1, false, false, CgRowEpi>, dim3(rg), dim3(kThreads), s, a, e);
-      else launch_k(row_sweep_kernel<T, 1, 1, false, false, CgRowEpi>, dim3(rg), dim3(kThreads), s, a, e);
+      launch_row<1, false, 0>(s, a, e);
     }
     launch_k(cg_update_kernel<T>, dim3(vg_n), dim3(kThreads), s, n, h->p, h->q, h->y, h->M, h->x, h->res, h->Yx,
                                                   h->z, h->sc, h->dotpart, h->cnt_dot, h->status,
@@ -307,7 +407,8 @@ struct Solver {
 
   CgGraph& get_graph(CgMode mode) {
     const int B = mode == CgMode::kWhile ? 1 : 6;
-    const CgKey key{(int)sizeof(T), V, mode == CgMode::kWhile ? 1 : 0, n, m, ldc, (uintptr_t)C};
+    const CgKey key{(int)sizeof(T) + (points ? 100 * d : 0), V, mode == CgMode::kWhile ? 1 : 0, n, m,
+                    ldc, points ? (uintptr_t)X ^ ((uintptr_t)Y << 1) : (uintptr_t)C};
     auto it = h->graphs.find(key);
     if (it != h->graphs.end()) return it->second;
     if (h->graphs.size() >= 32) free_graphs(h);

@@ -61,6 +61,25 @@ void run_hvp(eot_handle h, const eot_problem* P, const double* u, const double* 
   launch_k(weight_kernel<T>, dim3(S.vg_m), dim3(kThreads), st, P->m, h->colfac, dv, S.wsq());
   EOT_LAUNCH_CHECK();
   h->launches += 4;
+  if (S.points) {
+    // point costs: a row sweep (r(P), P dv) and a column sweep (c(P), P^T du), then
+    // out_u = r(P) du + s P dv, out_v = s P^T du + c(P) dv
+    SweepArgs<T> a = S.args();
+    a.wc[0] = S.zf();
+    a.wc[1] = S.wsq();
+    S.template row<2, false, 0>(a, RowSumEpi{h->rowfac, h->rP, h->y});
+    SweepArgs<T> b = S.args();
+    b.wr[0] = S.xw0();
+    b.wr[1] = S.xw1();
+    S.template col<2, false, 0>(b, ColSumEpi{h->colfac, h->cP, h->mt1});
+    launch_k(hvp_assemble_kernel, dim3(S.vg_n), dim3(kThreads), st, P->n, (const double*)h->rP,
+             (const double*)h->y, du, s, ou, r_out);
+    launch_k(hvp_assemble_kernel, dim3(S.vg_m), dim3(kThreads), st, P->m, (const double*)h->cP,
+             (const double*)h->mt1, dv, s, ov, c_out);
+    h->launches += 2;
+    S.read();
+    return;
+  }
   ensure_rowpart(h, P->n, S.geo.S);
   SweepArgs<T> a = S.args();
   a.wr[0] = S.xw0();
@@ -230,6 +249,7 @@ double run_sweep_bench(eot_handle h, const eot_problem* P, const double* u, cons
   launch_k(weight_kernel<T>, dim3(S.vg_n), dim3(kThreads), st, P->n, h->rowfac, h->p, S.xw0());
   S.set_scalar(SC_RZ, 1.0);
   EOT_LAUNCH_CHECK();
+  if (kind == 2 && S.points) throw EotError{EOT_ERR_UNSUPPORTED, "kind 2 (fused HVP sweep) needs a dense cost"};
   if (kind == 2) {
     launch_k(weight_kernel<T>, dim3(S.vg_n), dim3(kThreads), st, P->n, h->rowfac, nullptr, S.xw1());
     launch_k(weight_kernel<T>, dim3(S.vg_m), dim3(kThreads), st, P->m, h->colfac, nullptr, S.wsq());

@@ -28,7 +28,7 @@ struct SweepArgs {
   const T* Ah;          // [n] high part of the row offsets
   const T* Bh;          // [m] high part of the column offsets
   const T* wc[3];       // [m] column weights of row reductions
-  const T* wr[2];       // [n] row weights of column reductions
+  const T* wr[3];       // [n] row weights of column reductions
   T gamma;
   double* colpart;      // [NC or 2][R][m] column partials
   double* rowpart;      // [NR][S][n] row partials (column sweep with row reductions)
@@ -41,6 +41,12 @@ struct SweepArgs {
   const double* gamma_dev;  // nullable: read gamma here (keeps captured graphs valid)
   const double* active;     // nullable: the kernel does nothing while *active == 0
   int keep_l2;              // mark the cost's L2 lines evict-last (cost fits in L2)
+  // point-cloud cost (C == nullptr): C_ij = sC |x_i - y_j|^2
+  const float* X;           // [n][d]
+  const float* Y;           // [m][d]
+  int d;
+  double sC;
+  int64_t chunk;            // other-side elements per chunk (grid.y)
 };
 
 template <int N>
