@@ -166,7 +166,11 @@ eot_status eot_solve(eot_handle h, const eot_problem* prob, const eot_params* pa
  *   dX_i = grad_scale * 2 s_C sum_j P_ij (x_i - y_j)  (points; device n x d FP32)
  *   dY_j = grad_scale * 2 s_C sum_i P_ij (y_j - x_i)  (points; device m x d FP32)
  *   dr = grad_scale * u / gamma, dc = grad_scale * v / gamma (device FP64)
- * Each output nullable. s_C is the problem's cost scale, held constant. */
+ * Each output nullable. s_C is the problem's cost scale, held constant. P is
+ * formed with each side shifted by its own log-marginal, so (u + k, v - k) gives
+ * the same outputs for any k. dC needs a dense problem, dX / dY a point problem
+ * (EOT_ERR_UNSUPPORTED otherwise). Outputs below the FP32 range flush to zero.
+ * Errors: INVALID_ARG, UNSUPPORTED, NONFINITE, CUDA. Synchronises. */
 eot_status eot_backward(eot_handle h, const eot_problem* prob, const double* u, const double* v,
                         double gamma, double grad_scale, float* dC, float* dX, float* dY,
                         double* dr, double* dc, void* stream);

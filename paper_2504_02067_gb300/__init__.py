@@ -8,3 +8,11 @@ from .binding import (COST_DENSE_F32, COST_DENSE_F64, COST_SQEUCLID_POINTS, PREC
                       EotError, EotParams, EotProblem, EotStats, Handle, Problem,
                       default_params, load_library)
 from .buildlib import build  # noqa: F401
+
+
+def __getattr__(name):
+    # the autograd layer imports torch's autograd machinery; load it on first use
+    if name in ("EOTFunction", "eot_value"):
+        from . import autograd
+        return getattr(autograd, name)
+    raise AttributeError(name)

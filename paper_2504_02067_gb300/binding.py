@@ -143,7 +143,7 @@ class Problem:
         s.r = r.data_ptr() if r is not None else None
         s.c = c.data_ptr() if c is not None else None
         self.struct = s
-        self.n, self.m = int(s.n), int(s.m)
+        self.n, self.m, self.d = int(s.n), int(s.m), int(s.d)
         self.precision = precision
 
     def ref(self):

@@ -297,11 +297,17 @@ eot_status eot_backward(eot_handle h, const eot_problem* prob, const double* u, 
     check_problem(h, prob, false);
     check_gamma(gamma);
     if (!u || !v) throw EotError{EOT_ERR_INVALID_ARG, "u and v are required"};
-    if (dX || dY) throw EotError{EOT_ERR_UNSUPPORTED, "dX / dY need a point-cloud problem"};
+    const bool pts = prob->kind == EOT_COST_SQEUCLID_POINTS;
+    if ((dX || dY) && !pts) throw EotError{EOT_ERR_UNSUPPORTED, "dX / dY need a point-cloud problem"};
+    if (dC && pts) throw EotError{EOT_ERR_UNSUPPORTED, "dC needs a dense cost (points: use dX / dY)"};
     cudaStream_t st = (cudaStream_t)stream;
     if (dC) {
       if (is_f64(prob)) run_backward_dense<double>(h, prob, u, v, gamma, grad_scale, dC, st);
       else run_backward_dense<float>(h, prob, u, v, gamma, grad_scale, dC, st);
+    }
+    if (dX || dY) {
+      if (is_f64(prob)) run_backward_points<double>(h, prob, u, v, gamma, grad_scale, dX, dY, st);
+      else run_backward_points<float>(h, prob, u, v, gamma, grad_scale, dX, dY, st);
     }
     const double a = grad_scale / gamma;
     if (dr) {

@@ -279,6 +279,43 @@ struct Solver {
 
   // log r(P) and the running row max at (u, v): A = u - rshift, B = v.
   // With a target rt, also ||rt - r(P)||_1 -> SC_GL1 and chi^2(rt | r(P)) -> SC_CHI2.
+  // Point gradients: out = scale * ownfac * sum_o P-weights (x_own - x_other),
+  // components in groups of DG (one launch per group); ROWS: own = rows.
+  template <bool ROWS>
+  void grad_pts(double scale, const double* ownfac, float* out) {
+    const int64_t n_own = ROWS ? n : m, n_oth = ROWS ? m : n;
+    const int64_t B = (n_own + kThreads - 1) / kThreads;
+    int64_t S = (2 * (int64_t)h->sms + B - 1) / B;
+    S = std::max<int64_t>(1, std::min<int64_t>(S, (n_oth + 31) / 32));
+    const int64_t chunk = ((n_oth + S - 1) / S + 31) / 32 * 32;
+    S = (n_oth + chunk - 1) / chunk;
+    const int DG = d <= 4 ? 4 : 16;
+    ensure_rowpart_elems(h, (int64_t)DG * S * n_own);
+    if (B > h->rowblk_slots) throw EotError{EOT_ERR_INVALID_ARG, "ticket array too small"};
+    SweepArgs<T> a = args();
+    a.rowpart = h->rowpart;
+    a.chunk = chunk;
+    a.wc[0] = ewc();
+    a.wr[0] = ewr();
+    const dim3 grid((unsigned)B, (unsigned)S);
+    constexpr bool F32 = sizeof(T) == 4;
+    const bool precise = F32 && !plain;
+    for (int k0 = 0; k0 < d; k0 += DG) {
+      if (d <= 4) {
+        if (precise) launch_k(pts_grad_kernel<T, 4, 4, ROWS, F32>, grid, dim3(kThreads), st, a, k0, scale, ownfac, out);
+        else launch_k(pts_grad_kernel<T, 4, 4, ROWS, false>, grid, dim3(kThreads), st, a, k0, scale, ownfac, out);
+      } else if (d <= 16) {
+        if (precise) launch_k(pts_grad_kernel<T, 16, 16, ROWS, F32>, grid, dim3(kThreads), st, a, k0, scale, ownfac, out);
+        else launch_k(pts_grad_kernel<T, 16, 16, ROWS, false>, grid, dim3(kThreads), st, a, k0, scale, ownfac, out);
+      } else {
+        if (precise) launch_k(pts_grad_kernel<T, 64, 16, ROWS, F32>, grid, dim3(kThreads), st, a, k0, scale, ownfac, out);
+        else launch_k(pts_grad_kernel<T, 64, 16, ROWS, false>, grid, dim3(kThreads), st, a, k0, scale, ownfac, out);
+      }
+      EOT_LAUNCH_CHECK();
+      h->launches++;
+    }
+  }
+
   void row_lse(const double* u, const double* v, const double* rshift, double* out_lse,
                double* out_max, const double* rt, int s0 = SC_GL1, int s1 = SC_CHI2) {
     split_rows(u, nullptr, 0.0, rshift, h->Al, nullptr, nullptr, nullptr);
@@ -585,5 +622,8 @@ double run_sweep_bench(eot_handle h, const eot_problem* P, const double* u, cons
 template <class T>
 void run_backward_dense(eot_handle h, const eot_problem* P, const double* u, const double* v,
                         double gamma, double scale, float* dC, cudaStream_t st);
+template <class T>
+void run_backward_points(eot_handle h, const eot_problem* P, const double* u, const double* v,
+                         double gamma, double scale, float* dX, float* dY, cudaStream_t st);
 
 }  // namespace eot

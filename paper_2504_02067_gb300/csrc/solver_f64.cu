@@ -15,4 +15,6 @@ template void run_backward_dense<double>(eot_handle, const eot_problem*, const d
                                         double, double, float*, cudaStream_t);
 template double run_sweep_bench<double>(eot_handle, const eot_problem*, const double*, const double*,
                                       double, int, int, cudaStream_t);
+template void run_backward_points<double>(eot_handle, const eot_problem*, const double*, const double*,
+                                           double, double, float*, float*, cudaStream_t);
 }  // namespace eot

@@ -308,4 +308,30 @@ void run_backward_dense(eot_handle h, const eot_problem* P, const double* u, con
   S.read();
 }
 
+// dX_i = scale 2 s_C sum_j P_ij (x_i - y_j), dY_j = scale 2 s_C sum_i P_ij (y_j - x_i)
+// at the potentials (u, v). Each side is swept with its own log-marginal as the
+// shift (Ah = u - log r(P) for dX, Bh = v - log c(P) for dY), so the FP32
+// exponents are <= 0 whatever the gauge of (u, v).
+template <class T>
+void run_backward_points(eot_handle h, const eot_problem* P, const double* u, const double* v,
+                         double gamma, double scale, float* dX, float* dY, cudaStream_t st) {
+  Solver<T> S(h, P, st);
+  EOT_CUDA(cudaMemsetAsync(h->status, 0, sizeof(int), st));
+  S.set_scalar(SC_GAMMA, round_gamma<T>(gamma));
+  const double f = scale * 2.0 * S.sC;
+  if (dX) {
+    S.row_lse(u, v, nullptr, h->logrP, h->rowmax, nullptr, SC_AUX0, SC_AUX1);
+    S.split_rows(u, nullptr, 0.0, h->logrP, h->Al, nullptr, h->rowfac, h->logrP);
+    S.split_cols(v, nullptr, 0.0, nullptr, h->Bl, S.ewc(), nullptr, nullptr);
+    S.template grad_pts<true>(f, h->rowfac, dX);
+  }
+  if (dY) {
+    S.col_lse(u, nullptr, v, nullptr, 0.0, nullptr, h->logcP, 0, SC_AUX0, 0.0);
+    S.split_rows(u, nullptr, 0.0, nullptr, h->Al, S.ewr(), nullptr, nullptr);
+    S.split_cols(v, nullptr, 0.0, h->logcP, h->Bl, nullptr, h->colfac, h->logcP);
+    S.template grad_pts<false>(f, h->colfac, dY);
+  }
+  S.read();
+}
+
 }  // namespace eot

@@ -240,6 +240,100 @@ __global__ void __launch_bounds__(kThreads, 2) pts_sweep_kernel(SweepArgs<T> a, 
   }
 }
 
+// Gradient of the EOT value with respect to the owned points (envelope theorem
+// on the Lagrangian of Appx. A, with s_C held constant):
+//     out_e,k = scale * ownfac_e * sum_o exp(h_e + h_o - K D_eo) w_o (x_ek - x_ok)
+// for the components k0 <= k < k0 + DG, where ownfac_e * exp(h_e + h_o - K D) w_o
+// = P_eo with the owned side shifted by its own log-marginal (so every exponent
+// is <= 0 up to the 1/8 grid). ROWS: own = rows (dX); else own = columns (dY).
+// grid = (own blocks of 256, S chunks of the other side); FP64 partials
+// [DG][S][n_own], last CTA of each own block adds them in fixed order.
+template <class T, int DMAX, int DG, bool ROWS, bool PRECISE>
+__global__ void __launch_bounds__(kThreads, DMAX > 16 ? 1 : 2)
+    pts_grad_kernel(SweepArgs<T> a, int k0, double scale, const double* ownfac, float* out) {
+  constexpr int TO = (DMAX * (int)sizeof(T) * 256 <= 16384) ? 256 : 16384 / (DMAX * (int)sizeof(T));
+  __shared__ T sy[DMAX][TO];
+  __shared__ T sh[TO];
+  __shared__ T sw[TO];
+  __shared__ int last_blk;
+
+  const int64_t n_own = ROWS ? a.n : a.m, n_oth = ROWS ? a.m : a.n;
+  const float* xo = ROWS ? a.X : a.Y;
+  const float* xt = ROWS ? a.Y : a.X;
+  const int d = a.d;
+  const int64_t blk = blockIdx.x, s = blockIdx.y, S = gridDim.y;
+  const int64_t j0 = s * a.chunk, j1 = min(n_oth, j0 + a.chunk);
+  pdl_wait();
+  const T* ho = ROWS ? a.Ah : a.Bh;
+  const T* ht = ROWS ? a.Bh : a.Ah;
+  const T* wt = ROWS ? a.wc[0] : a.wr[0];
+  const T g = a.gamma_dev ? (T)*a.gamma_dev : a.gamma;
+  T Kh, Kl;
+  split_k<T>((double)g * a.sC, Kh, Kl);
+
+  const int64_t e = blk * (int64_t)kThreads + threadIdx.x;
+  const bool ev = e < n_own;
+  const T h = ev ? ho[e] : T(0);
+  T x[DMAX], xg[DG];
+#pragma unroll
+  for (int k = 0; k < DMAX; ++k) x[k] = (ev && k < d) ? (T)xo[e * d + k] : T(0);
+#pragma unroll
+  for (int k = 0; k < DG; ++k) xg[k] = (ev && k0 + k < d) ? (T)xo[e * d + k0 + k] : T(0);
+  T Sa[DG], Ca[DG];
+#pragma unroll
+  for (int k = 0; k < DG; ++k) { Sa[k] = T(0); Ca[k] = T(0); }
+
+  for (int64_t jt = j0; jt < j1; jt += TO) {
+    const int tn = (int)min((int64_t)TO, j1 - jt);
+    __syncthreads();
+    for (int q = threadIdx.x; q < tn; q += kThreads) {
+      const int64_t j = jt + q;
+      sh[q] = ht[j];
+      sw[q] = wt[j];
+#pragma unroll
+      for (int k = 0; k < DMAX; ++k) sy[k][q] = k < d ? (T)xt[j * d + k] : T(0);
+    }
+    __syncthreads();
+    T acc[DG];
+#pragma unroll
+    for (int k = 0; k < DG; ++k) acc[k] = T(0);
+    for (int q = 0; q < tn; ++q) {
+      T Dh, Dl;
+      dist2<PRECISE, T, DMAX>(x, [&](int k) { return sy[k][q]; }, Dh, Dl);
+      const T pw = expT(expo<PRECISE>(h + sh[q], Kh, Kl, Dh, Dl)) * sw[q];
+#pragma unroll
+      for (int k = 0; k < DG; ++k) acc[k] = fmaT(pw, xg[k] - sy[k0 + k][q], acc[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < DG; ++k) kadd(Sa[k], Ca[k], acc[k]);
+  }
+  pdl_trigger();
+
+  if (ev) {
+#pragma unroll
+    for (int k = 0; k < DG; ++k) a.rowpart[((int64_t)k * S + s) * n_own + e] = (double)Sa[k] + (double)Ca[k];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last_blk = (atomicAdd(a.cnt_rowblk + blk, 1) == (int)S - 1);
+  }
+  __syncthreads();
+  if (!last_blk) return;
+  __threadfence();
+  if (ev) {
+    const double f = scale * ownfac[e];
+#pragma unroll
+    for (int k = 0; k < DG; ++k) {
+      if (k0 + k >= d) break;
+      double v = 0.0;
+      for (int64_t q = 0; q < S; ++q) v += __ldcg(a.rowpart + ((int64_t)k * S + q) * n_own + e);
+      out[e * d + k0 + k] = (float)(f * v);
+    }
+  }
+  if (threadIdx.x == 0) a.cnt_rowblk[blk] = 0;
+}
+
 // Largest squared distance max_ij |x_i - y_j|^2 (the cost normalisation of
 // Sec. 4.1 for point costs): each thread scans its rows against a tile of
 // columns in FP32, keeps its arg-max pair, re-evaluates that pair in FP64, and
