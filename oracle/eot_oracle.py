@@ -451,6 +451,20 @@ def mdot(C, r, c, gamma_i=2.0 ** 4, gamma_f=2.0 ** 12, p=1.5, q1=2.0, w_r=0.45,
     temperatures.
     """
     rg = round_gamma or (lambda g: g)
+    n, m = C.shape
+    if n == 1 or m == 1:
+        # Reading: with one row or one column U(r, c) = {r c^T}, and Alg. 1's
+        # tolerance eps_d = min(H(r), H(c)) / gamma^p is 0, which no finite-
+        # precision iteration meets. The potentials of r c^T at gamma_f are
+        # returned directly (a zero mass is clamped to 1e-300).
+        gf = rg(gamma_f)
+        lr = np.log(np.maximum(r, 1e-300))
+        lc = np.log(np.maximum(c, 1e-300))
+        if n == 1:
+            u, v = lr.copy(), lc + gf * C[0, :]
+        else:
+            u, v = lr + gf * C[:, 0], lc.copy()
+        return SolveResult(u, v, gf, 0, 0, 0, 0, 0, [], True)
     H = min(entropy(r), entropy(c))
     gamma_f = rg(gamma_f)
     gamma = rg(min(gamma_i, gamma_f))

@@ -451,3 +451,19 @@ def test_sqeuclid_scale_is_max():
     D = O.sqeuclid(X, Y)
     assert O.sqeuclid_scale(X, Y, block=64) == pytest.approx(1 / D.max(), rel=1e-15)
     np.testing.assert_allclose(O.sqeuclid_rows(X, Y, [3, 7]), D[[3, 7]], rtol=1e-15)
+
+
+@pytest.mark.parametrize("n,m", [(1, 7), (5, 1), (1, 1)])
+def test_mdot_single_row_or_column_is_product_plan(n, m):
+    """With one row or one column the transport polytope U(r, c) holds a single
+    plan, r c^T (every row of a one-column plan is forced to r_i, and vice
+    versa); the oracle must return potentials whose plan is exactly that."""
+    rng = np.random.default_rng(n * 10 + m)
+    C = rng.uniform(0, 1, size=(n, m))
+    r = rng.dirichlet(np.ones(n))
+    c = rng.dirichlet(np.ones(m))
+    res = O.mdot(C, r, c, gamma_i=16.0, gamma_f=4096.0)
+    P = O.plan(res.u, res.v, 4096.0, C)
+    assert res.ok
+    assert np.abs(P - np.outer(r, c)).max() <= 1e-12
+    assert O.marginal_l1_error(res.u, res.v, 4096.0, C, r, c) <= 1e-12
