@@ -357,11 +357,21 @@ def truncated_newton_project(u, v, gamma, C, r, c, eps, rho_last=0.0,
             st.rho_last = nres.rho
         if not nres.converged:
             st.ok = False
-        d_u = nres.d_u
+        # Reading: the direction is taken modulo the gauge (u + k 1, v - k 1 give
+        # the same P, Sec. 2.1): d_u <- d_u - k 1 with k = <r(P), d_u> / sum r(P).
+        # (d_u - k 1, d_v + k 1) moves P, g and every later iterate exactly as
+        # (d_u, d_v) does; a large k only costs precision in d_v = -P_c d_u.
+        d_u = nres.d_u - (rP @ nres.d_u) / rP.sum()
         d_v = -(P.T @ d_u) / col_sum(P)
         slope = float(-grad_u @ d_u)  # <-grad_u g, d_u>
+        # Reading: the test's left side is taken relative to its computed value at
+        # alpha = 0, which is 0 in exact arithmetic (c(P) = c after lines 1 / 15,
+        # sum c = 1); measuring it removes the rounding offset of sum P - 1, which
+        # near the final tolerance can exceed the sufficient decrease itself.
+        lhs0, _ = armijo_lhs(u, v, d_u, d_v, 0.0, gamma, C)
         alpha = 1.0
         lhs, log_cPa = armijo_lhs(u, v, d_u, d_v, alpha, gamma, C)
+        lhs -= lhs0
         st.ls_trials += 1
         while lhs > 0.99 * alpha * slope:
             alpha *= 0.5
@@ -369,6 +379,7 @@ def truncated_newton_project(u, v, gamma, C, r, c, eps, rho_last=0.0,
                 st.ok = False
                 break
             lhs, log_cPa = armijo_lhs(u, v, d_u, d_v, alpha, gamma, C)
+            lhs -= lhs0
             st.ls_trials += 1
         u = u + alpha * d_u
         v = v + alpha * d_v
