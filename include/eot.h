@@ -142,8 +142,9 @@ eot_status eot_hvp(eot_handle h, const eot_problem* prob, const double* u, const
 
 /* NewtonSolve (Alg. 2) at (u, v): anneal rho from rho0, solving F_r(rho) d_u =
  * -grad_u g with Jacobi-preconditioned CG from 0 to ||res||_1 <= (eta/4)||grad g||_1,
- * until ||F_r(1) d_u + grad_u g||_1 <= eta ||grad g||_1; then d_v = -P_c d_u (Eq.
- * bellman2 with Alg. 4 line 7). grad_u g = r(P) - r_target, ||grad g||_1 =
+ * until ||F_r(1) d_u + grad_u g||_1 <= eta ||grad g||_1; d_u is then taken
+ * modulo the gauge (d_u - k 1 with <r(P), d_u - k 1> = 0: the same plans, since
+ * F_r(1) 1 = 0 and P_c 1 = 1) and d_v = -P_c d_u (Eq. bellman2 with Alg. 4 line 7). grad_u g = r(P) - r_target, ||grad g||_1 =
  * ||grad_u g||_1 (assumes c(P) = c, as Alg. 4 maintains).
  * r_target: device [n]. du_out: device [n]; dv_out: device [m] (nullable).
  * rho_out, cg_iters_out: host, nullable (rho of the last CG solve, Appx. B).
@@ -159,6 +160,33 @@ eot_status eot_newton_solve(eot_handle h, const eot_problem* prob, const double*
  * stats: host, nullable. Errors: any. Synchronises. */
 eot_status eot_solve(eot_handle h, const eot_problem* prob, const eot_params* params, double* u,
                      double* v, eot_stats* stats, void* stream);
+
+/* Many point-cloud problems in ONE persistent kernel launch (the batching
+ * regime: problems of uneven size solved together). Each problem runs the same
+ * method as eot_solve (Alg. 1 with Alg. 4, Alg. 3 and Alg. 2) on the device,
+ * with no host round trip: a cooperative launch of all co-resident CTAs, formed
+ * into groups of G CTAs that take problems from a queue, largest n m first.
+ * G and the own elements per thread are chosen by an autotuner that times
+ * probe sweeps of the actual batch (once per batch shape, cached in the
+ * handle; EOT_BATCH_CFG="G,k" in the environment forces G in {1,2,4,8} and
+ * k in {1,2,4}).
+ * probs: host array [nprob]; every problem EOT_COST_SQEUCLID_POINTS with
+ *   1 <= d <= 4, 1 <= n, m <= 32768, all MIXED or all FP64; r, c, X, Y device.
+ *   cost_scale <= 0: s_C = 1 / max |x_i - y_j|^2 computed per problem.
+ * u, v: host arrays [nprob] of device pointers to the outputs ([n_k], [m_k]).
+ * status_out: host [nprob], nullable: each problem's eot_status.
+ * stats: host [nprob], nullable (sweeps_total only among the sweep counters;
+ *   seconds = the whole call).
+ * Returns EOT_OK when every problem succeeded, else the status of the first
+ * failing problem (in input order); a failure of the launch itself (a group
+ * barrier wait bounded at 2 s ran out) returns EOT_ERR_CUDA. Synchronises. */
+eot_status eot_solve_batched(eot_handle h, int32_t nprob, const eot_problem* probs,
+                             const eot_params* params, double* const* u, double* const* v,
+                             int32_t* status_out, eot_stats* stats, void* stream);
+
+/* The configuration of the last batched launch: out3[0] = G (CTAs per group),
+ * out3[1] = own elements per thread and round, out3[2] = groups. Host pointer. */
+eot_status eot_batch_last_config(eot_handle h, int32_t* out3);
 
 /* Gradients of the EOT value F* = <P*, C> - H(P*) / gamma at the potentials (u, v)
  * (envelope theorem on the Lagrangian, Appx. A; not stated in the paper):

@@ -56,7 +56,8 @@ class EotStats(ctypes.Structure):
 
 EXPORTS = ["eot_create", "eot_destroy", "eot_last_error", "eot_status_string",
            "eot_params_default", "eot_marginals", "eot_hvp", "eot_newton_solve", "eot_solve",
-           "eot_backward", "eot_sweep_bench", "eot_marginals_noalloc", "eot_kernel_launches"]
+           "eot_backward", "eot_sweep_bench", "eot_marginals_noalloc", "eot_kernel_launches",
+           "eot_solve_batched", "eot_batch_last_config"]
 
 _LIB = None
 
@@ -89,10 +90,15 @@ def load_library(path=None):
     L.eot_sweep_bench.argtypes = [vp, P, vp, vp, dbl, i32, i32, ctypes.POINTER(dbl), vp]
     L.eot_marginals_noalloc.argtypes = [P, vp, vp, dbl, vp, vp, vp, vp]
     L.eot_marginals_noalloc.restype = ctypes.c_int
+    L.eot_solve_batched.argtypes = [vp, i32, P, ctypes.POINTER(EotParams), ctypes.POINTER(vp),
+                                    ctypes.POINTER(vp), ctypes.POINTER(i32), ctypes.POINTER(EotStats),
+                                    vp]
+    L.eot_batch_last_config.argtypes = [vp, ctypes.POINTER(i32)]
+    L.eot_batch_last_config.restype = ctypes.c_int
     L.eot_kernel_launches.argtypes = [vp]
     L.eot_kernel_launches.restype = i64
     for f in ("eot_create", "eot_destroy", "eot_marginals", "eot_hvp", "eot_newton_solve",
-              "eot_solve", "eot_backward", "eot_sweep_bench"):
+              "eot_solve", "eot_backward", "eot_sweep_bench", "eot_solve_batched"):
         getattr(L, f).restype = ctypes.c_int
     if path == _build.LIBPATH:
         _LIB = L
@@ -221,6 +227,26 @@ class Handle:
                                             _stream(stream)))
         return ms.value
 
+    def eot_solve_batched(self, probs, params, us, vs, stream=None):
+        """probs: list of point Problems; us, vs: lists of output tensors. Returns
+        (per-problem status list, per-problem stats dicts); raises on a failed launch."""
+        k = len(probs)
+        arr = (EotProblem * k)(*[p.struct for p in probs])
+        up = (ctypes.c_void_p * k)(*[u.data_ptr() for u in us])
+        vq = (ctypes.c_void_p * k)(*[v.data_ptr() for v in vs])
+        st = (ctypes.c_int32 * k)(*([-1] * k))
+        stats = (EotStats * k)()
+        rc = self.lib.eot_solve_batched(self.h, k, arr, ctypes.byref(params), up, vq, st, stats,
+                                        _stream(stream))
+        if rc != EOT_OK and (rc == 8 or all(x == -1 for x in st)):
+            self.check(rc)  # the batch did not run (bad arguments) or its launch failed
+        return [int(x) for x in st], [s.as_dict() for s in stats]
+
+    def batch_last_config(self):
+        out = (ctypes.c_int32 * 3)()
+        self.check(self.lib.eot_batch_last_config(self.h, out))
+        return tuple(int(x) for x in out)
+
     # ---- conveniences that allocate the outputs ----
     def marginals(self, prob, u, v, gamma):
         dev = u.device
@@ -252,6 +278,17 @@ class Handle:
         v = torch.empty(prob.m, dtype=torch.float64, device=dev)
         stats = self.eot_solve(prob, p, u, v)
         return u, v, stats.as_dict()
+
+
+def solve_batched(handle, probs, params=None, **overrides):
+    """Solve a list of point Problems in one launch; returns (us, vs, statuses, stats)."""
+    p = params or default_params()
+    for k, val in overrides.items():
+        setattr(p, k, val)
+    us = [torch.empty(q.n, dtype=torch.float64, device=q.r.device) for q in probs]
+    vs = [torch.empty(q.m, dtype=torch.float64, device=q.r.device) for q in probs]
+    st, stats = handle.eot_solve_batched(probs, p, us, vs)
+    return us, vs, st, stats
 
 
 def default_params(**overrides):

@@ -9,6 +9,7 @@
 // gamma * C_ij is formed inside one FMA (exact product, one rounding), so the
 // only FP32 error of t_ij is a single rounding relative to |t_ij|.
 #pragma once
+#include <cmath>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -20,6 +21,12 @@ constexpr int kColCtasPerSm = 2;     // resident column-sweep CTAs per SM (regis
 constexpr double kGrid = 0.125;      // split grid of the high parts
 constexpr double kSplitLimit = 524288.0;  // |A|, |B| < 2^19 keeps Ah + Bh exact in FP32
 constexpr float kLog2e = 1.4426950408889634f;
+// Rounding floor of sum P - 1 evaluated with FP32 plan entries: each marginal
+// entry errs by up to about 2^-22 relative (ex2.approx), and these errors add
+// with random signs over the max(n, m) entries of the marginal.
+inline double armijo_floor32(int64_t n, int64_t m) {
+  return (1.0 / 4194304.0) / std::sqrt((double)(n > m ? n : m));
+}
 constexpr float kTheta = 8.0f;       // lazy-rescale threshold of the online max
 constexpr float kLow = 32.0f;        // an empty LSE accumulator re-centres below -kLow
 
@@ -101,8 +108,9 @@ __device__ __forceinline__ void ld_vec(const T* p, T (&c)[V]) {
 // sums of the sweeps accurate to about one rounding without FP64 instructions in
 // the inner loops (the FP64 pipe of this GPU is narrow); in FP64 it is a plain add.
 __device__ __forceinline__ void kadd(float& s, float& c, float x) {
-  const float t = s + x;
-  c += (fabsf(s) >= fabsf(x)) ? ((s - t) + x) : ((x - t) + s);
+  // __fadd_rn / __fsub_rn: never contracted with a product that formed x
+  const float t = __fadd_rn(s, x);
+  c += (fabsf(s) >= fabsf(x)) ? __fadd_rn(__fsub_rn(s, t), x) : __fadd_rn(__fsub_rn(x, t), s);
   s = t;
 }
 __device__ __forceinline__ void kadd(double& s, double& c, double x) { s += x; }

@@ -188,6 +188,7 @@ eot_status eot_destroy(eot_handle h) {
   cudaSetDevice(h->device);
   cudaDeviceSynchronize();
   free_all(h);
+  if (h->bt_mem) cudaFree(h->bt_mem);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   delete h;
   return EOT_OK;

@@ -76,6 +76,13 @@ struct eot_handle_s {
 
   std::map<CgKey, CgGraph> graphs;
   cudaStream_t cap_stream = nullptr;
+
+  // eot_solve_batched: its own device block (not in `allocs`: growing the
+  // single-problem buffers must not free it) and the autotuner's choices
+  void* bt_mem = nullptr;
+  size_t bt_bytes = 0;
+  std::map<std::string, std::pair<int, int>> bt_tune;  // batch shape -> (G, elements per thread)
+  int bt_last[3] = {0, 0, 0};                          // G, elements per thread, groups of the last launch
 };
 
 namespace eot {

@@ -12,6 +12,7 @@ namespace eot {
 enum Sc : int {
   SC_RZ = 0, SC_PQ, SC_ALPHA, SC_BETA, SC_RESL1, SC_TOL, SC_RHO, SC_ITERS, SC_ACTIVE, SC_MAXIT,
   SC_CHECK, SC_GL1, SC_CHI2, SC_LHS, SC_SLOPE, SC_MASS, SC_CHK, SC_GAMMA, SC_AUX0, SC_AUX1,
+  SC_GRD, SC_GMASS,  // <r(P), d_u> and sum r(P): the gauge component of d_u
   SC_COUNT = 32
 };
 
@@ -422,17 +423,35 @@ static __global__ void cg_check_kernel(int64_t n, const double* res, const doubl
   vec_finish<1>(v, dotpart, cnt, f);
 }
 
-// Row weights rowfac * d_u of the d_v sweep and the Armijo slope <-grad_u g, d_u>
-// = <r~ - r(P), d_u>.
-template <class T>
-__global__ void prep_dv_kernel(int64_t n, const double* du, const double* rowfac, const double* rt,
-                               const double* rP, T* xw, double* sc, double* dotpart, int* cnt) {
+// Gauge component of d_u: <r(P), d_u> and sum r(P) into SC_GRD, SC_GMASS.
+static __global__ void gauge_kernel(int64_t n, const double* du, const double* rP, double* sc,
+                                    double* dotpart, int* cnt) {
   pdl_wait();
   double v[2] = {0.0, 0.0};
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    xw[i] = (T)(rowfac[i] * du[i]);
-    v[0] += (rt[i] - rP[i]) * du[i];
+    v[0] += rP[i] * du[i];
+    v[1] += rP[i];
+  }
+  SlotFinish f{sc, SC_GRD, SC_GMASS, 0.0, 0.0};
+  vec_finish<2>(v, dotpart, cnt, f);
+}
+
+// d_u <- d_u - k 1 with k = <r(P), d_u> / sum r(P) (the direction modulo the gauge:
+// (d_u - k 1, d_v + k 1) gives the same plans), then the row weights rowfac * d_u
+// of the d_v sweep and the Armijo slope <-grad_u g, d_u> = <r~ - r(P), d_u>.
+template <class T>
+__global__ void prep_dv_kernel(int64_t n, double* du, const double* rowfac, const double* rt,
+                               const double* rP, T* xw, double* sc, double* dotpart, int* cnt) {
+  pdl_wait();
+  const double kap = sc[SC_GRD] / sc[SC_GMASS];
+  double v[2] = {0.0, 0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double d = du[i] - kap;
+    du[i] = d;
+    xw[i] = (T)(rowfac[i] * d);
+    v[0] += (rt[i] - rP[i]) * d;
   }
   SlotFinish f{sc, SC_SLOPE, -1, 0.0, 0.0};
   vec_finish<1>(v, dotpart, cnt, f);
@@ -495,6 +514,40 @@ __global__ void weight_kernel(int64_t n, const double* f, const double* x, T* ou
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     out[i] = (T)(f[i] * (x ? x[i] : 1.0));
+}
+
+// One row or one column: U(r, c) = {r c^T}, whose potentials at gamma are
+// u = log r, v_j = log c_j + gamma C_0j (n = 1), or v = log c,
+// u_i = log r_i + gamma C_i0 (m = 1); zero masses are clamped to 1e-300.
+// C from the dense cost (Cd, ld ldc) or from points (X, Y, d, s_C) in FP64.
+template <class T>
+__global__ void closed_form_kernel(int64_t n, int64_t m, const double* r, const double* c,
+                                   double gamma, const T* Cd, int64_t ldc, const float* X,
+                                   const float* Y, int d, double sC, double* u, double* v) {
+  pdl_wait();
+  const int64_t L = n == 1 ? m : n;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < L;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = n == 1 ? 0 : k, j = n == 1 ? k : 0;
+    double C;
+    if (Cd) {
+      C = (double)Cd[i * ldc + j];
+    } else {
+      double D = 0.0;
+      for (int q = 0; q < d; ++q) {
+        const double df = (double)X[i * d + q] - (double)Y[j * d + q];
+        D += df * df;
+      }
+      C = sC * D;
+    }
+    if (n == 1) {
+      v[j] = log(fmax(c[j], 1e-300)) + gamma * C;
+      if (k == 0) u[0] = log(fmax(r[0], 1e-300));
+    } else {
+      u[i] = log(fmax(r[i], 1e-300)) + gamma * C;
+      if (k == 0) v[0] = log(fmax(c[0], 1e-300));
+    }
+  }
 }
 
 // dC_ij = scale * P_ij written densely (ld ldo), P_ij = rowfac_i colfac_j exp(Ah_i + Bh_j - gamma C_ij).

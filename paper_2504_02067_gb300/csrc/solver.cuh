@@ -405,7 +405,11 @@ struct Solver {
       }
     }
     if (du_final != h->du) copy(h->du, du_final, n);
-    // d_v = -(P^T d_u) / c(P) and the Armijo slope <r~ - r(P), d_u>
+    // d_u modulo the gauge, d_v = -(P^T d_u) / c(P) and the Armijo slope <r~ - r(P), d_u>
+    launch_k(gauge_kernel, dim3(vg_n), dim3(kThreads), st, n, (const double*)h->du, (const double*)h->rP,
+             h->sc, h->dotpart, h->cnt_dot);
+    EOT_LAUNCH_CHECK();
+    h->launches++;
     launch_k(prep_dv_kernel<T>, dim3(vg_n), dim3(kThreads), st, n, h->du, h->rowfac, rt, h->rP, xw0(), h->sc,
                                                  h->dotpart, h->cnt_dot);
     EOT_LAUNCH_CHECK();
@@ -557,8 +561,23 @@ struct Solver {
       const double rho = newton(u, v, rt, gl1, eta, rho0, max_cg, mode, &ran);
       if (ran) cnt.rho_last = rho;
       cnt.newton_steps++;
-      // lines 8-13: backtracking on the simplified Armijo test
+      // lines 8-13: backtracking on the simplified Armijo test, whose left side
+      // (sum P(alpha) - 1) is taken relative to its computed value at alpha = 0
+      // (0 in exact arithmetic, since c(P) = c~): this removes the rounding
+      // offset of the mass, which near the final tolerance can exceed the
+      // sufficient decrease itself
       sweep_bucket = &cnt.sweeps_ls;
+      // With FP32 plan entries sum P(alpha) carries a rounding floor (about
+      // 2^-22 / sqrt(max(n, m))); when the whole decrease the test asks for at
+      // alpha = 1 is below it
+      // the test cannot decide, and the unit step (accepted near the solution,
+      // Sec. 3) is taken. Trials outside the split range are still rejected.
+      const bool decidable = sizeof(T) == 8 || 0.99 * read()[SC_SLOPE] >= armijo_floor32(n, m);
+      double lhs0 = 0.0;
+      if (decidable) {
+        col_lse(u, h->du, v, h->dv, 0.0, logct, h->logcP, 0, SC_LHS, 1.0);
+        lhs0 = read()[SC_LHS];
+      }
       double alpha = 1.0;
       int trials = 0;
       for (;;) {
@@ -571,7 +590,10 @@ struct Solver {
         if (out_of_range) clear_status();
         s = read();
         cnt.ls_trials++;
-        if (!out_of_range && s[SC_LHS] <= 0.99 * alpha * s[SC_SLOPE]) break;
+        if (trace)
+          std::fprintf(stderr, "[eot]   trial alpha %.4g lhs %.6e lhs0 %.6e slope %.6e range %d\n", alpha,
+                       s[SC_LHS], lhs0, s[SC_SLOPE], out_of_range ? 1 : 0);
+        if (!out_of_range && (!decidable || s[SC_LHS] - lhs0 <= 0.99 * alpha * s[SC_SLOPE])) break;
         if (++trials > prm.max_ls) throw EotError{EOT_ERR_LINESEARCH, "Armijo backtracking exhausted"};
         alpha *= 0.5;
       }
@@ -586,9 +608,9 @@ struct Solver {
       chi2 = s[SC_CHI2];
       const double delta = (gl1 - new_gl1) / ((1.0 - eta) * gl1);
       if (trace)
-        std::fprintf(stderr, "[eot] gamma %.6g step %d grad %.3e -> %.3e eta %.3e alpha %.4g rho %.9f cg %lld curv %lld sk %lld\n",
+        std::fprintf(stderr, "[eot] gamma %.6g step %d grad %.3e -> %.3e eta %.3e alpha %.4g rho %.9f cg %lld curv %lld sk %lld decidable %d\n",
                      gamma_host, steps, gl1, new_gl1, eta, alpha, cnt.rho_last, (long long)cnt.cg_iters,
-                     (long long)cnt.curvature_stops, (long long)cnt.sk_iters);
+                     (long long)cnt.curvature_stops, (long long)cnt.sk_iters, decidable ? 1 : 0);
       if (delta < *delta_min) *delta_min = delta;
       gl1 = new_gl1;
       steps++;

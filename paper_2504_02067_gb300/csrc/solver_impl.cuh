@@ -158,7 +158,17 @@ void run_solve(eot_handle h, const eot_problem* P, const eot_params* prm_in, dou
   double gamma_prev = 0.0, q = prm.q1, gl1 = 0.0;
   const double w_c = 0.5 - prm.w_r;
   int t = 1;
-  for (;;) {
+  if (n == 1 || m == 1) {
+    // one row or one column: U(r, c) is the single plan r c^T and eps_d of Alg. 1
+    // (min(H(r), H(c)) / gamma^p) is 0; return its potentials directly
+    launch_k(closed_form_kernel<T>, dim3(std::max(S.vg_n, S.vg_m)), dim3(kThreads), st, n, m, P->r, P->c,
+             gamma_f, S.points ? (const T*)nullptr : S.C, P->ldc, S.X, S.Y, (int)S.d, S.sC, u, v);
+    EOT_LAUNCH_CHECK();
+    h->launches++;
+    gamma = gamma_f;
+    t = 0;
+  }
+  for (; t > 0;) {
     const bool done = gamma == gamma_f;
     double eps_d = H / std::pow(gamma, prm.p);
     if (done) eps_d = std::min(eps_d, 2.0 * prm.tol_final / 3.0);

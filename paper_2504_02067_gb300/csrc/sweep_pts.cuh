@@ -18,6 +18,11 @@
 
 namespace eot {
 
+// FP32 terms summed plainly before each compensated (Neumaier) flush: a plain
+// FP32 sum of k positive terms is off by up to ~k 2^-24 relative, which at k = 256
+// is already the 1e-6 scale of the marginal tolerance.
+constexpr int kPtsFlush = 16;
+
 template <class T>
 __device__ __forceinline__ void split_k(double K, T& hi, T& lo) {
   hi = (T)K;
@@ -29,6 +34,15 @@ __device__ __forceinline__ void split_k(double K, T& hi, T& lo) {
 // error term) and the accumulation compensated, so Dh + Dl carries D to about
 // 2^-44 relative: the product K D can reach hundreds and the exponent needs it
 // to ~1e-8. Without PRECISE (plain FP32, and FP64 where it is not needed) Dl = 0.
+// Round-to-nearest add / multiply that the compiler never contracts into an
+// FMA: the error-free transformations below need every rounding where written.
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
 template <bool PRECISE, class T, int DMAX, class YGet>
 __device__ __forceinline__ void dist2(const T (&x)[DMAX], YGet yk, T& Dh, T& Dl) {
   Dh = T(0);
@@ -36,19 +50,20 @@ __device__ __forceinline__ void dist2(const T (&x)[DMAX], YGet yk, T& Dh, T& Dl)
 #pragma unroll
   for (int k = 0; k < DMAX; ++k) {
     const T y = yk(k);
-    const T sd = x[k] - y;
     if constexpr (!PRECISE) {
+      const T sd = x[k] - y;
       Dh = fmaT(sd, sd, Dh);
     } else {
-      const T bv = sd - x[k];
-      const T e = (x[k] - (sd - bv)) - (y + bv);
-      const T p = sd * sd;
+      const T sd = sub_rn(x[k], y);                                  // TwoSum: x - y = sd + e
+      const T bv = sub_rn(sd, x[k]);
+      const T e = sub_rn(sub_rn(x[k], sub_rn(sd, bv)), add_rn(y, bv));
+      const T p = mul_rn(sd, sd);                                    // TwoProduct: sd^2 = p + pe
       const T pe = fmaT(sd, sd, -p);
-      const T t = Dh + p;
-      const T z = t - Dh;
-      const T err = (Dh - (t - z)) + (p - z);
+      const T t = add_rn(Dh, p);                                     // TwoSum: Dh + p = t + err
+      const T z = sub_rn(t, Dh);
+      const T err = add_rn(sub_rn(Dh, sub_rn(t, z)), sub_rn(p, z));
       Dh = t;
-      Dl += err + fmaT(sd + sd, e, pe);
+      Dl += err + fmaT(sd + sd, e, pe);                              // (sd + e)^2 - sd^2 to first order
     }
   }
 }
@@ -124,13 +139,15 @@ __global__ void __launch_bounds__(kThreads, 2) pts_sweep_kernel(SweepArgs<T> a, 
       for (int k = 0; k < DMAX; ++k) sy[k][q] = k < d ? (T)xt[j * d + k] : T(0);
     }
     __syncthreads();
+    for (int q0 = 0; q0 < tn; q0 += kPtsFlush) {
+    const int q1 = min(tn, q0 + kPtsFlush);
     T acc[RO][NA];
 #pragma unroll
     for (int r = 0; r < RO; ++r)
 #pragma unroll
       for (int k = 0; k < NA; ++k) acc[r][k] = T(0);
 #pragma unroll 2
-    for (int q = 0; q < tn; ++q) {
+    for (int q = q0; q < q1; ++q) {
       constexpr bool YREG = DMAX <= 16;  // keep the other point in registers for small d
       T y[YREG ? DMAX : 1];
       if constexpr (YREG) {
@@ -179,6 +196,7 @@ __global__ void __launch_bounds__(kThreads, 2) pts_sweep_kernel(SweepArgs<T> a, 
     for (int r = 0; r < RO; ++r)
 #pragma unroll
       for (int k = 0; k < NA; ++k) kadd(Sa[r][k], Ca[r][k], acc[r][k]);
+    }
   }
   pdl_trigger();
 
@@ -294,18 +312,21 @@ __global__ void __launch_bounds__(kThreads, DMAX > 16 ? 1 : 2)
       for (int k = 0; k < DMAX; ++k) sy[k][q] = k < d ? (T)xt[j * d + k] : T(0);
     }
     __syncthreads();
-    T acc[DG];
+    for (int q0 = 0; q0 < tn; q0 += kPtsFlush) {
+      const int q1 = min(tn, q0 + kPtsFlush);
+      T acc[DG];
 #pragma unroll
-    for (int k = 0; k < DG; ++k) acc[k] = T(0);
-    for (int q = 0; q < tn; ++q) {
-      T Dh, Dl;
-      dist2<PRECISE, T, DMAX>(x, [&](int k) { return sy[k][q]; }, Dh, Dl);
-      const T pw = expT(expo<PRECISE>(h + sh[q], Kh, Kl, Dh, Dl)) * sw[q];
+      for (int k = 0; k < DG; ++k) acc[k] = T(0);
+      for (int q = q0; q < q1; ++q) {
+        T Dh, Dl;
+        dist2<PRECISE, T, DMAX>(x, [&](int k) { return sy[k][q]; }, Dh, Dl);
+        const T pw = expT(expo<PRECISE>(h + sh[q], Kh, Kl, Dh, Dl)) * sw[q];
 #pragma unroll
-      for (int k = 0; k < DG; ++k) acc[k] = fmaT(pw, xg[k] - sy[k0 + k][q], acc[k]);
+        for (int k = 0; k < DG; ++k) acc[k] = fmaT(pw, xg[k] - sy[k0 + k][q], acc[k]);
+      }
+#pragma unroll
+      for (int k = 0; k < DG; ++k) kadd(Sa[k], Ca[k], acc[k]);
     }
-#pragma unroll
-    for (int k = 0; k < DG; ++k) kadd(Sa[k], Ca[k], acc[k]);
   }
   pdl_trigger();
 
