@@ -391,6 +391,196 @@ def run_reference(args):
     return out
 
 
+# ---------------------------------------------------------------------------
+# further workloads (parity-test configurations; each prints its own JSON line)
+# ---------------------------------------------------------------------------
+
+MUFU_PER_CLK_SM = 16     # ex2 results per clock per SM (4 per SM sub-partition)
+FP32_LANES_SM = 128      # FP32 lanes per SM
+
+
+def _gpu_props(dev):
+    import torch
+    pr = torch.cuda.get_device_properties(dev)
+    return pr.multi_processor_count
+
+
+def _point_problem_tensors(p, dev):
+    import torch
+    hs = {k: torch.from_numpy(p[k]).pin_memory() for k in ("X", "Y", "r", "c")}
+    ds = {k: v.to(dev) for k, v in hs.items()}
+    return hs, ds
+
+
+def _sweep_rates(h, E, prob, u, v, gamma, n, m, sms, kinds=((0, "cg_col_sweep"), (1, "cg_row_sweep"),
+                                                             (3, "row_lse_sweep")), iters=3):
+    out = {}
+    for kind, name in kinds:
+        ms = h.eot_sweep_bench(prob, u, v, gamma, kind, iters)
+        ent = n * m / (ms * 1e-3)
+        out[name] = {"ms": round(ms, 3), "p_entries_per_s": round(ent, 1),
+                     "ex2_frac_of_mufu_peak": round(ent / (sms * MUFU_PER_CLK_SM * 2.07e9), 4)}
+    return out
+
+
+def run_batch256(args):
+    """256 point problems (n = m uniform in [256, 4096], points uniform in the unit
+    square, Dirichlet(1) weights, squared-Euclidean cost normalised per problem),
+    gamma 2^4 -> 2^12, mixed precision, tol 1e-6, one eot_solve_batched call per
+    step. value = seconds for the whole batch."""
+    import numpy as np
+    import torch
+
+    import paper_2504_02067_gb300 as E
+    import workloads as W
+    E.build()
+    dev = torch.device("cuda", 0)
+    sizes = W.batch_sizes(0)
+    ps = [W.uniform_points_problem(1000 + k, int(nk)) for k, nk in enumerate(sizes)]
+    host, devs = zip(*[_point_problem_tensors(p, dev) for p in ps])
+    probs = [E.Problem(X=d["X"], Y=d["Y"], r=d["r"], c=d["c"], precision="mixed", cost_scale=0.0)
+             for d in devs]
+    us = [torch.empty(int(nk), dtype=torch.float64, device=dev) for nk in sizes]
+    vs = [torch.empty(int(nk), dtype=torch.float64, device=dev) for nk in sizes]
+    h = E.Handle(0, 64, 64)
+    prm = E.default_params(gamma_i=16.0, gamma_f=4096.0, tol_final=TOL)
+    t0 = time.perf_counter()
+    for _ in range(args.warmup):
+        st, stats = h.eot_solve_batched(probs, prm, us, vs)
+    tune_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    sampler = ClockSampler(0)
+    torch.cuda.synchronize()
+    l0 = h.launches()
+    sampler.start()
+    times = []
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st, stats = h.eot_solve_batched(probs, prm, us, vs)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    clocks = sampler.stop()
+    launches = h.launches() - l0
+    sec = sum(times) / len(times)
+    entries = sum(s["sweeps_total"] * int(nk) * int(nk) for s, nk in zip(stats, sizes))
+    # end to end: inputs from pinned host memory, potentials back
+    uh = [torch.empty(int(nk), dtype=torch.float64).pin_memory() for nk in sizes]
+    vh = [torch.empty(int(nk), dtype=torch.float64).pin_memory() for nk in sizes]
+    e_times = []
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for hh, dd in zip(host, devs):
+            for k in ("X", "Y", "r", "c"):
+                dd[k].copy_(hh[k], non_blocking=True)
+        h.eot_solve_batched(probs, prm, us, vs)
+        for a, b in zip(uh + vh, us + vs):
+            a.copy_(b, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e_times.append(e0.elapsed_time(e1) / 1e3)
+    h2d = sum(sum(t.numel() * t.element_size() for t in hh.values()) for hh in host)
+    d2h = sum(t.numel() * 8 for t in uh + vh)
+    G, ro, groups = h.batch_last_config()
+    cpu = None
+    if not args.no_cpu_baseline:
+        # the oracle's full solve of the smallest problems, scaled by sum n_k m_k
+        from oracle import eot_oracle as O
+        order = np.argsort(sizes)
+        t0 = time.perf_counter()
+        done, work = 0, 0
+        while done < 3 and time.perf_counter() - t0 < args.cpu_seconds:
+            p = ps[order[done]]
+            C64 = O.sqeuclid_scale(p["X"], p["Y"]) * O.sqeuclid(p["X"], p["Y"])
+            O.mdot(C64, p["r"], p["c"], gamma_i=16.0, gamma_f=4096.0, tol_final=TOL)
+            work += int(sizes[order[done]]) ** 2
+            done += 1
+        dt = time.perf_counter() - t0
+        total_work = int(np.sum(sizes.astype(np.int64) ** 2))
+        cpu = {"value": round(dt * total_work / work, 1), "unit": "s", "cores": os.cpu_count(),
+               "kind": "oracle",
+               "sample": "oracle MDOT of the %d smallest problems (n = %s) in %.1f s, scaled by "
+                         "sum n_k^2 of the batch" % (done, [int(sizes[i]) for i in order[:done]], dt)}
+    out = {"metric": METRIC, "value": round(sec, 4), "unit": "s", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(sec * 1e3, 2), "higher_is_better": False,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32 exp/sums on f64 potentials (mixed)",
+           "data": "synthetic",
+           "config": {"workload": "batch256_uniform2d_n256-4096_gamma2^12", "problems": len(ps),
+                      "sum_n2": int(np.sum(sizes.astype(np.int64) ** 2)), "gamma_f": 4096.0,
+                      "tol": TOL, "parallelism": "single", "l2": "inputs < L2; not flushed"},
+           "all_ok": all(x == 0 for x in st), "max_marg_err_l1": max(s["marg_err_l1"] for s in stats),
+           "p_entries_per_s": round(entries / sec, 1), "first_call_incl_autotune_s": round(tune_s, 3),
+           "batch_config": {"ctas_per_group": G, "elements_per_thread": ro, "groups": groups},
+           "e2e": {"value": round(sum(e_times) / len(e_times), 4), "unit": "s",
+                   "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+           "gpu_launches": int(launches), "cpu_baseline": cpu, "clocks": clocks}
+    print(json.dumps(out), flush=True)
+    h.close()
+    return out
+
+
+def run_points_workload(args, kind):
+    """d64: n = m = 16384 points in d = 64 (8-component Gaussian mixtures), gamma
+    2^4 -> 2^10, mixed, tol 1e-6: one solve per step plus sweep rates.
+    colour: n = m = 2^20 RGB points (d = 3, 16-component mixtures), sweep rates of
+    the CG halves and the row LSE at gamma 2^10 (a full solve is out of the bench's
+    time budget)."""
+    import numpy as np
+    import torch
+
+    import paper_2504_02067_gb300 as E
+    import workloads as W
+    E.build()
+    dev = torch.device("cuda", 0)
+    sms = _gpu_props(dev)
+    p = W.gmm_problem_d64(0) if kind == "d64" else W.colour_problem(0)
+    n = p["X"].shape[0]
+    hs, ds = _point_problem_tensors(p, dev)
+    h = E.Handle(0, 64, 64)
+    prob = E.Problem(X=ds["X"], Y=ds["Y"], r=ds["r"], c=ds["c"], precision="mixed", cost_scale=0.0)
+    gf = 1024.0
+    rng = np.random.default_rng(0)
+    u = torch.from_numpy(np.full(n, -np.log(n)) + rng.normal(0, 0.1, n)).to(dev)
+    v = torch.from_numpy(np.full(n, -np.log(n))).to(dev)
+    rates = _sweep_rates(h, E, prob, u, v, gf, n, n, sms, iters=2 if kind == "colour" else 5)
+    out = {"metric": METRIC, "unit": "s", "n_gpus": 1, "higher_is_better": False, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32 exp/sums on f64 potentials (mixed)", "data": "synthetic",
+           "sweeps": rates}
+    if kind == "d64":
+        prm = E.default_params(gamma_i=16.0, gamma_f=gf, tol_final=TOL)
+        uu = torch.empty(n, dtype=torch.float64, device=dev)
+        vv = torch.empty(n, dtype=torch.float64, device=dev)
+        for _ in range(min(args.warmup, 1)):
+            h.eot_solve(prob, prm, uu, vv)
+        sampler = ClockSampler(0)
+        sampler.start()
+        times = []
+        for _ in range(max(1, min(args.steps, 2))):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            st = h.eot_solve(prob, prm, uu, vv).as_dict()
+            e1.record()
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+        out["clocks"] = sampler.stop()
+        sec = sum(times) / len(times)
+        out.update({"value": round(sec, 3), "ms_per_step": round(sec * 1e3, 1), "steps": len(times),
+                    "marg_err_l1": st["marg_err_l1"],
+                    "solve_stats": {k: st[k] for k in ("stages", "newton_steps", "cg_iters", "ls_trials",
+                                                       "sweeps_total")},
+                    "p_entries_per_s": round(st["sweeps_total"] * n * n / sec, 1),
+                    "config": {"workload": "gmm8_d64_n16384_gamma2^10", "n": n, "d": 64,
+                               "gamma_f": gf, "tol": TOL}})
+    else:
+        out.update({"value": None, "config": {"workload": "rgb_gmm16_d3_n2^20_gamma2^10", "n": n,
+                                               "d": 3, "gamma": gf}})
+    print(json.dumps(out), flush=True)
+    h.close()
+    return out
+
+
 def run_profile_sweep(args):
     """A few launches of one sweep kernel on the full-size workload (for ncu):
     the set-up launches come first (one row LSE, the Newton-step column and row
@@ -430,9 +620,17 @@ def main():
     ap.add_argument("--profile-sweep", type=int, default=-1,
                     help="run only eot_sweep_bench of this kind (0 CG column, 1 CG row, 2 HVP, 3 row LSE)")
     ap.add_argument("--profile-iters", type=int, default=3)
+    ap.add_argument("--workload", default="grid4096", choices=["grid4096", "batch256", "d64", "colour"],
+                    help="grid4096 = the headline line; the others print their own lines")
     args = ap.parse_args()
     if args.profile_sweep >= 0:
         run_profile_sweep(args)
+        return
+    if args.workload != "grid4096" and args.impl == "ours":
+        if args.workload == "batch256":
+            run_batch256(args)
+        else:
+            run_points_workload(args, args.workload)
         return
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -67,9 +67,11 @@ struct Solver {
       Y = P->Y;
       d = (int)P->d;
       V = 1;
-      // partial buffers of both orientations, before any graph capture
-      ensure_rowpart_elems(h, 2 * pts_geo(true).S * n);
-      ensure_rowpart_elems(h, 2 * pts_geo(false).S * m);
+      // partial buffers of both orientations, before any graph capture: up to
+      // kPtsMaxPartials FP64 partials per owned element and chunk (the Newton
+      // set-up row sweep reduces three sums)
+      ensure_rowpart_elems(h, kPtsMaxPartials * pts_geo(true).S * n);
+      ensure_rowpart_elems(h, kPtsMaxPartials * pts_geo(false).S * m);
       sC = P->cost_scale > 0.0 ? P->cost_scale : max_cost_scale();
     } else {
       const bool aligned = ((uintptr_t)C % 16) == 0;
@@ -230,6 +232,10 @@ struct Solver {
     const PtsGeo g = pts_geo(ROWS);
     a.chunk = g.chunk;
     const dim3 grid((unsigned)g.B, (unsigned)g.S);
+    constexpr int NP = LSE ? 2 : NR;  // FP64 partials per owned element and chunk
+    static_assert(NP <= kPtsMaxPartials, "point partial buffer sized for kPtsMaxPartials");
+    if ((int64_t)NP * g.S * (ROWS ? n : m) > h->cap_rowpart || g.B > h->rowblk_slots)
+      throw EotError{EOT_ERR_INVALID_ARG, "point sweep scratch smaller than the launch needs"};
     // the FP32 mixed path forms D compensated; plain FP32 and FP64 use the
     // direct sum of squares
     constexpr bool F32 = sizeof(T) == 4;

@@ -22,6 +22,7 @@ namespace eot {
 // FP32 sum of k positive terms is off by up to ~k 2^-24 relative, which at k = 256
 // is already the 1e-6 scale of the marginal tolerance.
 constexpr int kPtsFlush = 16;
+constexpr int kPtsMaxPartials = 3;  // widest point sweep: three sums per owned element
 
 template <class T>
 __device__ __forceinline__ void split_k(double K, T& hi, T& lo) {
