@@ -42,7 +42,7 @@ void ensure_capacity(eot_handle h, int64_t n, int64_t m) {
   h->sc = (double*)dev_alloc(h, SC_COUNT * sizeof(double));
   h->status = (int*)dev_alloc(h, sizeof(int));
   h->cnt_strip = (int*)dev_alloc(h, h->max_strips * sizeof(int));
-  h->rowblk_slots = std::max<int64_t>(h->max_rowblk, L / 256 + 2);
+  h->rowblk_slots = std::max<int64_t>(h->max_rowblk, L / 128 + 2);  // 128-point blocks of the tensor-core sweeps
   h->cnt_rowblk = (int*)dev_alloc(h, h->rowblk_slots * sizeof(int));
   h->maxbuf_len = L / 256 + 8 * (int64_t)h->sms + 64;
   h->maxbuf = (double*)dev_alloc(h, h->maxbuf_len * sizeof(double));
@@ -189,6 +189,7 @@ eot_status eot_destroy(eot_handle h) {
   cudaDeviceSynchronize();
   free_all(h);
   if (h->bt_mem) cudaFree(h->bt_mem);
+  if (h->tc_mem) cudaFree(h->tc_mem);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   delete h;
   return EOT_OK;

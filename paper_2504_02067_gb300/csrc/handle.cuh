@@ -79,6 +79,8 @@ struct eot_handle_s {
 
   // eot_solve_batched: its own device block (not in `allocs`: growing the
   // single-problem buffers must not free it) and the autotuner's choices
+  void* tc_mem = nullptr;  // tensor-core point path: digit slices and row data (own block)
+  size_t tc_bytes = 0;
   void* bt_mem = nullptr;
   size_t bt_bytes = 0;
   std::map<std::string, std::pair<int, int>> bt_tune;  // batch shape -> (G, elements per thread)
@@ -97,6 +99,24 @@ inline bool pdl_enabled() {
     return !(e && e[0] == '0');
   }();
   return on;
+}
+// launch_k with dynamic shared memory
+template <typename... KArgs, typename... Args>
+inline void launch_kd(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                      Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl_enabled() ? 1 : 0;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+  if (e != cudaSuccess)
+    throw EotError{EOT_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e)};
 }
 template <typename... KArgs, typename... Args>
 inline void launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t st, Args&&... args) {

@@ -16,6 +16,7 @@
 
 #include "handle.cuh"
 #include "sweep_pts.cuh"
+#include "sweep_tc.cuh"
 
 namespace eot {
 
@@ -73,6 +74,9 @@ struct Solver {
       ensure_rowpart_elems(h, kPtsMaxPartials * pts_geo(true).S * n);
       ensure_rowpart_elems(h, kPtsMaxPartials * pts_geo(false).S * m);
       sC = P->cost_scale > 0.0 ? P->cost_scale : max_cost_scale();
+      if constexpr (sizeof(T) == 4) {
+        if (!plain && d >= tc::kMinD && tc_enabled()) setup_tc();
+      }
     } else {
       const bool aligned = ((uintptr_t)C % 16) == 0;
       V = (aligned && (m % VEC) == 0 && (ldc % VEC) == 0) ? VEC : 1;
@@ -99,6 +103,111 @@ struct Solver {
     g.S = (n_oth + g.chunk - 1) / g.chunk;
     return g;
   }
+  // ---- tensor-core point path (mixed precision, d >= tc::kMinD) ----
+  bool tc_on = false;
+  tc::TcArgs targs{};
+  static bool tc_enabled() {
+    const char* e = std::getenv("EOT_TC");
+    return !(e && e[0] == '0');
+  }
+  struct TcGeo {
+    int64_t B, S, chunk;
+  };
+  // own blocks of 128 points x S chunks of the other side (multiples of 48),
+  // S chosen so that B S fills whole waves of one-CTA-per-SM blocks
+  TcGeo tc_geo(bool rows) const {
+    const int64_t n_own = rows ? n : m, n_oth = rows ? m : n;
+    TcGeo g;
+    g.B = (n_own + tc::kM - 1) / tc::kM;
+    double best = -1.0;
+    g.S = 1;
+    g.chunk = (n_oth + tc::kN - 1) / tc::kN * tc::kN;
+    for (int64_t S = 1; S <= 128; ++S) {
+      const int64_t chunk = ((n_oth + S - 1) / S + tc::kN - 1) / tc::kN * tc::kN;
+      const int64_t Sr = (n_oth + chunk - 1) / chunk;
+      if (Sr != S) continue;
+      if (S > 1 && chunk < 2 * tc::kN) break;
+      const int64_t ctas = g.B * S, waves = (ctas + h->sms - 1) / h->sms;
+      const double eff = (double)ctas / (double)(waves * h->sms) - 0.002 * (double)S;  // prefer fewer chunks
+      if (eff > best) {
+        best = eff;
+        g.S = S;
+        g.chunk = chunk;
+      }
+    }
+    return g;
+  }
+  template <int NR, bool LSE, int SQM, bool ROWS, class Epi>
+  static void tc_attr() {
+    static bool done = false;
+    if (done) return;
+    EOT_CUDA(cudaFuncSetAttribute(tc::tc_sweep_kernel<NR, LSE, SQM, ROWS, Epi>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::kSmemBytes));
+    done = true;
+  }
+  void setup_tc() {
+    const int64_t npX = tc::pad_rows(n), npY = tc::pad_rows(m);
+    auto side_bytes = [](int64_t np) { return (size_t)np * (tc::kSlices * 64 * 2 + 3 * 4) + 1024; };
+    const size_t need = side_bytes(npX) + side_bytes(npY);
+    if (need > h->tc_bytes) {
+      EOT_CUDA(cudaStreamSynchronize(st));
+      if (h->tc_mem) cudaFree(h->tc_mem);
+      h->tc_mem = nullptr;
+      h->tc_bytes = 0;
+      EOT_CUDA(cudaMalloc(&h->tc_mem, need));
+      h->tc_bytes = need;
+    }
+    unsigned char* b = (unsigned char*)h->tc_mem;
+    auto carve = [&](tc::Side& sd, int64_t np, const float* P, int64_t len) {
+      __nv_bfloat16* sl = (__nv_bfloat16*)b;
+      b += (size_t)np * tc::kSlices * 64 * 2;
+      float* sc = (float*)b;
+      b += (size_t)np * 4;
+      float* nxh = (float*)b;
+      b += (size_t)np * 4;
+      float* nxl = (float*)b;
+      b += (size_t)np * 4;
+      b = (unsigned char*)(((uintptr_t)b + 255) & ~(uintptr_t)255);
+      sd = tc::Side{sl, sc, nxh, nxl, np};
+      const int64_t threads = np * 32;
+      launch_k(tc::tc_prep_kernel, dim3((unsigned)((threads + kThreads - 1) / kThreads)), dim3(kThreads), st, P,
+               len, d, np, sl, sc, nxh, nxl);
+      EOT_LAUNCH_CHECK();
+      h->launches++;
+    };
+    carve(targs.X, npX, X, n);
+    carve(targs.Y, npY, Y, m);
+    targs.err = h->status;
+    for (bool rows : {true, false}) {
+      const TcGeo g = tc_geo(rows);
+      ensure_rowpart_elems(h, kPtsMaxPartials * g.S * (rows ? n : m));
+      if (g.B > h->rowblk_slots) throw EotError{EOT_ERR_INVALID_ARG, "ticket array too small"};
+    }
+    // shared-memory opt-in for every instantiation, before any graph capture
+    tc_attr<1, true, 0, true, RowLseEpi>();
+    tc_attr<1, true, 0, false, ColLseEpi>();
+    tc_attr<2, false, 0, false, SetupColEpi<float>>();
+    tc_attr<3, false, 2, true, SetupRowEpi>();
+    tc_attr<1, false, 0, false, CgColEpi<float>>();
+    tc_attr<1, false, 0, true, CgRowEpi>();
+    tc_attr<1, false, 0, false, DvColEpi>();
+    tc_attr<2, false, 0, true, RowSumEpi>();
+    tc_attr<2, false, 0, false, ColSumEpi>();
+    tc_on = true;
+  }
+  template <int NR, bool LSE, int SQM, bool ROWS, class Epi>
+  void launch_tc(cudaStream_t s, SweepArgs<T> a, const Epi& e) {
+    const TcGeo g = tc_geo(ROWS);
+    a.chunk = g.chunk;
+    constexpr int NP = LSE ? 2 : NR;
+    static_assert(NP <= kPtsMaxPartials, "point partial buffer sized for kPtsMaxPartials");
+    if ((int64_t)NP * g.S * (ROWS ? n : m) > h->cap_rowpart || g.B > h->rowblk_slots)
+      throw EotError{EOT_ERR_INVALID_ARG, "tensor-core sweep scratch smaller than the launch needs"};
+    tc_attr<NR, LSE, SQM, ROWS, Epi>();
+    launch_kd(tc::tc_sweep_kernel<NR, LSE, SQM, ROWS, Epi>, dim3((unsigned)g.B, (unsigned)g.S),
+              dim3(tc::kTcThreads), (size_t)tc::kSmemBytes, s, a, targs, e);
+  }
+
   // s_C = 1 / max_ij |x_i - y_j|^2 (cost normalised to max 1, Sec. 4.1): FP32 scan,
   // FP64 re-evaluation of each thread's arg-max pair, maximum on the host.
   double max_cost_scale() {
@@ -195,6 +304,7 @@ struct Solver {
     if (s & kStatNonfinite) throw EotError{EOT_ERR_NONFINITE, "non-finite potential or marginal" + ctx};
     if (s & kStatCgNan) throw EotError{EOT_ERR_NONFINITE, "non-finite CG residual" + ctx};
     if (s & kStatRange) throw EotError{EOT_ERR_RANGE, "|potential| >= 2^19 (mixed-precision split)" + ctx};
+    if (s & kStatTimeout) throw EotError{EOT_ERR_CUDA, "a bounded device wait ran out" + ctx};
     return h->h_sc;
   }
   int status_bits() const { return *h->h_status; }
@@ -229,6 +339,12 @@ struct Solver {
   // point sweep: own side = rows (ROWS) or columns, dispatched on d
   template <int NR, bool LSE, int SQM, bool ROWS, class Epi>
   void launch_pts(cudaStream_t s, SweepArgs<T> a, const Epi& e) {
+    if constexpr (sizeof(T) == 4) {
+      if (tc_on) {
+        launch_tc<NR, LSE, SQM, ROWS>(s, a, e);
+        return;
+      }
+    }
     const PtsGeo g = pts_geo(ROWS);
     a.chunk = g.chunk;
     const dim3 grid((unsigned)g.B, (unsigned)g.S);

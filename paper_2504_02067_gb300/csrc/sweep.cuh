@@ -58,12 +58,12 @@ struct DotArr {
 // CTA-level deterministic sum of per-warp epilogue contributions, then a ticket
 // so that the last CTA calls epi.finish with the totals over all CTAs.
 // ----------------------------------------------------------------------------
-template <int ND, class Epi>
+template <int ND, class Epi, int NW = kWarps>
 __device__ __forceinline__ void cta_dot_finish(double (&wd)[ND > 0 ? ND : 1], int64_t part_idx,
                                                int64_t nparts, double* dotpart, int* cnt,
                                                Epi& epi) {
   if constexpr (ND > 0) {
-    __shared__ double sd[kWarps][ND];
+    __shared__ double sd[NW][ND];
     __shared__ int last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0) {
@@ -75,7 +75,7 @@ __device__ __forceinline__ void cta_dot_finish(double (&wd)[ND > 0 ? ND : 1], in
 #pragma unroll
       for (int k = 0; k < ND; ++k) {
         double t = 0.0;
-        for (int w = 0; w < kWarps; ++w) t += sd[w][k];
+        for (int w = 0; w < NW; ++w) t += sd[w][k];
         dotpart[part_idx * 2 + k] = t;
       }
       __threadfence();
@@ -89,7 +89,7 @@ __device__ __forceinline__ void cta_dot_finish(double (&wd)[ND > 0 ? ND : 1], in
       double v[ND];
 #pragma unroll
       for (int k = 0; k < ND; ++k) v[k] = 0.0;
-      for (int64_t p = threadIdx.x; p < nparts; p += kThreads) {
+      for (int64_t p = threadIdx.x; p < nparts; p += NW * 32) {
 #pragma unroll
         for (int k = 0; k < ND; ++k) v[k] += __ldcg(dotpart + p * 2 + k);
       }
@@ -106,7 +106,7 @@ __device__ __forceinline__ void cta_dot_finish(double (&wd)[ND > 0 ? ND : 1], in
 #pragma unroll
         for (int k = 0; k < ND; ++k) {
           tot.v[k] = 0.0;
-          for (int w = 0; w < kWarps; ++w) tot.v[k] += sd[w][k];
+          for (int w = 0; w < NW; ++w) tot.v[k] += sd[w][k];
         }
         *cnt = 0;
         epi.finish(tot.v);

@@ -42,7 +42,8 @@ def gam(g, prec):
 
 
 @pytest.mark.parametrize("n,m,d", [(1, 1, 2), (37, 53, 3), (300, 517, 2), (1000, 700, 3),
-                                   (129, 300, 8), (200, 150, 64)])
+                                   (129, 300, 8), (200, 150, 64), (129, 300, 17), (300, 517, 33),
+                                   (1000, 700, 64)])
 @pytest.mark.parametrize("prec", ["mixed", "fp64"])
 def test_point_marginals(H, n, m, d, prec):
     from paper_2504_02067_gb300 import Problem
@@ -176,3 +177,29 @@ def test_point_marginals_n2pow20_sampled(H):
     # relative error of the marginal entries (log difference) below 1e-6
     assert np.abs(lr[i_s] - ref_lr).max() <= 1e-6
     assert np.abs(lc[i_s] - ref_lc).max() <= 1e-6
+
+
+@pytest.mark.parametrize("d", [17, 64])
+def test_point_tensor_core_path_matches_simt(H, d, monkeypatch):
+    """For d >= 17 the mixed path forms x.y on the tensor cores from exact 8-bit
+    digit slices (levels summed exactly in FP32); EOT_TC=0 selects the SIMT
+    compensated distance instead. Both must match the oracle within the mixed
+    tolerance, and each other within twice that."""
+    from paper_2504_02067_gb300 import Problem
+    n, m = 700, 650
+    X, Y, r, c = cloud(77 + d, n, m, d)
+    sC = O.sqeuclid_scale(X, Y)
+    C64 = sC * O.sqeuclid(X, Y)
+    g = gam(1024.0, "mixed")
+    u = np.log(r) + np.random.default_rng(4).normal(0, 0.3, n) + 2.0
+    v = np.log(c) - O.lse_c(u[:, None] - g * C64)
+    P = O.plan(u, v, g, C64)
+    out = {}
+    for flag in ("1", "0"):
+        monkeypatch.setenv("EOT_TC", flag)
+        prob = Problem(X=t(X, torch.float32), Y=t(Y, torch.float32), precision="mixed", cost_scale=sC)
+        rr, cc, _, _, _ = H.marginals(prob, t(u), t(v), g)
+        out[flag] = (rr.cpu().numpy(), cc.cpu().numpy())
+        assert np.abs(out[flag][0] - O.row_sum(P)).sum() <= 1e-6
+        assert np.abs(out[flag][1] - O.col_sum(P)).sum() <= 1e-6
+    assert np.abs(out["1"][0] - out["0"][0]).sum() <= 2e-6
