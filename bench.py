@@ -581,6 +581,31 @@ def run_points_workload(args, kind):
     return out
 
 
+def run_profile_points(args):
+    """A few launches of one point sweep kernel (for ncu) on the d = 64 workload
+    (n = m = 16384, gamma 2^10, mixed): set-up launches first, then
+    `args.profile_iters` launches of kind args.profile_points."""
+    import numpy as np
+    import torch
+
+    import paper_2504_02067_gb300 as E
+    import workloads as W
+    E.build()
+    dev = torch.device("cuda", 0)
+    p = W.gmm_problem_d64(0)
+    n = p["X"].shape[0]
+    X, Y = torch.from_numpy(p["X"]).to(dev), torch.from_numpy(p["Y"]).to(dev)
+    r, c = torch.from_numpy(p["r"]).to(dev), torch.from_numpy(p["c"]).to(dev)
+    h = E.Handle(0, 64, 64)
+    prob = E.Problem(X=X, Y=Y, r=r, c=c, precision="mixed", cost_scale=0.0)
+    rng = np.random.default_rng(0)
+    u = torch.from_numpy(np.full(n, -np.log(n)) + rng.normal(0, 0.1, n)).to(dev)
+    v = torch.from_numpy(np.full(n, -np.log(n))).to(dev)
+    ms = h.eot_sweep_bench(prob, u, v, 1024.0, args.profile_points, args.profile_iters)
+    print(json.dumps({"kind": args.profile_points, "iters": args.profile_iters, "ms_per_launch": ms}))
+    h.close()
+
+
 def run_profile_sweep(args):
     """A few launches of one sweep kernel on the full-size workload (for ncu):
     the set-up launches come first (one row LSE, the Newton-step column and row
@@ -620,11 +645,16 @@ def main():
     ap.add_argument("--profile-sweep", type=int, default=-1,
                     help="run only eot_sweep_bench of this kind (0 CG column, 1 CG row, 2 HVP, 3 row LSE)")
     ap.add_argument("--profile-iters", type=int, default=3)
+    ap.add_argument("--profile-points", type=int, default=-1,
+                    help="run only eot_sweep_bench of this kind on the d = 64 point workload")
     ap.add_argument("--workload", default="grid4096", choices=["grid4096", "batch256", "d64", "colour"],
                     help="grid4096 = the headline line; the others print their own lines")
     args = ap.parse_args()
     if args.profile_sweep >= 0:
         run_profile_sweep(args)
+        return
+    if args.profile_points >= 0:
+        run_profile_points(args)
         return
     if args.workload != "grid4096" and args.impl == "ours":
         if args.workload == "batch256":

@@ -142,7 +142,9 @@ __device__ bool gbar(Grp& c, Smem<T>& s) {
         s.fail = 1;
         break;
       }
-      if ((it & 63u) == 63u && gtimer() - t0 > kWaitNs) {
+      // the timer alone is not trusted (it can jump under a profiler): at least
+      // 2^16 polls of >= 64 ns as well, and 2^26 polls always end the wait
+      if ((it & 63u) == 63u && ((it >= (1u << 16) && gtimer() - t0 > kWaitNs) || it >= (1u << 26))) {
         atomicExch(c.abort, 1);
         s.fail = 1;
         break;

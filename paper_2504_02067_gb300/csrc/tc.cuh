@@ -3,8 +3,8 @@
 // shared-memory and instruction descriptors of kind::f16 MMAs on BF16 operands
 // in the 128-byte-swizzled K-major layout.
 //
-// Every wait here is bounded: mbar_wait gives up after kWaitNs of %globaltimer
-// (or when *err is already set), sets *err and returns false, so a kernel that
+// Every wait here is bounded: mbar_wait gives up (after enough polls and time,
+// or when *err is already set), sets *err and returns false, so a kernel that
 // meets a stuck pipeline stops instead of hanging the GPU.
 #pragma once
 #include <cstdint>
@@ -52,14 +52,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 // Waits for the completion of the phase with the given parity; false (and *err
 // set) if that takes longer than kTcWaitNs or *err is already set.
+// The bound needs both kMinPolls polls and limit_ns of %globaltimer (the timer
+// alone is not trusted: under a profiler it can jump), and kMaxPolls polls
+// always end the wait (in case the timer stands still).
+constexpr uint32_t kMinPolls = 1u << 20;
+constexpr uint32_t kMaxPolls = 1u << 28;
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, int err_bit,
                                           unsigned long long limit_ns = kTcWaitNs) {
   const unsigned long long t0 = now_ns();
+  const uint32_t min_polls = limit_ns < kTcWaitNs ? kMinPolls >> 6 : kMinPolls;
   for (uint32_t it = 0;; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
     if ((it & 15u) == 15u) {
       if (*(volatile int*)err & err_bit) return false;
-      if (now_ns() - t0 > limit_ns) {
+      if ((it >= min_polls && now_ns() - t0 > limit_ns) || it >= kMaxPolls) {
         atomicOr(err, err_bit);
         return false;
       }
