@@ -171,7 +171,7 @@ struct Solver {
       sd = tc::Side{sl, sc, nxh, nxl, np};
       const int64_t threads = np * 32;
       launch_k(tc::tc_prep_kernel, dim3((unsigned)((threads + kThreads - 1) / kThreads)), dim3(kThreads), st, P,
-               len, d, np, sl, sc, nxh, nxl);
+               len, d, np, X /* the first point of X is the common centre */, sl, sc, nxh, nxl);
       EOT_LAUNCH_CHECK();
       h->launches++;
     };

@@ -2,7 +2,8 @@
 // (tcgen05, kind::f16 on BF16, FP32 accumulation in TMEM), for the mixed path at
 // larger d (up to 64 coordinates).
 //
-// Exactness (an exact-slice / Ozaki-style splitting). Each point x is scaled by
+// Exactness (an exact-slice / Ozaki-style splitting). Both point sets are moved
+// by one common centre (exact in FP64; distances are unchanged). Each point x is then scaled by
 // 2^-e (e from its largest coordinate, so |x_k| < 2^e) and each coordinate cut
 // into five signed 8-bit digits:  x_k = 2^e sum_s d_sk 2^-8(s+1)  (to 2^-40 of
 // the largest coordinate). A digit is an integer of magnitude <= 255, exact in
@@ -17,15 +18,18 @@
 // with |x|^2 precomputed as an FP32 pair from FP64), then the exponent exactly
 // as the SIMT point sweep does (expo), exp, and the reductions.
 //
-// CTA roles (320 threads, one CTA per SM: 143 KB of shared memory):
+// CTA roles (576 threads, one CTA per SM: 146 KB of shared memory):
 //   warp 0, lane 0: bulk copies (the own 128 points' slices once; the other
 //     side's 48-point tiles into two buffers) and the MMAs of each tile into one
 //     of two TMEM accumulator buffers (5 levels x 48 columns each);
 //   warp 1: TMEM allocation (512 columns) and release;
-//   warps 2-9: epilogue. Warp w reads TMEM lanes 32 (w mod 4) .. +31 (one own
-//     point per thread) and half of the tile's 48 columns.
+//   warps 2-17: epilogue. Warp w reads TMEM lanes 32 (w mod 4) .. +31 (one own
+//     point per thread) and a quarter (12) of the tile's 48 columns.
+// The other side's per-point data of a tile (h, scale, |y|^2, weights) arrive in
+// shared memory with the tile's slices (slot tile mod 4: a slot is refilled only
+// after the epilogue of the tile four back has finished).
 // Hand-offs are mbarriers: full[b] (copies landed), mmad[b] (MMAs of buffer b
-// done: accumulators readable and the slice buffer reusable), tfree[b] (the 8
+// done: accumulators readable and the slice buffer reusable), tfree[b] (the 16
 // epilogue warps have read buffer b). Every wait is bounded (tc.cuh).
 #pragma once
 #include <cuda_bf16.h>
@@ -40,15 +44,21 @@ constexpr int kM = 128;     // own points per CTA = TMEM lanes = MMA M
 constexpr int kN = 48;      // other-side points per tile = MMA N
 constexpr int kSlices = 5;  // 8-bit digits per coordinate
 constexpr int kLevels = 5;  // s + t = 0 .. 4
-constexpr int kTcThreads = 320;
+constexpr int kEpiWarps = 16;                 // 4 per TMEM lane quarter
+constexpr int kParts = kEpiWarps / 4;          // column parts of a tile
+constexpr int kPartCols = kN / kParts;         // 12 columns per epilogue warp and tile
+constexpr int kTcThreads = 32 * (2 + kEpiWarps);
 constexpr int kTcWarps = kTcThreads / 32;
-constexpr int kEpiWarps = 8;
-constexpr int kHalfCols = kN / 2;  // columns per epilogue warp and tile
 constexpr uint32_t kRowB = 128;    // bytes per point and slice: 64 BF16 coordinates
 constexpr uint32_t kOwnSlice = kM * kRowB;                          // 16 KB
 constexpr uint32_t kOthSlice = kN * kRowB;                          // 6 KB
 constexpr uint32_t kOffOth = kSlices * kOwnSlice;                   // 80 KB
-constexpr uint32_t kOffBar = kOffOth + 2 * kSlices * kOthSlice;     // + 60 KB
+constexpr int kSliceBufs = 3;                                       // tile tt: slice buffer tt % 3
+constexpr uint32_t kOffCol = kOffOth + kSliceBufs * kSlices * kOthSlice;  // + 90 KB
+constexpr int kColArrays = 7;                                       // h, scale, |y|^2 hi, lo, up to 3 weights
+constexpr uint32_t kColSlot = 8 * kN * 4;                           // 1536 bytes per tile
+constexpr int kColSlots = 4;                                        // tile tt uses slot tt % 4
+constexpr uint32_t kOffBar = kOffCol + kColSlots * kColSlot;        // + 6 KB
 constexpr uint32_t kSmemBytes = kOffBar + 128 + 1024;               // barriers + 1024-byte alignment slack
 constexpr int kBufCols = kLevels * kN;                              // 240 TMEM columns per buffer
 constexpr uint32_t kTmemCols = 512;
@@ -71,27 +81,31 @@ struct TcArgs {
 
 __host__ __device__ inline int64_t pad_rows(int64_t n) { return (n + kPadRows - 1) / kPadRows * kPadRows; }
 
-// One warp per point (rows >= n and coordinates >= d are zero).
-static __global__ void tc_prep_kernel(const float* X, int64_t n, int d, int64_t npad, __nv_bfloat16* sl,
-                                      float* sc, float* nxh, float* nxl) {
+// One warp per point (rows >= n and coordinates >= d are zero). Both point sets
+// are first moved by the same centre (the first point of X): |x - y|^2 does not
+// change, but |x|^2, |y|^2 and x.y become bounded by the data's extent, so the
+// expansion |x|^2 + |y|^2 - 2 x.y keeps its relative accuracy however far the
+// clouds lie from the origin. The differences are exact in FP64.
+static __global__ void tc_prep_kernel(const float* X, int64_t n, int d, int64_t npad, const float* centre,
+                                      __nv_bfloat16* sl, float* sc, float* nxh, float* nxl) {
   pdl_wait();
   const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (row >= npad) return;
-  float xv[2] = {0.f, 0.f};
+  double xv[2] = {0.0, 0.0};
   if (row < n) {
-    if (lane < d) xv[0] = X[row * d + lane];
-    if (lane + 32 < d) xv[1] = X[row * d + lane + 32];
+    if (lane < d) xv[0] = (double)X[row * d + lane] - (double)centre[lane];
+    if (lane + 32 < d) xv[1] = (double)X[row * d + lane + 32] - (double)centre[lane + 32];
   }
-  float mx = fmaxf(fabsf(xv[0]), fabsf(xv[1]));
-  double q = (double)xv[0] * xv[0] + (double)xv[1] * xv[1];
+  double mx = fmax(fabs(xv[0]), fabs(xv[1]));
+  double q = xv[0] * xv[0] + xv[1] * xv[1];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     q += __shfl_xor_sync(0xffffffffu, q, o);
   }
   int e = 0;
-  if (mx > 0.f) frexpf(mx, &e);  // mx = f 2^e, f in [0.5, 1): every |x_k| < 2^e
+  if (mx > 0.0) frexp(mx, &e);  // mx = f 2^e, f in [0.5, 1): every |x_k| < 2^e
   if (lane == 0) {
     sc[row] = ldexpf(1.f, e);
     const float h = (float)q;
@@ -101,7 +115,7 @@ static __global__ void tc_prep_kernel(const float* X, int64_t n, int d, int64_t 
 #pragma unroll
   for (int c = 0; c < 2; ++c) {
     const int k = lane + 32 * c;
-    const double Qd = trunc(ldexp((double)xv[c], 40 - e));  // |Q| < 2^40
+    const double Qd = trunc(ldexp(xv[c], 40 - e));  // |Q| < 2^40
     const long long Q = (long long)Qd;
     const unsigned long long aQ = (unsigned long long)(Q < 0 ? -Q : Q);
     const float sgn = Q < 0 ? -1.f : 1.f;
@@ -132,14 +146,15 @@ template <int NR, bool LSE, int SQM, bool ROWS, class Epi>
 __global__ void __launch_bounds__(kTcThreads, 1) tc_sweep_kernel(SweepArgs<float> a, TcArgs ta, Epi epi) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* full = (uint64_t*)(sm + kOffBar);  // [2]
-  uint64_t* mmad = full + 2;                   // [2]
-  uint64_t* tfree = full + 4;                  // [2]
-  uint64_t* ownf = full + 6;
-  uint32_t* tslot = (uint32_t*)(full + 7);
+  uint64_t* full = (uint64_t*)(sm + kOffBar);  // [3] per slice buffer
+  uint64_t* mmad = full + 3;                   // [2] per TMEM buffer
+  uint64_t* tfree = full + 5;                  // [2] per TMEM buffer
+  uint64_t* ownf = full + 7;
+  uint32_t* tslot = (uint32_t*)(full + 8);
   constexpr int NA = LSE ? 1 : NR;
+  constexpr int NW = LSE ? 1 : NR;
   constexpr int ND = Epi::kDot;
-  __shared__ float hsum[NA][kM], hcmp[NA][kM], hmax[kM];
+  __shared__ float hsum[kParts - 1][NA][kM], hcmp[kParts - 1][NA][kM], hmax[kParts - 1][kM];
   __shared__ int last_blk;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -153,6 +168,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_sweep_kernel(SweepArgs<float
   if (threadIdx.x == 0) {
     mbar_init(&full[0], 1);
     mbar_init(&full[1], 1);
+    mbar_init(&full[2], 1);
     mbar_init(&mmad[0], 1);
     mbar_init(&mmad[1], 1);
     mbar_init(&tfree[0], kEpiWarps);
@@ -172,8 +188,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_sweep_kernel(SweepArgs<float
     return;
   }
 
-  // per-thread results of the epilogue (own point r of this CTA, one column half)
-  const int q = warp & 3, hf = warp >= 2 ? (warp - 2) >> 2 : 0;
+  // per-thread results of the epilogue (own point r of this CTA, one column part)
+  const int q = warp & 3, part = warp >= 2 ? (warp - 2) >> 2 : 0;
   const int r = 32 * q + lane;
   const int64_t e = blk * kM + r;
   const bool ev = warp >= 2 && e < n_own;
@@ -185,6 +201,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_sweep_kernel(SweepArgs<float
     Ca[k] = 0.f;
   }
 
+  const float* ht = ROWS ? a.Bh : a.Ah;
+  const float* const* wt = ROWS ? a.wc : a.wr;
   if (warp == 0) {
     // ---------------- copies and MMAs (one thread) ----------------
     if (lane == 0) {
@@ -193,26 +211,41 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_sweep_kernel(SweepArgs<float
       mbar_arrive_expect_tx(ownf, kSlices * kOwnSlice);
       for (int s = 0; s < kSlices; ++s)
         bulk_g2s(sm + s * kOwnSlice, own_src + (int64_t)s * so.npad * kRowB, kOwnSlice, ownf);
+      // tile tt: its slices into buffer tt % 2, its per-point data into slot tt % 4
+      // (48 floats per array; the arrays hold at least 47 entries past n, and
+      // the epilogue masks j >= j1)
       auto issue = [&](int tt) {
-        const int b = tt & 1;
-        mbar_arrive_expect_tx(&full[b], kSlices * kOthSlice);
-        const unsigned char* src = oth_src + (j0 + (int64_t)tt * kN) * kRowB;
+        const int sb = tt % kSliceBufs;
+        const int64_t jt = j0 + (int64_t)tt * kN;
+        mbar_arrive_expect_tx(&full[sb], kSlices * kOthSlice + (4 + NW) * kN * 4);
+        const unsigned char* src = oth_src + jt * kRowB;
         for (int s = 0; s < kSlices; ++s)
-          bulk_g2s(sm + kOffOth + (b * kSlices + s) * kOthSlice, src + (int64_t)s * sq.npad * kRowB, kOthSlice,
-                   &full[b]);
+          bulk_g2s(sm + kOffOth + (sb * kSlices + s) * kOthSlice, src + (int64_t)s * sq.npad * kRowB, kOthSlice,
+                   &full[sb]);
+        float* cd = (float*)(sm + kOffCol + (tt & (kColSlots - 1)) * kColSlot);
+        bulk_g2s(cd + 0 * kN, ht + jt, kN * 4, &full[sb]);
+        bulk_g2s(cd + 1 * kN, sq.sc + jt, kN * 4, &full[sb]);
+        bulk_g2s(cd + 2 * kN, sq.nxh + jt, kN * 4, &full[sb]);
+        bulk_g2s(cd + 3 * kN, sq.nxl + jt, kN * 4, &full[sb]);
+#pragma unroll
+        for (int k = 0; k < NW; ++k) bulk_g2s(cd + (4 + k) * kN, wt[k] + jt, kN * 4, &full[sb]);
       };
+      // Schedule: tiles 0 and 1 are prefetched; after committing tile tt the
+      // copies of tile tt + 2 go into the slice buffer of tile tt - 1 once its
+      // MMAs are done (queued before tile tt's, so the tensor pipe stays busy)
+      // and into the column slot of tile tt - 2, whose epilogue finished before
+      // the MMAs of tile tt were issued.
       int issued = 0, landed = 0, committed = 0, retired = 0;
       for (; issued < 2 && issued < T; ++issued) issue(issued);
       const bool own_ok = mbar_wait(ownf, 0, ta.err, kStatTimeout);
       const uint32_t own_s = smem_u32(sm);
       for (int tt = 0; own_ok && tt < T; ++tt) {
-        const int b = tt & 1;
-        const uint32_t ph = (tt >> 1) & 1;
-        if (!mbar_wait(&full[b], ph, ta.err, kStatTimeout)) break;
+        const int b = tt & 1, sb = tt % kSliceBufs;
+        if (!mbar_wait(&full[sb], (tt / kSliceBufs) & 1, ta.err, kStatTimeout)) break;
         landed = tt + 1;
         if (tt >= 2 && !mbar_wait(&tfree[b], ((tt - 2) >> 1) & 1, ta.err, kStatTimeout)) break;
         tc_fence_after();
-        const uint32_t oth_s = smem_u32(sm + kOffOth + b * kSlices * kOthSlice);
+        const uint32_t oth_s = smem_u32(sm + kOffOth + sb * kSlices * kOthSlice);
 #pragma unroll 1
         for (int L = 0; L < kLevels; ++L) {
           const uint32_t d_tmem = tbase + (uint32_t)(b * kBufCols + L * kN);
@@ -230,8 +263,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_sweep_kernel(SweepArgs<float
         mma_commit(&mmad[b]);
         committed = tt + 1;
         if (tt + 2 < T) {
-          if (!mbar_wait(&mmad[b], ph, ta.err, kStatTimeout)) break;
-          retired = tt + 1;
+          if (tt >= 1) {
+            if (!mbar_wait(&mmad[(tt - 1) & 1], ((tt - 1) >> 1) & 1, ta.err, kStatTimeout)) break;
+            retired = tt;
+          }
           issue(tt + 2);
           ++issued;
         }
@@ -239,7 +274,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_sweep_kernel(SweepArgs<float
       // leave nothing in flight (bounded waits that ignore the error flag):
       // copies issued but not seen landed, and the MMAs not seen retired
       if (!own_ok) mbar_wait(ownf, 0, ta.err, 0, kTcDrainNs);
-      for (int tt = landed; tt < issued; ++tt) mbar_wait(&full[tt & 1], (tt >> 1) & 1, ta.err, 0, kTcDrainNs);
+      for (int tt = landed; tt < issued; ++tt)
+        mbar_wait(&full[tt % kSliceBufs], (tt / kSliceBufs) & 1, ta.err, 0, kTcDrainNs);
       for (int tt = (retired > committed - 2 ? retired : committed - 2); tt < committed; ++tt)
         if (tt >= 0) mbar_wait(&mmad[tt & 1], (tt >> 1) & 1, ta.err, 0, kTcDrainNs);
     }
@@ -247,8 +283,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_sweep_kernel(SweepArgs<float
   } else if (warp >= 2) {
     // ---------------- epilogue ----------------
     const float* ho = ROWS ? a.Ah : a.Bh;
-    const float* ht = ROWS ? a.Bh : a.Ah;
-    const float* const* wt = ROWS ? a.wc : a.wr;
     const float h = ev ? ho[e] : 0.f;
     float hm = h;
     const float sc_own = so.sc[e], nxh = so.nxh[e], nxl = so.nxl[e];  // e < npad
@@ -258,25 +292,26 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_sweep_kernel(SweepArgs<float
     const uint32_t lane_base = (uint32_t)(32 * q) << 16;
     for (int tt = 0; tt < T; ++tt) {
       const int b = tt & 1;
-      if (!warp_wait(&mmad[b], (tt >> 1) & 1, ta.err)) break;
+      if (!warp_wait(&mmad[b], (tt >> 1) & 1, ta.err)) break;  // also covers the tile's copies
       tc_fence_after();
+      const float* cd = (const float*)(sm + kOffCol + (tt & (kColSlots - 1)) * kColSlot);
 #pragma unroll 1
-      for (int c = 0; c < kHalfCols / 8; ++c) {
-        const int col0 = hf * kHalfCols + c * 8;
-        uint32_t lv[kLevels][8];
+      for (int c = 0; c < kPartCols / 4; ++c) {
+        const int col0 = part * kPartCols + c * 4;
+        uint32_t lv[kLevels][4];
 #pragma unroll
         for (int L = 0; L < kLevels; ++L)
-          tmem_ld8(tbase + lane_base + (uint32_t)(b * kBufCols + L * kN + col0), lv[L]);
+          tmem_ld4(tbase + lane_base + (uint32_t)(b * kBufCols + L * kN + col0), lv[L]);
         tmem_ld_wait();
         float acc[NA];
 #pragma unroll
         for (int k = 0; k < NA; ++k) acc[k] = 0.f;
 #pragma unroll
-        for (int jj = 0; jj < 8; ++jj) {
-          const int64_t j = j0 + (int64_t)tt * kN + col0 + jj;
-          if (j >= j1) break;  // uniform across the warp
-          const float hb = ht[j];
-          const float f = sc_own * sq.sc[j] * 0x1p-16f;  // powers of two: exact
+        for (int jj = 0; jj < 4; ++jj) {
+          const int cj = col0 + jj;
+          if (j0 + (int64_t)tt * kN + cj >= j1) break;  // uniform across the warp
+          const float hb = cd[cj];
+          const float f = sc_own * cd[kN + cj] * 0x1p-16f;  // powers of two: exact
           float gh, gl;
           two_sum(__uint_as_float(lv[0][jj]), __uint_as_float(lv[1][jj]) * 0x1p-8f, gh, gl);
           gl += __uint_as_float(lv[2][jj]) * 0x1p-16f +
@@ -284,14 +319,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_sweep_kernel(SweepArgs<float
           gh *= f;
           gl *= f;
           float s1, e1, Dh, e2;
-          two_sum(nxh, sq.nxh[j], s1, e1);
+          two_sum(nxh, cd[2 * kN + cj], s1, e1);
           two_sum(s1, -2.f * gh, Dh, e2);
-          const float Dl = e2 + ((e1 + (nxl + sq.nxl[j])) - 2.f * gl);
+          const float Dl = e2 + ((e1 + (nxl + cd[3 * kN + cj])) - 2.f * gl);
           if constexpr (!LSE) {
             const float ex = expT(expo<true>(h + hb, Kh, Kl, Dh, Dl));
 #pragma unroll
             for (int k = 0; k < NR; ++k) {
-              const float w = wt[k][j];
+              const float w = cd[(4 + k) * kN + cj];
               if ((SQM >> k) & 1) acc[k] = fmaf(ex * ex, w, acc[k]);
               else acc[k] = fmaf(ex, w, acc[k]);
             }
@@ -312,7 +347,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_sweep_kernel(SweepArgs<float
               Ca[0] *= fsc;
               tv = expo<true>(hm + hb, Kh, Kl, Dh, Dl);
             }
-            acc[0] = fmaf(expT(tv), wt[0][j], acc[0]);
+            acc[0] = fmaf(expT(tv), cd[4 * kN + cj], acc[0]);
           }
         }
 #pragma unroll
@@ -322,13 +357,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_sweep_kernel(SweepArgs<float
       __syncwarp();
       if (lane == 0) mbar_arrive(&tfree[b]);
     }
-    if (hf == 1) {  // the second column half hands its sums to the first
+    if (part > 0) {  // parts 1-3 hand their sums to part 0
 #pragma unroll
       for (int k = 0; k < NA; ++k) {
-        hsum[k][r] = Sa[k];
-        hcmp[k][r] = Ca[k];
+        hsum[part - 1][k][r] = Sa[k];
+        hcmp[part - 1][k][r] = Ca[k];
       }
-      hmax[r] = mx_set ? mx : 0.f;
+      hmax[part - 1][r] = mx_set ? mx : 0.f;
     }
   }
   pdl_trigger();
@@ -338,18 +373,24 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_sweep_kernel(SweepArgs<float
     tc_fence_after();
     tmem_free(tbase, kTmemCols);
   }
-  if (warp >= 2 && hf == 0 && ev) {
+  if (warp >= 2 && part == 0 && ev) {
     if constexpr (!LSE) {
 #pragma unroll
       for (int k = 0; k < NR; ++k) {
-        const double v = ((double)Sa[k] + (double)Ca[k]) + ((double)hsum[k][r] + (double)hcmp[k][r]);
+        double v = (double)Sa[k] + (double)Ca[k];
+#pragma unroll
+        for (int pp = 0; pp < kParts - 1; ++pp) v += (double)hsum[pp][k][r] + (double)hcmp[pp][k][r];
         a.rowpart[((int64_t)k * S + sidx) * n_own + e] = v;
       }
     } else {
-      const double s0 = (double)Sa[0] + (double)Ca[0], s1 = (double)hsum[0][r] + (double)hcmp[0][r];
       LsePair p{0.0, 0.0};
+      const double s0 = (double)Sa[0] + (double)Ca[0];
       if (s0 > 0.0) p = lse_combine<float>(p, LsePair{(double)mx, s0});
-      if (s1 > 0.0) p = lse_combine<float>(p, LsePair{(double)hmax[r], s1});
+#pragma unroll
+      for (int pp = 0; pp < kParts - 1; ++pp) {
+        const double sp = (double)hsum[pp][0][r] + (double)hcmp[pp][0][r];
+        if (sp > 0.0) p = lse_combine<float>(p, LsePair{(double)hmax[pp][r], sp});
+      }
       a.rowpart[((int64_t)0 * S + sidx) * n_own + e] = p.m;
       a.rowpart[((int64_t)1 * S + sidx) * n_own + e] = p.s;
     }

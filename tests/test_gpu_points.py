@@ -179,15 +179,18 @@ def test_point_marginals_n2pow20_sampled(H):
     assert np.abs(lc[i_s] - ref_lc).max() <= 1e-6
 
 
-@pytest.mark.parametrize("d", [17, 64])
-def test_point_tensor_core_path_matches_simt(H, d, monkeypatch):
+@pytest.mark.parametrize("d,shift", [(17, 0.0), (64, 0.0), (64, 1000.0)])
+def test_point_tensor_core_path_matches_simt(H, d, shift, monkeypatch):
     """For d >= 17 the mixed path forms x.y on the tensor cores from exact 8-bit
     digit slices (levels summed exactly in FP32); EOT_TC=0 selects the SIMT
     compensated distance instead. Both must match the oracle within the mixed
-    tolerance, and each other within twice that."""
+    tolerance, and each other within twice that; also for clouds moved 1000 away
+    from the origin (the kernels centre both sets on a common point)."""
     from paper_2504_02067_gb300 import Problem
     n, m = 700, 650
     X, Y, r, c = cloud(77 + d, n, m, d)
+    # far from the origin relative to their extent (the expansion must not care)
+    X, Y = (X + np.float32(shift)).astype(np.float32), (Y + np.float32(shift)).astype(np.float32)
     sC = O.sqeuclid_scale(X, Y)
     C64 = sC * O.sqeuclid(X, Y)
     g = gam(1024.0, "mixed")
