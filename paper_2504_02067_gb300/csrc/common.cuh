@@ -115,6 +115,23 @@ __device__ __forceinline__ void kadd(float& s, float& c, float x) {
 }
 __device__ __forceinline__ void kadd(double& s, double& c, double x) { s += x; }
 
+// Warp-wide sum of Neumaier pairs (s, c) in FP32 (compensated at every step).
+// The xor butterfly gives every lane the same bits (the steps are symmetric).
+__device__ __forceinline__ void warp_sum_pair(float& s, float& c) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float s2 = __shfl_xor_sync(0xffffffffu, s, o);
+    const float c2 = __shfl_xor_sync(0xffffffffu, c, o);
+    kadd(s, c, s2);
+    c += c2;
+  }
+}
+__device__ __forceinline__ float warp_max_f(float x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x = fmaxf(x, __shfl_xor_sync(0xffffffffu, x, o));
+  return x;
+}
+
 // V consecutive elements from shared memory (16-byte aligned when V > 1)
 template <int V, class T>
 __device__ __forceinline__ void ld_vec_smem(const T* p, T (&c)[V]) {

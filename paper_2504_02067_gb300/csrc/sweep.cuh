@@ -275,24 +275,56 @@ __global__ void __launch_bounds__(kThreads, 4) row_sweep_kernel(SweepArgs<T> a, 
   }
   pdl_trigger();
   if (rv) {
-    if constexpr (!LSE) {
-      double tot[NR];
+    if constexpr (sizeof(T) == 4) {
+      // FP32 path: the lanes' compensated pairs are combined in FP32 (the FP64
+      // pipe is narrow); only lane 0 converts the row's result to FP64
+      if constexpr (!LSE) {
+        double tot[NR];
 #pragma unroll
-      for (int k = 0; k < NR; ++k) tot[k] = warp_sum((double)S[k] + (double)Cc[k]);
-      if (lane == 0) {
-        DotArr<ND> d;
-        epi.row(i, tot, d.v);  // tot: [NR] sums
+        for (int k = 0; k < NR; ++k) {
+          float s0 = S[k], c0 = Cc[k];
+          warp_sum_pair(s0, c0);
+          tot[k] = (double)s0 + (double)c0;
+        }
+        if (lane == 0) {
+          DotArr<ND> d;
+          epi.row(i, tot, d.v);  // tot: [NR] sums
 #pragma unroll
-        for (int k = 0; k < ND; ++k) wd[k] += d.v[k];
+          for (int k = 0; k < ND; ++k) wd[k] += d.v[k];
+        }
+      } else {
+        // common max of the lanes (1/8 grid: exact), one rescale per lane
+        const float M = warp_max_f(mx_set ? (float)mx : -INFINITY);
+        const float f = mx_set ? (float)expT((T)(mx - (T)M)) : 0.f;
+        float s0 = (float)S[0] * f, c0 = (float)Cc[0] * f;
+        warp_sum_pair(s0, c0);
+        if (lane == 0) {
+          DotArr<ND> d;
+          epi.row_lse(i, (double)M, (double)s0 + (double)c0, d.v);
+#pragma unroll
+          for (int k = 0; k < ND; ++k) wd[k] += d.v[k];
+        }
       }
     } else {
-      LsePair p{(double)mx, (double)S[0] + (double)Cc[0]};
-      p = warp_lse<T>(p);
-      if (lane == 0) {
-        DotArr<ND> d;
-        epi.row_lse(i, p.m, p.s, d.v);
+      if constexpr (!LSE) {
+        double tot[NR];
 #pragma unroll
-        for (int k = 0; k < ND; ++k) wd[k] += d.v[k];
+        for (int k = 0; k < NR; ++k) tot[k] = warp_sum((double)S[k] + (double)Cc[k]);
+        if (lane == 0) {
+          DotArr<ND> d;
+          epi.row(i, tot, d.v);  // tot: [NR] sums
+#pragma unroll
+          for (int k = 0; k < ND; ++k) wd[k] += d.v[k];
+        }
+      } else {
+        LsePair p{mx_set ? (double)mx : 0.0, (double)S[0] + (double)Cc[0]};
+        p = warp_lse<T>(p);
+        if (lane == 0) {
+          DotArr<ND> d;
+          epi.row_lse(i, p.m, p.s, d.v);
+#pragma unroll
+          for (int k = 0; k < ND; ++k) wd[k] += d.v[k];
+        }
       }
     }
   }
@@ -470,33 +502,82 @@ __global__ void __launch_bounds__(kThreads, kColCtasPerSm) col_sweep_kernel(Swee
   }
 
   pdl_trigger();
-  // ---- combine the 8 warps of this CTA in FP64 and write the [R][m] partials ----
-  __shared__ double sred[NP][kWarps][SW];
-  __shared__ double smax[LSE ? kWarps : 1][LSE ? SW : 1];
+  // ---- combine the 8 warps of this CTA and write the [R][m] partials ----
+  // FP32 path: compensated FP32 pairs (the FP64 pipe is narrow), stored as a
+  // float2 (sum, compensation) per partial slot; LSE: (max, 0) in slot 0 and the
+  // pair in slot 1. FP64 path: FP64 partials.
+  if constexpr (sizeof(T) == 4) {
+    __shared__ float fsum[NP][kWarps][SW], fcmp[NP][kWarps][SW];
+    __shared__ float fmx[LSE ? kWarps : 1][LSE ? SW : 1];
 #pragma unroll
-  for (int k = 0; k < NP; ++k)
+    for (int k = 0; k < NP; ++k)
 #pragma unroll
-    for (int e = 0; e < V; ++e) sred[k][warp][lane * V + e] = (double)tot[k][e] + (double)cmp[k][e];
-  if constexpr (LSE) {
-#pragma unroll
-    for (int e = 0; e < V; ++e) smax[warp][lane * V + e] = (double)mx[e];
-  }
-  __syncthreads();
-  for (int cc = threadIdx.x; cc < SW; cc += kThreads) {
-    const int64_t jj = strip * SW + cc;
-    if (jj >= a.m) continue;
-    if constexpr (!LSE) {
-#pragma unroll
-      for (int k = 0; k < NP; ++k) {
-        double t = 0.0;
-        for (int w = 0; w < kWarps; ++w) t += sred[k][w][cc];
-        a.colpart[((int64_t)k * R + rb) * a.m + jj] = t;
+      for (int e = 0; e < V; ++e) {
+        fsum[k][warp][lane * V + e] = (float)tot[k][e];
+        fcmp[k][warp][lane * V + e] = (float)cmp[k][e];
       }
-    } else {
-      LsePair p{0.0, 0.0};
-      for (int w = 0; w < kWarps; ++w) p = lse_combine<T>(p, LsePair{smax[w][cc], sred[1][w][cc]});
-      a.colpart[((int64_t)0 * R + rb) * a.m + jj] = p.m;
-      a.colpart[((int64_t)1 * R + rb) * a.m + jj] = p.s;
+    if constexpr (LSE) {
+#pragma unroll
+      for (int e = 0; e < V; ++e) fmx[warp][lane * V + e] = (float)mx[e];
+    }
+    __syncthreads();
+    float2* cp2 = reinterpret_cast<float2*>(a.colpart);
+    for (int cc = threadIdx.x; cc < SW; cc += kThreads) {
+      const int64_t jj = strip * SW + cc;
+      if (jj >= a.m) continue;
+      if constexpr (!LSE) {
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+          float s0 = 0.f, c0 = 0.f;
+          for (int w = 0; w < kWarps; ++w) {
+            kadd(s0, c0, fsum[k][w][cc]);
+            c0 += fcmp[k][w][cc];
+          }
+          cp2[((int64_t)k * R + rb) * a.m + jj] = make_float2(s0, c0);
+        }
+      } else {
+        float M = -INFINITY;
+        for (int w = 0; w < kWarps; ++w)
+          if (fsum[1][w][cc] != 0.f || fcmp[1][w][cc] != 0.f) M = fmaxf(M, fmx[w][cc]);
+        float s0 = 0.f, c0 = 0.f;
+        for (int w = 0; w < kWarps; ++w) {
+          if (fsum[1][w][cc] == 0.f && fcmp[1][w][cc] == 0.f) continue;
+          const float f = (float)expT((T)(fmx[w][cc] - M));
+          kadd(s0, c0, fsum[1][w][cc] * f);
+          c0 += fcmp[1][w][cc] * f;
+        }
+        cp2[((int64_t)0 * R + rb) * a.m + jj] = make_float2(M, 0.f);
+        cp2[((int64_t)1 * R + rb) * a.m + jj] = make_float2(s0, c0);
+      }
+    }
+  } else {
+    __shared__ double sred[NP][kWarps][SW];
+    __shared__ double smax[LSE ? kWarps : 1][LSE ? SW : 1];
+#pragma unroll
+    for (int k = 0; k < NP; ++k)
+#pragma unroll
+      for (int e = 0; e < V; ++e) sred[k][warp][lane * V + e] = (double)tot[k][e] + (double)cmp[k][e];
+    if constexpr (LSE) {
+#pragma unroll
+      for (int e = 0; e < V; ++e) smax[warp][lane * V + e] = (double)mx[e];
+    }
+    __syncthreads();
+    for (int cc = threadIdx.x; cc < SW; cc += kThreads) {
+      const int64_t jj = strip * SW + cc;
+      if (jj >= a.m) continue;
+      if constexpr (!LSE) {
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+          double t = 0.0;
+          for (int w = 0; w < kWarps; ++w) t += sred[k][w][cc];
+          a.colpart[((int64_t)k * R + rb) * a.m + jj] = t;
+        }
+      } else {
+        LsePair p{0.0, 0.0};
+        for (int w = 0; w < kWarps; ++w) p = lse_combine<T>(p, LsePair{smax[w][cc], sred[1][w][cc]});
+        a.colpart[((int64_t)0 * R + rb) * a.m + jj] = p.m;
+        a.colpart[((int64_t)1 * R + rb) * a.m + jj] = p.s;
+      }
     }
   }
 
@@ -518,7 +599,38 @@ __global__ void __launch_bounds__(kThreads, kColCtasPerSm) col_sweep_kernel(Swee
       const int64_t jj = strip * SW + cc;
       if (jj >= a.m) continue;
       DotArr<ND> d;
-      if constexpr (!LSE) {
+      if constexpr (sizeof(T) == 4) {
+        const float2* cp2 = reinterpret_cast<const float2*>(a.colpart);
+        if constexpr (!LSE) {
+          double s[NC];
+#pragma unroll
+          for (int k = 0; k < NC; ++k) {
+            float s0 = 0.f, c0 = 0.f;
+            for (int r = 0; r < R; ++r) {
+              const float2 q = __ldcg(cp2 + ((int64_t)k * R + r) * a.m + jj);
+              kadd(s0, c0, q.x);
+              c0 += q.y;
+            }
+            s[k] = (double)s0 + (double)c0;
+          }
+          epi.col(jj, s, d.v);
+        } else {
+          float M = -INFINITY;
+          for (int r = 0; r < R; ++r) {
+            const float2 qs = __ldcg(cp2 + ((int64_t)R + r) * a.m + jj);
+            if (qs.x != 0.f || qs.y != 0.f) M = fmaxf(M, __ldcg(cp2 + (int64_t)r * a.m + jj).x);
+          }
+          float s0 = 0.f, c0 = 0.f;
+          for (int r = 0; r < R; ++r) {
+            const float2 qs = __ldcg(cp2 + ((int64_t)R + r) * a.m + jj);
+            if (qs.x == 0.f && qs.y == 0.f) continue;
+            const float f = (float)expT((T)(__ldcg(cp2 + (int64_t)r * a.m + jj).x - M));
+            kadd(s0, c0, qs.x * f);
+            c0 += qs.y * f;
+          }
+          epi.col_lse(jj, (double)M, (double)s0 + (double)c0, d.v);
+        }
+      } else if constexpr (!LSE) {
         double s[NC];
 #pragma unroll
         for (int k = 0; k < NC; ++k) {
