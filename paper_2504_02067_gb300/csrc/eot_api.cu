@@ -56,7 +56,7 @@ void ensure_capacity(eot_handle h, int64_t n, int64_t m) {
   h->dotpart = (double*)dev_alloc(h, 2 * h->dot_slots * sizeof(double));
   double** nv[] = {&h->Al, &h->rowfac, &h->rP, &h->logrP, &h->rowmax, &h->rt, &h->logrt,
                    &h->du, &h->x, &h->res, &h->z, &h->p, &h->q, &h->y, &h->Yx, &h->M,
-                   &h->diag, &h->y0, &h->du0, &h->nt0, &h->nt1, &h->rPs};
+                   &h->diag, &h->y0, &h->du0, &h->nt0, &h->nt1, &h->rPs, &h->p2};
   for (double** p : nv) *p = (double*)dev_alloc(h, N * sizeof(double));
   double** mv[] = {&h->Bl, &h->colfac, &h->cP, &h->logcP, &h->ct, &h->logct, &h->dv, &h->mt0, &h->mt1};
   for (double** p : mv) *p = (double*)dev_alloc(h, Mm * sizeof(double));
@@ -190,6 +190,7 @@ eot_status eot_destroy(eot_handle h) {
   free_all(h);
   if (h->bt_mem) cudaFree(h->bt_mem);
   if (h->tc_mem) cudaFree(h->tc_mem);
+  if (h->pcg_mem) cudaFree(h->pcg_mem);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   delete h;
   return EOT_OK;

@@ -67,6 +67,7 @@ struct eot_handle_s {
   double *z = nullptr, *p = nullptr, *q = nullptr, *y = nullptr, *Yx = nullptr, *M = nullptr;
   double *diag = nullptr, *y0 = nullptr, *du0 = nullptr, *nt0 = nullptr, *nt1 = nullptr;
   double* rPs = nullptr;  // row sums of the factorised plan used inside F_r
+  double* p2 = nullptr;   // second p buffer of the persistent CG kernel
   // FP64 m-vectors
   double *Bl = nullptr, *colfac = nullptr, *cP = nullptr, *logcP = nullptr, *ct = nullptr;
   double *logct = nullptr, *dv = nullptr, *mt0 = nullptr, *mt1 = nullptr;
@@ -79,6 +80,8 @@ struct eot_handle_s {
 
   // eot_solve_batched: its own device block (not in `allocs`: growing the
   // single-problem buffers must not free it) and the autotuner's choices
+  void* pcg_mem = nullptr;  // persistent CG kernel: CTA partials, barrier counter (own block)
+  size_t pcg_bytes = 0;
   void* tc_mem = nullptr;  // tensor-core point path: digit slices and row data (own block)
   size_t tc_bytes = 0;
   void* bt_mem = nullptr;

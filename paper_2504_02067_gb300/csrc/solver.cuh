@@ -17,6 +17,7 @@
 #include "handle.cuh"
 #include "sweep_pts.cuh"
 #include "sweep_tc.cuh"
+#include "cg_persistent.cuh"
 
 namespace eot {
 
@@ -604,6 +605,88 @@ struct Solver {
     return h->graphs.emplace(key, g).first->second;
   }
 
+  // ---- the persistent CG kernel (dense FP32 cost, mixed path) ----
+  // Opt-in (EOT_CG_PERSIST=1): on the 64 x 64 grid workload its four grid
+  // barriers per iteration at two CTAs per SM cost more (57 us per CG iteration)
+  // than the kernel boundaries of the graph path (29 us), so it is not the default.
+  static bool persist_env() {
+    const char* e = std::getenv("EOT_CG_PERSIST");
+    return e && e[0] == '1';
+  }
+  struct PcgGeo {
+    int S = 0, R = 0, rpb = 0, G = 0;
+  };
+  PcgGeo pcg_geo() const {
+    PcgGeo g;
+    if constexpr (sizeof(T) != 4) return g;
+    if (points || plain || V != 4 || m > pcg::kTWp || !persist_env()) return g;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pcg::cg_persistent_kernel, kThreads, 0) != cudaSuccess)
+      return g;
+    const int gmax = nb * h->sms;
+    const int S = (int)((m + pcg::kSW - 1) / pcg::kSW);
+    if (S > gmax) return g;
+    int R = (int)std::min<int64_t>(gmax / S, (n + kWarps - 1) / kWarps);
+    R = std::max(R, 1);
+    const int rpb = (int)((n + R - 1) / R);
+    R = (int)((n + rpb - 1) / rpb);
+    if ((int64_t)R * m > 2 * h->max_rowblk * h->cap_m) return g;  // FP32-pair partials in colpart
+    g.S = S;
+    g.R = R;
+    g.rpb = rpb;
+    g.G = R * S;
+    return g;
+  }
+  void run_cg_persistent(const PcgGeo& geo) {
+    const size_t need = (size_t)4 * geo.G * sizeof(double) + 256;
+    if (need > h->pcg_bytes) {
+      EOT_CUDA(cudaStreamSynchronize(st));
+      if (h->pcg_mem) cudaFree(h->pcg_mem);
+      h->pcg_mem = nullptr;
+      h->pcg_bytes = 0;
+      EOT_CUDA(cudaMalloc(&h->pcg_mem, need));
+      h->pcg_bytes = need;
+    }
+    unsigned char* b = (unsigned char*)h->pcg_mem;
+    pcg::Args a{};
+    a.C = (const float*)C;
+    a.n = n;
+    a.m = m;
+    a.ldc = ldc;
+    a.Ah = (const float*)h->Ah;
+    a.Bh = (const float*)h->Bh;
+    a.rowfac = h->rowfac;
+    a.colfac = h->colfac;
+    a.cP = h->cP;
+    a.rPs = h->rPs;
+    a.M = h->M;
+    a.x = h->x;
+    a.res = h->res;
+    a.z = h->z;
+    a.q = h->q;
+    a.y = h->y;
+    a.Yx = h->Yx;
+    a.pbuf[0] = h->p;
+    a.pbuf[1] = h->p2;
+    a.xw = (float*)h->xw0;
+    a.zf = (float*)h->zf;
+    a.colpart = reinterpret_cast<float2*>(h->colpart);
+    a.dots = (double*)(b + 256);
+    a.sc = h->sc;
+    a.bar = (unsigned*)b;
+    a.abort = (int*)(b + 64);
+    a.status = h->status;
+    a.R = geo.R;
+    a.S = geo.S;
+    a.rows_per_block = geo.rpb;
+    a.keep_l2 = keep_l2 ? 1 : 0;
+    EOT_CUDA(cudaMemsetAsync(b, 0, 256, st));
+    void* args[] = {&a};
+    EOT_CUDA(cudaLaunchCooperativeKernel((const void*)pcg::cg_persistent_kernel, dim3(geo.G), dim3(kThreads), args,
+                                         0, st));
+    h->launches++;
+  }
+
   // Runs PCG from x = 0 on F_r(rho) until the device stop flag clears.
   void run_cg(CgMode mode, int max_cg, const double* rt) {
     launch_k(cg_init_kernel<T>, dim3(vg_n), dim3(kThreads), st, n, h->rP, h->rPs, rt, h->diag, h->rowfac, h->M, h->x,
@@ -611,6 +694,13 @@ struct Solver {
                                                  h->dotpart, h->cnt_dot);
     EOT_LAUNCH_CHECK();
     h->launches++;
+    {
+      const PcgGeo geo = pcg_geo();
+      if (geo.G > 0) {
+        run_cg_persistent(geo);
+        return;
+      }
+    }
     if (mode == CgMode::kHost) {
       for (int it = 0; it < max_cg; it += 4) {
         for (int b = 0; b < 4; ++b) cg_iteration(st, 0);

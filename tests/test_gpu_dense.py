@@ -236,3 +236,35 @@ def test_solve_grid4096_matches_oracle_trace(H, prec):
     assert O.marginal_l1_error(u, v, 16384.0, C64, p["r"], p["c"]) <= 1e-6
     cost = O.transport_cost(u, v, 16384.0, C64)
     assert abs(cost - ref["transport_cost"]) <= 1e-6 * ref["transport_cost"]
+
+
+def test_persistent_cg_kernel_matches_graph_path(H, monkeypatch):
+    """The opt-in persistent CG kernel (one cooperative launch per linear solve,
+    grid barriers between the phases) runs the same PCG: Newton directions agree
+    with the per-kernel path and the oracle within the mixed tolerance."""
+    from paper_2504_02067_gb300 import Problem
+    n = m = 1024
+    rng = np.random.default_rng(31)
+    C = rng.uniform(0, 1, size=(n, m)).astype(np.float32)
+    C64 = C.astype(np.float64)
+    gamma = 64.0
+    u, v, r, c = near_feasible(32, n, m, gamma, C64)
+    P = O.plan(u, v, gamma, C64)
+    rP = O.row_sum(P)
+    rt = rP * (1 + 0.02 * rng.normal(size=n))
+    rt /= rt.sum()
+    gu = rP - rt
+    gl1 = np.abs(gu).sum()
+    eta = max(gl1, 0.8 * 1e-4 / gl1)
+    ref = O.newton_solve(P, gu, gl1, eta, 0.0)
+    ref_du = ref.d_u - (rP @ ref.d_u) / rP.sum()
+    out = {}
+    for flag in ("1", "0"):
+        monkeypatch.setenv("EOT_CG_PERSIST", flag)
+        prob = Problem(t(C, torch.float32), precision="mixed")
+        du, dv, rho, it = H.newton_solve(prob, t(u), t(v), gamma, t(rt), eta, 0.0)
+        out[flag] = (du.cpu().numpy(), rho, it)
+        diff = out[flag][0] - ref_du
+        assert np.abs(diff - diff.mean()).sum() <= 1e-5 * np.abs(ref_du).sum()
+        assert abs(it - ref.cg_iters) <= 1 + ref.cg_solves
+    assert out["1"][1] == out["0"][1]
