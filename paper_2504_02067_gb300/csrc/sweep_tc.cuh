@@ -18,18 +18,18 @@
 // with |x|^2 precomputed as an FP32 pair from FP64), then the exponent exactly
 // as the SIMT point sweep does (expo), exp, and the reductions.
 //
-// CTA roles (576 threads, one CTA per SM: 146 KB of shared memory):
+// CTA roles (320 threads, one CTA per SM: 177 KB of shared memory):
 //   warp 0, lane 0: bulk copies (the own 128 points' slices once; the other
 //     side's 48-point tiles into two buffers) and the MMAs of each tile into one
 //     of two TMEM accumulator buffers (5 levels x 48 columns each);
 //   warp 1: TMEM allocation (512 columns) and release;
-//   warps 2-17: epilogue. Warp w reads TMEM lanes 32 (w mod 4) .. +31 (one own
-//     point per thread) and a quarter (12) of the tile's 48 columns.
-// The other side's per-point data of a tile (h, scale, |y|^2, weights) arrive in
-// shared memory with the tile's slices (slot tile mod 4: a slot is refilled only
-// after the epilogue of the tile four back has finished).
+//   warps 2-9: epilogue. Warp w reads TMEM lanes 32 (w mod 4) .. +31 (one own
+//     point per thread) and half (24) of the tile's 48 columns.
+// The other side's per-point data (h, scale, |y|^2, weights) are read by the
+// epilogue straight from global memory (the same address in all lanes: one L1
+// broadcast).
 // Hand-offs are mbarriers: full[b] (copies landed), mmad[b] (MMAs of buffer b
-// done: accumulators readable and the slice buffer reusable), tfree[b] (the 16
+// done: accumulators readable and the slice buffer reusable), tfree[b] (the 8
 // epilogue warps have read buffer b). Every wait is bounded (tc.cuh).
 #pragma once
 #include <cuda_bf16.h>
@@ -44,9 +44,9 @@ constexpr int kM = 128;     // own points per CTA = TMEM lanes = MMA M
 constexpr int kN = 48;      // other-side points per tile = MMA N
 constexpr int kSlices = 5;  // 8-bit digits per coordinate
 constexpr int kLevels = 5;  // s + t = 0 .. 4
-constexpr int kEpiWarps = 16;                 // 4 per TMEM lane quarter
+constexpr int kEpiWarps = 8;                  // 2 per TMEM lane quarter
 constexpr int kParts = kEpiWarps / 4;          // column parts of a tile
-constexpr int kPartCols = kN / kParts;         // 12 columns per epilogue warp and tile
+constexpr int kPartCols = kN / kParts;         // 24 columns per epilogue warp and tile
 constexpr int kTcThreads = 32 * (2 + kEpiWarps);
 constexpr int kTcWarps = kTcThreads / 32;
 constexpr uint32_t kRowB = 128;    // bytes per point and slice: 64 BF16 coordinates
@@ -55,10 +55,7 @@ constexpr uint32_t kOthSlice = kN * kRowB;                          // 6 KB
 constexpr uint32_t kOffOth = kSlices * kOwnSlice;                   // 80 KB
 constexpr int kSliceBufs = 3;                                       // tile tt: slice buffer tt % 3
 constexpr uint32_t kOffCol = kOffOth + kSliceBufs * kSlices * kOthSlice;  // + 90 KB
-constexpr int kColArrays = 7;                                       // h, scale, |y|^2 hi, lo, up to 3 weights
-constexpr uint32_t kColSlot = 8 * kN * 4;                           // 1536 bytes per tile
-constexpr int kColSlots = 4;                                        // tile tt uses slot tt % 4
-constexpr uint32_t kOffBar = kOffCol + kColSlots * kColSlot;        // + 6 KB
+constexpr uint32_t kOffBar = kOffCol;
 constexpr uint32_t kSmemBytes = kOffBar + 128 + 1024;               // barriers + 1024-byte alignment slack
 constexpr int kBufCols = kLevels * kN;                              // 240 TMEM columns per buffer
 constexpr uint32_t kTmemCols = 512;
@@ -217,18 +214,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_sweep_kernel(SweepArgs<float
       auto issue = [&](int tt) {
         const int sb = tt % kSliceBufs;
         const int64_t jt = j0 + (int64_t)tt * kN;
-        mbar_arrive_expect_tx(&full[sb], kSlices * kOthSlice + (4 + NW) * kN * 4);
+        mbar_arrive_expect_tx(&full[sb], kSlices * kOthSlice);
         const unsigned char* src = oth_src + jt * kRowB;
         for (int s = 0; s < kSlices; ++s)
           bulk_g2s(sm + kOffOth + (sb * kSlices + s) * kOthSlice, src + (int64_t)s * sq.npad * kRowB, kOthSlice,
                    &full[sb]);
-        float* cd = (float*)(sm + kOffCol + (tt & (kColSlots - 1)) * kColSlot);
-        bulk_g2s(cd + 0 * kN, ht + jt, kN * 4, &full[sb]);
-        bulk_g2s(cd + 1 * kN, sq.sc + jt, kN * 4, &full[sb]);
-        bulk_g2s(cd + 2 * kN, sq.nxh + jt, kN * 4, &full[sb]);
-        bulk_g2s(cd + 3 * kN, sq.nxl + jt, kN * 4, &full[sb]);
-#pragma unroll
-        for (int k = 0; k < NW; ++k) bulk_g2s(cd + (4 + k) * kN, wt[k] + jt, kN * 4, &full[sb]);
       };
       // Schedule: tiles 0 and 1 are prefetched; after committing tile tt the
       // copies of tile tt + 2 go into the slice buffer of tile tt - 1 once its
@@ -294,24 +284,25 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_sweep_kernel(SweepArgs<float
       const int b = tt & 1;
       if (!warp_wait(&mmad[b], (tt >> 1) & 1, ta.err)) break;  // also covers the tile's copies
       tc_fence_after();
-      const float* cd = (const float*)(sm + kOffCol + (tt & (kColSlots - 1)) * kColSlot);
+      const int64_t jt = j0 + (int64_t)tt * kN;
 #pragma unroll 1
-      for (int c = 0; c < kPartCols / 4; ++c) {
-        const int col0 = part * kPartCols + c * 4;
-        uint32_t lv[kLevels][4];
+      for (int c = 0; c < kPartCols / 8; ++c) {
+        const int col0 = part * kPartCols + c * 8;
+        uint32_t lv[kLevels][8];
 #pragma unroll
         for (int L = 0; L < kLevels; ++L)
-          tmem_ld4(tbase + lane_base + (uint32_t)(b * kBufCols + L * kN + col0), lv[L]);
+          tmem_ld8(tbase + lane_base + (uint32_t)(b * kBufCols + L * kN + col0), lv[L]);
         tmem_ld_wait();
         float acc[NA];
 #pragma unroll
         for (int k = 0; k < NA; ++k) acc[k] = 0.f;
 #pragma unroll
-        for (int jj = 0; jj < 4; ++jj) {
+        for (int jj = 0; jj < 8; ++jj) {
           const int cj = col0 + jj;
           if (j0 + (int64_t)tt * kN + cj >= j1) break;  // uniform across the warp
-          const float hb = cd[cj];
-          const float f = sc_own * cd[kN + cj] * 0x1p-16f;  // powers of two: exact
+          const int64_t j = jt + cj;
+          const float hb = ht[j];
+          const float f = sc_own * sq.sc[j] * 0x1p-16f;  // powers of two: exact
           float gh, gl;
           two_sum(__uint_as_float(lv[0][jj]), __uint_as_float(lv[1][jj]) * 0x1p-8f, gh, gl);
           gl += __uint_as_float(lv[2][jj]) * 0x1p-16f +
@@ -319,14 +310,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_sweep_kernel(SweepArgs<float
           gh *= f;
           gl *= f;
           float s1, e1, Dh, e2;
-          two_sum(nxh, cd[2 * kN + cj], s1, e1);
+          two_sum(nxh, sq.nxh[j], s1, e1);
           two_sum(s1, -2.f * gh, Dh, e2);
-          const float Dl = e2 + ((e1 + (nxl + cd[3 * kN + cj])) - 2.f * gl);
+          const float Dl = e2 + ((e1 + (nxl + sq.nxl[j])) - 2.f * gl);
           if constexpr (!LSE) {
             const float ex = expT(expo<true>(h + hb, Kh, Kl, Dh, Dl));
 #pragma unroll
             for (int k = 0; k < NR; ++k) {
-              const float w = cd[(4 + k) * kN + cj];
+              const float w = wt[k][j];
               if ((SQM >> k) & 1) acc[k] = fmaf(ex * ex, w, acc[k]);
               else acc[k] = fmaf(ex, w, acc[k]);
             }
@@ -347,7 +338,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_sweep_kernel(SweepArgs<float
               Ca[0] *= fsc;
               tv = expo<true>(hm + hb, Kh, Kl, Dh, Dl);
             }
-            acc[0] = fmaf(expT(tv), cd[4 * kN + cj], acc[0]);
+            acc[0] = fmaf(expT(tv), wt[0][j], acc[0]);
           }
         }
 #pragma unroll
