@@ -149,6 +149,23 @@ class ClockSampler:
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
 
 
+def max_over_ranks(value, world, device=None):
+    """The job's time is the slowest rank's: MAX all-reduce of one float over the
+    process group (identity for a single process)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
+def replica_seed(rank):
+    """Replicas only: every rank solves its own problem of the workload, seeded by its rank."""
+    return rank
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -194,7 +211,7 @@ def run_ours(args):
 
     E.build()
     dev = torch.device("cuda", local)
-    p = W.grid_problem_4096(rank, args.cost)
+    p = W.grid_problem_4096(replica_seed(rank), args.cost)
     C_h = torch.from_numpy(p["C"]).pin_memory()
     r_h = torch.from_numpy(p["r"]).pin_memory()
     c_h = torch.from_numpy(p["c"]).pin_memory()
@@ -233,11 +250,7 @@ def run_ours(args):
     barrier()
     clocks = sampler.stop()
     launches = h.launches() - launches0
-    total = sum(times)
-    if world > 1:
-        t = torch.tensor([total], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total = t.item()
+    total = max_over_ranks(sum(times), world, dev)
     sec = total / args.steps
     last = stats[-1]
     sweeps = last["sweeps_total"]
@@ -261,11 +274,7 @@ def run_ours(args):
         e1.record(stream)
         e1.synchronize()
         e_times.append(e0.elapsed_time(e1) / 1e3)
-    e2e = sum(e_times) / len(e_times)
-    if world > 1:
-        t = torch.tensor([e2e], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e = t.item()
+    e2e = max_over_ranks(sum(e_times) / len(e_times), world, dev)
 
     # ---- roofline of the dominant kernels (CG column / row halves) ----
     bytes_per_launch = N * N * 4  # the FP32 cost streamed once per sweep (vectors are O(n))
