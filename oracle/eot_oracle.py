@@ -286,6 +286,29 @@ def chi_sinkhorn(u, v, gamma, C, r, c, log_rP, eps_chi, max_iter=100000):
     return u, v, log_rP, it
 
 
+def sinkhorn_project(u, v, gamma, C, r, c, eps, max_iter=1_000_000):
+    """Sinkhorn as the Bregman projection of Alg. 1 (MDOT-Sinkhorn, the paper's
+    main comparison, Sec. 4): the column fix, then alternating row and column
+    fixes while ||grad g||_1 = ||r - r(P)||_1 > eps, then the same last row step
+    as Alg. 4. Returns (u, v, ProjectStats) with sinkhorn_iters counted."""
+    st = ProjectStats()
+    log_r, log_c = np.log(r), np.log(c)
+    v = log_c - lse_c(u[:, None] - gamma * C)
+    log_rP = log_row_sum(u, v, gamma, C)
+    grad_l1 = float(np.abs(r - np.exp(log_rP)).sum())
+    while grad_l1 > eps:
+        if st.sinkhorn_iters >= max_iter:
+            st.ok = False
+            break
+        u = u + log_r - log_rP
+        v = log_c - lse_c(u[:, None] - gamma * C)
+        log_rP = log_row_sum(u, v, gamma, C)
+        grad_l1 = float(np.abs(r - np.exp(log_rP)).sum())
+        st.sinkhorn_iters += 1
+    u = u + log_r - log_rP
+    return u, v, st
+
+
 # --------------------------------------------------------------------------
 # Algorithm 4: TruncatedNewtonProject
 # --------------------------------------------------------------------------
@@ -440,7 +463,8 @@ class SolveResult:
 
 
 def mdot(C, r, c, gamma_i=2.0 ** 4, gamma_f=2.0 ** 12, p=1.5, q1=2.0, w_r=0.45,
-         tol_final=1e-6, round_gamma=None, max_stages=200, max_newton=200, max_cg=None):
+         tol_final=1e-6, round_gamma=None, max_stages=200, max_newton=200, max_cg=None,
+         projector="newton"):
     """Algorithm 1 (MDOT) driving Algorithm 4, Sec. 2.2 and Sec. 3.
 
     Line 1:  t <- 1, gamma^(1) <- min(gamma_i, gamma_f), q^(1) <- q, gamma^(0) <- 0
@@ -460,6 +484,8 @@ def mdot(C, r, c, gamma_i=2.0 ** 4, gamma_f=2.0 ** 12, p=1.5, q1=2.0, w_r=0.45,
     Reading: round_gamma (e.g. a round-to-float32 map) is applied to every
     gamma^(t) so that a reduced-precision solver and this oracle see the same
     temperatures.
+    projector="sinkhorn" replaces Alg. 4 by sinkhorn_project (MDOT-Sinkhorn); a
+    stage then has no Newton steps, so AdjustSchedule sees delta_min = +inf.
     """
     rg = round_gamma or (lambda g: g)
     n, m = C.shape
@@ -497,8 +523,11 @@ def mdot(C, r, c, gamma_i=2.0 ** 4, gamma_f=2.0 ** 12, p=1.5, q1=2.0, w_r=0.45,
         if t == 1:
             z = (np.log(rs), np.log(cs))
             z_prev = z
-        u, v, st = truncated_newton_project(z[0], z[1], gamma, C, rs, cs, eps_d / 2.0,
-                                            rho_last, max_newton=max_newton, max_cg=max_cg)
+        if projector == "sinkhorn":
+            u, v, st = sinkhorn_project(z[0], z[1], gamma, C, rs, cs, eps_d / 2.0)
+        else:
+            u, v, st = truncated_newton_project(z[0], z[1], gamma, C, rs, cs, eps_d / 2.0,
+                                                rho_last, max_newton=max_newton, max_cg=max_cg)
         rho_last = st.rho_last
         ok = ok and st.ok
         totals["newton"] += st.newton_steps

@@ -467,3 +467,19 @@ def test_mdot_single_row_or_column_is_product_plan(n, m):
     assert res.ok
     assert np.abs(P - np.outer(r, c)).max() <= 1e-12
     assert O.marginal_l1_error(res.u, res.v, 4096.0, C, r, c) <= 1e-12
+
+
+def test_mdot_sinkhorn_reaches_the_same_optimum():
+    """MDOT with Sinkhorn projections (the paper's comparison) converges to the
+    same unique plan as with TruncatedNewtonProject (Sec. 2.1: strictly convex
+    problem), each within its marginal tolerance."""
+    rng = np.random.default_rng(13)
+    C = rng.uniform(0, 1, size=(40, 33))
+    r = rng.dirichlet(np.ones(40))
+    c = rng.dirichlet(np.ones(33))
+    a = O.mdot(C, r, c, gamma_i=16.0, gamma_f=512.0, tol_final=1e-8)
+    b = O.mdot(C, r, c, gamma_i=16.0, gamma_f=512.0, tol_final=1e-8, projector="sinkhorn")
+    assert a.ok and b.ok and b.newton_steps == 0 and b.sinkhorn_iters > 0
+    assert O.marginal_l1_error(b.u, b.v, 512.0, C, r, c) <= 1e-8
+    Pa, Pb = O.plan(a.u, a.v, 512.0, C), O.plan(b.u, b.v, 512.0, C)
+    assert np.abs(Pa - Pb).sum() <= 1e-6
