@@ -314,6 +314,25 @@ def run_ours(args):
             torch.cuda.synchronize()
             plain = {"seconds": time.perf_counter() - t0, "reached": False, "error": str(ex)[:160]}
 
+    # ---- MDOT-Sinkhorn on the same problem (Sec. 4's comparison method) ----
+    mdot_sk = None
+    if not args.no_sinkhorn:
+        prm_sk = E.default_params(gamma_i=GAMMA_I, gamma_f=GAMMA_F, tol_final=TOL,
+                                  projector=E.PROJECT_SINKHORN)
+        h.eot_solve(prob, prm_sk, u, v)
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sk = h.eot_solve(prob, prm_sk, u, v).as_dict()
+        e1.record(stream)
+        e1.synchronize()
+        sk_sec = e0.elapsed_time(e1) / 1e3
+        mdot_sk = {"seconds": round(sk_sec, 5), "marg_err_l1": sk["marg_err_l1"],
+                   "reached_tol": sk["marg_err_l1"] <= TOL, "stages": sk["stages"],
+                   "sinkhorn_iters": sk["sinkhorn_iters"], "sweeps_total": sk["sweeps_total"],
+                   "newton_over_sinkhorn_time": round(sec / sk_sec, 4),
+                   "newton_over_sinkhorn_sweeps": round(sweeps / sk["sweeps_total"], 4)}
+
     result = None
     if rank == 0:
         cpu = None
@@ -344,7 +363,7 @@ def run_ours(args):
                     "h2d_bytes_per_step": int(C_h.numel() * 4 + r_h.numel() * 8 + c_h.numel() * 8),
                     "d2h_bytes_per_step": int(2 * N * 8)},
             "gpu_launches": int(launches), "roofline": roofline, "cpu_baseline": cpu,
-            "plain_fp32": plain, "clocks": clocks,
+            "plain_fp32": plain, "mdot_sinkhorn": mdot_sk, "clocks": clocks,
         }
         print(json.dumps(result), flush=True)
     h.close()
@@ -651,6 +670,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-sinkhorn", action="store_true",
+                    help="skip the MDOT-Sinkhorn comparison solve on the headline workload")
     ap.add_argument("--profile-sweep", type=int, default=-1,
                     help="run only eot_sweep_bench of this kind (0 CG column, 1 CG row, 2 HVP, 3 row LSE)")
     ap.add_argument("--profile-iters", type=int, default=3)

@@ -91,7 +91,13 @@ typedef struct {
   int32_t max_newton;  /* Newton steps per stage; default 200 */
   int32_t max_cg;      /* CG iterations per linear solve; default min(4n, 2000) when 0 */
   int32_t max_ls;      /* Armijo halvings per step; default 30 */
+  int32_t projector;   /* Bregman projection of each stage: EOT_PROJECT_NEWTON (Alg. 4,
+                          default) or EOT_PROJECT_SINKHORN (alternating row/column fixes
+                          until ||grad g||_1 <= eps: MDOT-Sinkhorn, Sec. 4) */
+  int32_t max_sinkhorn; /* Sinkhorn iterations per projection; default 10^6 when 0 */
 } eot_params;
+
+enum { EOT_PROJECT_NEWTON = 0, EOT_PROJECT_SINKHORN = 1 };
 
 typedef struct {       /* host-side counters of one eot_solve call */
   int64_t sweeps_cg;        /* O(nm) sweeps inside linear CG (2 per CG iteration) */

@@ -36,7 +36,11 @@ class EotParams(ctypes.Structure):
                 ("p", ctypes.c_double), ("q1", ctypes.c_double), ("w_r", ctypes.c_double),
                 ("tol_final", ctypes.c_double), ("max_stages", ctypes.c_int32),
                 ("max_newton", ctypes.c_int32), ("max_cg", ctypes.c_int32),
-                ("max_ls", ctypes.c_int32)]
+                ("max_ls", ctypes.c_int32), ("projector", ctypes.c_int32),
+                ("max_sinkhorn", ctypes.c_int32)]
+
+
+PROJECT_NEWTON, PROJECT_SINKHORN = 0, 1
 
 
 class EotStats(ctypes.Structure):

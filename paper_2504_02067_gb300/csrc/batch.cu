@@ -1243,6 +1243,8 @@ extern "C" eot_status eot_solve_batched(eot_handle h, int32_t nprob, const eot_p
     const eot_params& prm = *params;
     if (!(prm.gamma_i > 0.0) || !(prm.gamma_f > 0.0) || prm.gamma_f >= kSplitLimit)
       throw EotError{EOT_ERR_INVALID_ARG, "0 < gamma_i, 0 < gamma_f < 2^19"};
+    if (prm.projector != EOT_PROJECT_NEWTON)
+      throw EotError{EOT_ERR_INVALID_ARG, "batched solves use the Newton projector (Alg. 4)"};
     const cudaStream_t st = (cudaStream_t)stream;
     if (prec == EOT_PREC_FP64) return run_batched<double>(h, nprob, probs, prm, u, v, status_out, stats, st);
     if (prec == EOT_PREC_MIXED) return run_batched<float>(h, nprob, probs, prm, u, v, status_out, stats, st);

@@ -226,6 +226,8 @@ eot_params eot_params_default(void) {
   p.max_newton = 200;
   p.max_cg = 0;
   p.max_ls = 30;
+  p.projector = EOT_PROJECT_NEWTON;
+  p.max_sinkhorn = 0;
   return p;
 }
 
@@ -284,7 +286,8 @@ eot_status eot_solve(eot_handle h, const eot_problem* prob, const eot_params* pa
     check_gamma(prm.gamma_f);
     check_gamma(prm.gamma_i);
     if (!(prm.p >= 1.0) || !(prm.q1 > 1.0) || !(prm.w_r > 0.25 && prm.w_r < 0.5) ||
-        !(prm.tol_final > 0.0) || prm.max_stages < 1 || prm.max_newton < 1 || prm.max_ls < 1)
+        !(prm.tol_final > 0.0) || prm.max_stages < 1 || prm.max_newton < 1 || prm.max_ls < 1 ||
+        (prm.projector != EOT_PROJECT_NEWTON && prm.projector != EOT_PROJECT_SINKHORN) || prm.max_sinkhorn < 0)
       throw EotError{EOT_ERR_INVALID_ARG, "invalid eot_params"};
     if (stats) std::memset(stats, 0, sizeof(*stats));
     cudaStream_t st = (cudaStream_t)stream;

@@ -471,6 +471,20 @@ static __global__ void axpy4_kernel(int64_t n, double* y, double b, const double
   }
 }
 
+// One Sinkhorn row fix of the MDOT-Sinkhorn projector, taken only while the
+// last row sweep's ||r~ - r(P)||_1 (sc[SC_GL1]) is above eps: u <- u + log r~ -
+// log r(P). Once the test passes, u stays fixed and the sweeps that follow
+// recompute the same v and log r(P), so the host may check every few
+// iterations. sc[SC_AUX1] counts the fixes taken.
+static __global__ void sk_step_kernel(int64_t n, double* u, const double* logrt, const double* logrP, double* sc,
+                                      double eps) {
+  pdl_wait();
+  if (!(sc[SC_GL1] > eps)) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) sc[SC_AUX1] += 1.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    u[i] = (u[i] + logrt[i]) - logrP[i];
+}
+
 // Asymmetric smoothing (Sec. 3.4): t = (1 - w eps) r + (w eps / n); log t.
 static __global__ void smooth_kernel(int64_t n, const double* r, double w_eps, double* t, double* logt) {
   pdl_wait();

@@ -724,6 +724,51 @@ struct Solver {
     }
   }
 
+  // ---------------- MDOT-Sinkhorn projection (Sec. 4 comparison) ----------------
+  // Column fix, then row and column fixes while ||r~ - r(P)||_1 > eps, then the
+  // closing row step of Alg. 4. The host reads the gradient norm every kSkCheck
+  // iterations; sk_step_kernel makes the iterations past the stopping point
+  // no-ops, so the result and the count are those of a per-iteration test.
+  static constexpr int kSkCheck = 8;
+  bool project_sinkhorn(double* u, double* v, double eps, const eot_params& prm, double* gl1_out) {
+    double* rt = h->rt;
+    double* logrt = h->logrt;
+    double* logct = h->logct;
+    sweep_bucket = &cnt.sweeps_sk;
+    col_lse(u, nullptr, v, nullptr, 0.0, logct, v, 1, SC_AUX0, 0.0);
+    row_lse(u, v, logrt, h->logrP, h->rowmax, rt);
+    set_scalar(SC_AUX1, 0.0);
+    const int64_t max_it = prm.max_sinkhorn > 0 ? prm.max_sinkhorn : 1000000;
+    double gl1 = read()[SC_GL1];
+    int64_t it = 0;
+    bool ok = true;
+    while (gl1 > eps) {
+      if (it >= max_it) {
+        ok = false;
+        break;
+      }
+      const int64_t k = std::min<int64_t>(kSkCheck, max_it - it);
+      for (int64_t j = 0; j < k; ++j) {
+        launch_k(sk_step_kernel, dim3(vg_n), dim3(kThreads), st, n, u, (const double*)logrt,
+                 (const double*)h->logrP, h->sc, eps);
+        EOT_LAUNCH_CHECK();
+        h->launches++;
+        col_lse(u, nullptr, v, nullptr, 0.0, logct, v, 1, SC_AUX0, 0.0);
+        row_lse(u, v, logrt, h->logrP, h->rowmax, rt);
+      }
+      const double* s = read();
+      gl1 = s[SC_GL1];
+      it = (int64_t)s[SC_AUX1];
+    }
+    cnt.sk_iters += it;
+    if (trace)
+      std::fprintf(stderr, "[eot] sinkhorn stage gamma %.6g iters %lld grad %.4e eps %.4e\n", gamma_host,
+                   (long long)it, gl1, eps);
+    axpy(n, u, 1.0, logrt, 1.0, h->logrP, -1.0);
+    *gl1_out = gl1;
+    return ok;
+  }
+
   // ---------------- Alg. 4: TruncatedNewtonProject ----------------
   // (u, v) in/out; targets (rt, ct) = smoothed marginals with logs; tolerance eps.
   // Returns false if the Newton budget ran out. delta_min is reported.

@@ -184,8 +184,12 @@ void run_solve(eot_handle h, const eot_problem* P, const eot_params* prm_in, dou
     }
     S.set_scalar(SC_GAMMA, gamma);
     double dmin = INFINITY;
-    if (!S.project(u, v, eps_d / 2.0, prm, max_cg, mode, &dmin, &gl1))
+    if (prm.projector == EOT_PROJECT_SINKHORN) {
+      if (!S.project_sinkhorn(u, v, eps_d / 2.0, prm, &gl1))
+        throw EotError{EOT_ERR_MAXNEWTON, "Sinkhorn projection exceeded max_sinkhorn"};
+    } else if (!S.project(u, v, eps_d / 2.0, prm, max_cg, mode, &dmin, &gl1)) {
       throw EotError{EOT_ERR_MAXNEWTON, "TruncatedNewtonProject exceeded max_newton"};
+    }
     // AdjustSchedule (Sec. 3.3); a stage without Newton steps has delta_min = +inf
     if (dmin > 0.95) q = std::min(2.0, q * q);
     else if (dmin < 0.8) q = std::sqrt(q);

@@ -52,5 +52,5 @@ def test_library_loads_and_binding_matches(libpath):
     assert p.gamma_i == 16.0 and p.gamma_f == 4096.0 and p.p == 1.5 and p.w_r == 0.45
     assert L.eot_status_string(3) == b"EOT_ERR_CG_MAXITER"
     assert ctypes.sizeof(binding.EotProblem) == 88
-    assert ctypes.sizeof(binding.EotParams) == 64
+    assert ctypes.sizeof(binding.EotParams) == 72
     assert ctypes.sizeof(binding.EotStats) == 112
