@@ -314,6 +314,17 @@ def run_ours(args):
             torch.cuda.synchronize()
             plain = {"seconds": time.perf_counter() - t0, "reached": False, "error": str(ex)[:160]}
 
+    # ---- Round (Alg. 1's closing step) of the last solve's plan ----
+    h.eot_solve(prob, prm, u, v)
+    flush.zero_()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    rcost, rcorr = h.eot_round(prob, u, v, GAMMA_F)
+    e1.record(stream)
+    e1.synchronize()
+    rounded = {"transport_cost": rcost, "correction_l1": rcorr,
+               "ms": round(e0.elapsed_time(e1), 3)}
+
     # ---- MDOT-Sinkhorn on the same problem (Sec. 4's comparison method) ----
     mdot_sk = None
     if not args.no_sinkhorn:
@@ -332,6 +343,26 @@ def run_ours(args):
                    "sinkhorn_iters": sk["sinkhorn_iters"], "sweeps_total": sk["sweeps_total"],
                    "newton_over_sinkhorn_time": round(sec / sk_sec, 4),
                    "newton_over_sinkhorn_sweeps": round(sweeps / sk["sweeps_total"], 4)}
+        # plain Sinkhorn at gamma_f (MDOT-Sinkhorn with gamma_i = gamma_f, Sec. 4),
+        # capped at 200000 iterations
+        prm_pl = E.default_params(gamma_i=GAMMA_F, gamma_f=GAMMA_F, tol_final=TOL,
+                                  projector=E.PROJECT_SINKHORN, max_sinkhorn=200000)
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        try:
+            pl = h.eot_solve(prob, prm_pl, u, v).as_dict()
+            e1.record(stream)
+            e1.synchronize()
+            mdot_sk["plain_sinkhorn_gamma_f"] = {
+                "seconds": round(e0.elapsed_time(e1) / 1e3, 4), "sinkhorn_iters": pl["sinkhorn_iters"],
+                "marg_err_l1": pl["marg_err_l1"], "reached_tol": pl["marg_err_l1"] <= TOL}
+        except E.EotError as ex:
+            e1.record(stream)
+            e1.synchronize()
+            mdot_sk["plain_sinkhorn_gamma_f"] = {
+                "seconds": round(e0.elapsed_time(e1) / 1e3, 4), "reached_tol": False,
+                "error": str(ex)[:120]}
 
     result = None
     if rank == 0:
@@ -363,7 +394,7 @@ def run_ours(args):
                     "h2d_bytes_per_step": int(C_h.numel() * 4 + r_h.numel() * 8 + c_h.numel() * 8),
                     "d2h_bytes_per_step": int(2 * N * 8)},
             "gpu_launches": int(launches), "roofline": roofline, "cpu_baseline": cpu,
-            "plain_fp32": plain, "mdot_sinkhorn": mdot_sk, "clocks": clocks,
+            "plain_fp32": plain, "rounded": rounded, "mdot_sinkhorn": mdot_sk, "clocks": clocks,
         }
         print(json.dumps(result), flush=True)
     h.close()

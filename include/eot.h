@@ -160,6 +160,20 @@ eot_status eot_newton_solve(eot_handle h, const eot_problem* prob, const double*
                             double rho0, int32_t max_cg, double* du_out, double* dv_out,
                             double* rho_out, int32_t* cg_iters_out, void* stream);
 
+/* Round (Alg. 1's closing step; the paper cites Algorithm 2 of Altschuler, Weed and
+ * Rigollet, 2017) of P = P(u, v; gamma) onto U(r, c), kept implicit:
+ *   x = min(r / r(P), 1), y = min(c / c(D(x) P), 1), F = D(x) P D(y),
+ *   a = r - r(F), b = c - c(F),  Round(P) = F + a b^T / ||a||_1,
+ * where F = P(u + log x, v + log y; gamma). Evaluated in FP64 (three passes over C).
+ * u, v: device [n], [m]. Outputs, each nullable: u_out [n] = u + log x (-inf where
+ * r_i = 0), v_out [m] = v + log y, a_out [n], b_out [m] (device FP64);
+ * cost_out = <Round(P), C> (host; C as the solver sees it, s_C |x - y|^2 for points),
+ * corr_l1_out = ||a||_1 (host). prob->r and prob->c are required.
+ * Errors: INVALID_ARG, CUDA. Synchronises. */
+eot_status eot_round(eot_handle h, const eot_problem* prob, const double* u, const double* v,
+                     double gamma, double* u_out, double* v_out, double* a_out, double* b_out,
+                     double* cost_out, double* corr_l1_out, void* stream);
+
 /* Full solve: MDOT (Alg. 1) with adaptive q and asymmetric smoothing, each
  * stage projected by TruncatedNewtonProject (Alg. 4 with Alg. 2 and Alg. 3).
  * u: device [n], v: device [m]: outputs (the last projected potentials at gamma_f).

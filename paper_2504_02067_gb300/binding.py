@@ -61,7 +61,7 @@ class EotStats(ctypes.Structure):
 EXPORTS = ["eot_create", "eot_destroy", "eot_last_error", "eot_status_string",
            "eot_params_default", "eot_marginals", "eot_hvp", "eot_newton_solve", "eot_solve",
            "eot_backward", "eot_sweep_bench", "eot_marginals_noalloc", "eot_kernel_launches",
-           "eot_solve_batched", "eot_batch_last_config"]
+           "eot_solve_batched", "eot_batch_last_config", "eot_round"]
 
 _LIB = None
 
@@ -99,10 +99,11 @@ def load_library(path=None):
                                     vp]
     L.eot_batch_last_config.argtypes = [vp, ctypes.POINTER(i32)]
     L.eot_batch_last_config.restype = ctypes.c_int
+    L.eot_round.argtypes = [vp, P, vp, vp, dbl, vp, vp, vp, vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl), vp]
     L.eot_kernel_launches.argtypes = [vp]
     L.eot_kernel_launches.restype = i64
     for f in ("eot_create", "eot_destroy", "eot_marginals", "eot_hvp", "eot_newton_solve",
-              "eot_solve", "eot_backward", "eot_sweep_bench", "eot_solve_batched"):
+              "eot_solve", "eot_backward", "eot_sweep_bench", "eot_solve_batched", "eot_round"):
         getattr(L, f).restype = ctypes.c_int
     if path == _build.LIBPATH:
         _LIB = L
@@ -195,6 +196,17 @@ class Handle:
         self.check(self.lib.eot_marginals(self.h, prob.ref(), _p(u), _p(v), float(gamma),
                                           _p(r_out), _p(c_out), _p(log_r_out), _p(log_c_out),
                                           _p(total_out), _stream(stream)))
+
+    def eot_round(self, prob, u, v, gamma, u_out=None, v_out=None, a_out=None, b_out=None,
+                  stream=None):
+        """Round of P(u, v; gamma) onto U(r, c) (eot_round of include/eot.h); returns
+        (<Round(P), C>, ||a||_1) and fills the given implicit-plan outputs."""
+        cost = ctypes.c_double(0.0)
+        corr = ctypes.c_double(0.0)
+        self.check(self.lib.eot_round(self.h, prob.ref(), _p(u), _p(v), float(gamma), _p(u_out),
+                                      _p(v_out), _p(a_out), _p(b_out), ctypes.byref(cost),
+                                      ctypes.byref(corr), _stream(stream)))
+        return cost.value, corr.value
 
     def eot_hvp(self, prob, u, v, gamma, s, du, dv, out_u, out_v, r_out=None, c_out=None,
                 stream=None):

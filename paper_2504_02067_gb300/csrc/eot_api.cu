@@ -191,6 +191,7 @@ eot_status eot_destroy(eot_handle h) {
   if (h->bt_mem) cudaFree(h->bt_mem);
   if (h->tc_mem) cudaFree(h->tc_mem);
   if (h->pcg_mem) cudaFree(h->pcg_mem);
+  if (h->rd_mem) cudaFree(h->rd_mem);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   delete h;
   return EOT_OK;
@@ -241,6 +242,19 @@ eot_status eot_marginals(eot_handle h, const eot_problem* prob, const double* u,
     cudaStream_t st = (cudaStream_t)stream;
     if (is_f64(prob)) run_marginals<double>(h, prob, u, v, gamma, r_out, c_out, log_r_out, log_c_out, total_out, st);
     else run_marginals<float>(h, prob, u, v, gamma, r_out, c_out, log_r_out, log_c_out, total_out, st);
+  });
+}
+
+eot_status eot_round(eot_handle h, const eot_problem* prob, const double* u, const double* v,
+                     double gamma, double* u_out, double* v_out, double* a_out, double* b_out,
+                     double* cost_out, double* corr_l1_out, void* stream) {
+  return guarded(h, [&] {
+    check_problem(h, prob, true);
+    check_gamma(gamma);
+    if (!u || !v) throw EotError{EOT_ERR_INVALID_ARG, "u and v are required"};
+    cudaStream_t st = (cudaStream_t)stream;
+    if (is_f64(prob)) run_round<double>(h, prob, u, v, gamma, u_out, v_out, a_out, b_out, cost_out, corr_l1_out, st);
+    else run_round<float>(h, prob, u, v, gamma, u_out, v_out, a_out, b_out, cost_out, corr_l1_out, st);
   });
 }
 

@@ -82,6 +82,8 @@ struct eot_handle_s {
   // single-problem buffers must not free it) and the autotuner's choices
   void* pcg_mem = nullptr;  // persistent CG kernel: CTA partials, barrier counter (own block)
   size_t pcg_bytes = 0;
+  void* rd_mem = nullptr;  // Round: FP64 vectors and column partials (own block)
+  size_t rd_bytes = 0;
   void* tc_mem = nullptr;  // tensor-core point path: digit slices and row data (own block)
   size_t tc_bytes = 0;
   void* bt_mem = nullptr;

@@ -904,5 +904,9 @@ void run_backward_dense(eot_handle h, const eot_problem* P, const double* u, con
 template <class T>
 void run_backward_points(eot_handle h, const eot_problem* P, const double* u, const double* v,
                          double gamma, double scale, float* dX, float* dY, cudaStream_t st);
+template <class T>
+void run_round(eot_handle h, const eot_problem* P, const double* u, const double* v, double gamma,
+               double* u_out, double* v_out, double* a_out, double* b_out, double* cost_out, double* corr_out,
+               cudaStream_t st);
 
 }  // namespace eot

@@ -17,4 +17,6 @@ template double run_sweep_bench<double>(eot_handle, const eot_problem*, const do
                                       double, int, int, cudaStream_t);
 template void run_backward_points<double>(eot_handle, const eot_problem*, const double*, const double*,
                                            double, double, float*, float*, cudaStream_t);
+template void run_round<double>(eot_handle, const eot_problem*, const double*, const double*, double, double*,
+                            double*, double*, double*, double*, double*, cudaStream_t);
 }  // namespace eot

@@ -3,6 +3,7 @@
 #pragma once
 #include <algorithm>
 
+#include "round.cuh"
 #include "solver.cuh"
 
 namespace eot {
@@ -346,6 +347,66 @@ void run_backward_points(eot_handle h, const eot_problem* P, const double* u, co
     S.template grad_pts<false>(f, h->colfac, dY);
   }
   S.read();
+}
+
+}  // namespace eot
+
+namespace eot {
+
+// Round (see round.cuh) of P(u, v; gamma) onto U(r, c), implicit: outputs
+// u + log x, v + log y, a, b (device, nullable) and <Round(P), C>, ||a||_1 (host,
+// nullable). gamma is rounded as the solver rounds it for this precision.
+template <class T>
+void run_round(eot_handle h, const eot_problem* P, const double* u, const double* v, double gamma,
+               double* u_out, double* v_out, double* a_out, double* b_out, double* cost_out, double* corr_out,
+               cudaStream_t st) {
+  Solver<T> S(h, P, st);
+  const int64_t n = P->n, m = P->m;
+  const double g = round_gamma<T>(gamma);
+  const int64_t strips = (m + 31) / 32;
+  int64_t nrb = std::min<int64_t>(64, std::max<int64_t>(1, (8 * (int64_t)h->sms + strips - 1) / strips));
+  nrb = std::min<int64_t>(nrb, n);
+  const int64_t rows_per = (n + nrb - 1) / nrb;
+  nrb = (n + rows_per - 1) / rows_per;
+  const size_t need = (size_t)(4 * n + 3 * m + nrb * m + 2) * sizeof(double);
+  if (need > h->rd_bytes) {
+    EOT_CUDA(cudaStreamSynchronize(st));
+    if (h->rd_mem) cudaFree(h->rd_mem);
+    h->rd_mem = nullptr;
+    h->rd_bytes = 0;
+    EOT_CUDA(cudaMalloc(&h->rd_mem, need));
+    h->rd_bytes = need;
+  }
+  double* w = (double*)h->rd_mem;
+  double* x = w;
+  double* a = a_out ? a_out : w + n;
+  double* rowc = w + 2 * n;
+  double* rowcb = w + 3 * n;
+  double* y = w + 4 * n;
+  double* b = b_out ? b_out : w + 4 * n + m;
+  double* part = w + 4 * n + 2 * m;
+  double* tot = part + nrb * m;
+  const int row_blocks = (int)std::min<int64_t>((n + 7) / 8, 32 * (int64_t)h->sms);
+  const dim3 col_grid((unsigned)strips, (unsigned)nrb);
+  const int fin_blocks = (int)std::min<int64_t>((m + rnd::kThreads - 1) / rnd::kThreads, 8 * (int64_t)h->sms);
+  auto go = [&](auto cost) {
+    rnd::round_row_kernel<<<row_blocks, rnd::kThreads, 0, st>>>(n, m, u, v, g, cost, P->r, nullptr, nullptr, nullptr,
+                                                              x, u_out, nullptr, nullptr, nullptr);
+    rnd::round_col_kernel<<<col_grid, rnd::kThreads, 0, st>>>(n, m, u, x, v, g, cost, rows_per, part);
+    rnd::round_colfin_kernel<<<fin_blocks, rnd::kThreads, 0, st>>>(m, (int)nrb, part, P->c, v, y, v_out, b);
+    rnd::round_row_kernel<<<row_blocks, rnd::kThreads, 0, st>>>(n, m, u, v, g, cost, P->r, x, y, b, nullptr,
+                                                              nullptr, a, rowc, rowcb);
+    rnd::round_total_kernel<<<1, 1024, 0, st>>>(n, a, rowc, rowcb, tot);
+    EOT_LAUNCH_CHECK();
+    h->launches += 5;
+  };
+  if (S.points) go(rnd::PointCost{S.X, S.Y, S.d, S.sC});
+  else if (P->kind == EOT_COST_DENSE_F64) go(rnd::DenseCost<double>{(const double*)P->C, P->ldc});
+  else go(rnd::DenseCost<float>{(const float*)P->C, P->ldc});
+  EOT_CUDA(cudaMemcpyAsync(h->h_sc + SC_COUNT - 2, tot, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  EOT_CUDA(cudaStreamSynchronize(st));
+  if (cost_out) *cost_out = h->h_sc[SC_COUNT - 2];
+  if (corr_out) *corr_out = h->h_sc[SC_COUNT - 1];
 }
 
 }  // namespace eot
