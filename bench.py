@@ -21,6 +21,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -197,6 +198,33 @@ def traffic_record():
 # our arm
 # ---------------------------------------------------------------------------
 
+def roofline_at_scale(h, E, dev, flush, peak, side=128):
+    """The same CG sweep kernels on a 128 x 128 grid (n = m = 16384, 1 GiB FP32
+    squared-Euclidean cost made on the device, larger than L2): one pass per
+    launch from HBM, each launch timed alone after the L2 overwrite."""
+    import torch
+    n = side * side
+    g = torch.arange(side, dtype=torch.float32, device=dev) / (side - 1)
+    px = g.repeat_interleave(side)
+    py = g.repeat(side)
+    C = ((px[:, None] - px[None, :]) ** 2 + (py[:, None] - py[None, :]) ** 2) * 0.5
+    w = torch.full((n,), 1.0 / n, dtype=torch.float64, device=dev)
+    prob = E.Problem(C, w, w, precision="mixed")
+    gen = torch.Generator(device="cpu").manual_seed(0)
+    u = (torch.full((n,), -math.log(n), dtype=torch.float64)
+         + 0.1 * torch.randn(n, generator=gen, dtype=torch.float64)).to(dev)
+    v = torch.full((n,), -math.log(n), dtype=torch.float64, device=dev)
+    nbytes = n * n * 4
+    out = {"workload": "grid128x128_sqeuclid_f32_n16384_gamma2^10", "bytes_per_launch": nbytes}
+    for kind, name in ((0, "cg_col_sweep"), (1, "cg_row_sweep")):
+        ms = h.eot_sweep_bench(prob, u, v, 1024.0, kind, 5, flush=flush)
+        gbs = nbytes / (ms * 1e-3) / 1e9
+        out[name] = {"us": round(ms * 1e3, 2), "achieved": round(gbs, 1), "frac": round(gbs / peak, 4)}
+    del C
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -277,15 +305,15 @@ def run_ours(args):
     e2e = max_over_ranks(sum(e_times) / len(e_times), world, dev)
 
     # ---- roofline of the dominant kernels (CG column / row halves) ----
+    # ms_hbm: each launch timed alone right after a 512 MiB overwrite (the cost
+    # comes from HBM); ms_l2warm: back-to-back launches (the cost stays in L2, as
+    # inside a solve)
     bytes_per_launch = N * N * 4  # the FP32 cost streamed once per sweep (vectors are O(n))
     kern = {}
     for kind, name in ((0, "cg_col_sweep"), (1, "cg_row_sweep")):
-        flushed = []
-        for _ in range(10):
-            flush.zero_()
-            flushed.append(h.eot_sweep_bench(prob, u, v, GAMMA_F, kind, 1))
+        cold = h.eot_sweep_bench(prob, u, v, GAMMA_F, kind, 10, flush=flush)
         warm = h.eot_sweep_bench(prob, u, v, GAMMA_F, kind, 50)
-        kern[name] = {"ms_hbm": statistics.median(flushed), "ms_l2warm": warm}
+        kern[name] = {"ms_hbm": cold, "ms_l2warm": warm}
     dom = max(kern, key=lambda k: kern[k]["ms_l2warm"])
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
@@ -297,7 +325,8 @@ def run_ours(args):
                 "peak_source": "measured" if peaks else "fallback",
                 "algorithmic_bytes_per_launch": bytes_per_launch,
                 "achieved_l2warm": round(bytes_per_launch / (kern[dom]["ms_l2warm"] * 1e-3) / 1e9, 1),
-                "sweeps_us": {k: {kk: round(vv * 1e3, 2) for kk, vv in d.items()} for k, d in kern.items()}}
+                "sweeps_us": {k: {kk: round(vv * 1e3, 2) for kk, vv in d.items()} for k, d in kern.items()},
+                "at_scale": roofline_at_scale(h, E, dev, flush, peak)}
 
     # ---- plain FP32 comparator (same workload, same tolerance) ----
     plain = None
@@ -686,8 +715,10 @@ def run_profile_sweep(args):
     rng = np.random.default_rng(0)
     u = torch.from_numpy(np.log(p["r"] + 1e-6) + rng.normal(0, 1, N)).to(dev)
     v = torch.from_numpy(np.log(p["c"] + 1e-6)).to(dev)
-    ms = h.eot_sweep_bench(prob, u, v, GAMMA_F, args.profile_sweep, args.profile_iters)
-    print(json.dumps({"kind": args.profile_sweep, "iters": args.profile_iters, "ms_per_launch": ms}))
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev) if args.profile_cold else None
+    ms = h.eot_sweep_bench(prob, u, v, GAMMA_F, args.profile_sweep, args.profile_iters, flush=flush)
+    print(json.dumps({"kind": args.profile_sweep, "iters": args.profile_iters, "cold": bool(args.profile_cold),
+                      "ms_per_launch": ms}))
     h.close()
 
 
@@ -706,6 +737,8 @@ def main():
     ap.add_argument("--profile-sweep", type=int, default=-1,
                     help="run only eot_sweep_bench of this kind (0 CG column, 1 CG row, 2 HVP, 3 row LSE)")
     ap.add_argument("--profile-iters", type=int, default=3)
+    ap.add_argument("--profile-cold", action="store_true",
+                    help="with --profile-sweep: time each launch alone after an L2 overwrite")
     ap.add_argument("--profile-points", type=int, default=-1,
                     help="run only eot_sweep_bench of this kind on the d = 64 point workload")
     ap.add_argument("--workload", default="grid4096", choices=["grid4096", "batch256", "d64", "colour"],

@@ -223,15 +223,20 @@ eot_status eot_backward(eot_handle h, const eot_problem* prob, const double* u, 
                         double gamma, double grad_scale, float* dC, float* dX, float* dY,
                         double* dr, double* dc, void* stream);
 
-/* Measurement aid: times `iters` back-to-back launches of one sweep kernel at (u, v)
- * with CUDA events recorded on `stream` (after an untimed set-up at the same point):
+/* Measurement aid: times `iters` launches of one sweep kernel at (u, v) with CUDA
+ * events recorded on `stream` (after an untimed set-up at the same point):
  *   kind 0: the CG column half  w = P^T p            (Alg. 2 inner CG, F_r(rho) p)
  *   kind 1: the CG row half     y = P (w / c(P)), q = r(P) p - rho y, <p, q>
  *   kind 2: the fused two-sided HVP sweep of eot_hvp
  *   kind 3: the row log-sum-exp sweep (Alg. 3 / Alg. 4 row updates)
- * ms_out: host, average milliseconds per launch. Synchronises. */
+ * flush == NULL: the launches run back to back between two events (the cost stays
+ * in L2 when it fits, as inside a solve). flush != NULL: a device buffer of
+ * flush_bytes (caller's, larger than L2) is overwritten on `stream` before each
+ * launch and each launch is timed alone, so every launch reads the cost from
+ * HBM. ms_out: host, average milliseconds per launch. Synchronises. */
 eot_status eot_sweep_bench(eot_handle h, const eot_problem* prob, const double* u, const double* v,
-                           double gamma, int32_t kind, int32_t iters, double* ms_out, void* stream);
+                           double gamma, int32_t kind, int32_t iters, void* flush, size_t flush_bytes,
+                           double* ms_out, void* stream);
 
 /* The marginals of eot_marginals without a handle and without allocating any
  * device memory, for callers that cannot allocate (their allocator or memory

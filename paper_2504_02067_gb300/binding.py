@@ -91,7 +91,7 @@ def load_library(path=None):
                                    ctypes.POINTER(dbl), ctypes.POINTER(i32), vp]
     L.eot_solve.argtypes = [vp, P, ctypes.POINTER(EotParams), vp, vp, ctypes.POINTER(EotStats), vp]
     L.eot_backward.argtypes = [vp, P, vp, vp, dbl, dbl, vp, vp, vp, vp, vp, vp]
-    L.eot_sweep_bench.argtypes = [vp, P, vp, vp, dbl, i32, i32, ctypes.POINTER(dbl), vp]
+    L.eot_sweep_bench.argtypes = [vp, P, vp, vp, dbl, i32, i32, vp, ctypes.c_size_t, ctypes.POINTER(dbl), vp]
     L.eot_marginals_noalloc.argtypes = [P, vp, vp, dbl, vp, vp, vp, vp]
     L.eot_marginals_noalloc.restype = ctypes.c_int
     L.eot_solve_batched.argtypes = [vp, i32, P, ctypes.POINTER(EotParams), ctypes.POINTER(vp),
@@ -236,11 +236,14 @@ class Handle:
                                          float(grad_scale), _p(dC), _p(dX), _p(dY), _p(dr),
                                          _p(dc), _stream(stream)))
 
-    def eot_sweep_bench(self, prob, u, v, gamma, kind, iters, stream=None):
+    def eot_sweep_bench(self, prob, u, v, gamma, kind, iters, flush=None, stream=None):
+        """Milliseconds per launch of sweep kind `kind`; with `flush` (a device
+        tensor larger than L2) every launch is timed alone after overwriting it."""
         ms = ctypes.c_double(0.0)
+        nbytes = flush.numel() * flush.element_size() if flush is not None else 0
         self.check(self.lib.eot_sweep_bench(self.h, prob.ref(), _p(u), _p(v), float(gamma),
-                                            int(kind), int(iters), ctypes.byref(ms),
-                                            _stream(stream)))
+                                            int(kind), int(iters), _p(flush), nbytes,
+                                            ctypes.byref(ms), _stream(stream)))
         return ms.value
 
     def eot_solve_batched(self, probs, params, us, vs, stream=None):

@@ -343,15 +343,16 @@ eot_status eot_backward(eot_handle h, const eot_problem* prob, const double* u, 
 }
 
 eot_status eot_sweep_bench(eot_handle h, const eot_problem* prob, const double* u, const double* v,
-                           double gamma, int32_t kind, int32_t iters, double* ms_out, void* stream) {
+                           double gamma, int32_t kind, int32_t iters, void* flush, size_t flush_bytes,
+                           double* ms_out, void* stream) {
   return guarded(h, [&] {
     check_problem(h, prob, false);
     check_gamma(gamma);
-    if (!u || !v || !ms_out || kind < 0 || kind > 3 || iters < 1)
-      throw EotError{EOT_ERR_INVALID_ARG, "u, v, ms_out required; kind in 0..3; iters >= 1"};
+    if (!u || !v || !ms_out || kind < 0 || kind > 3 || iters < 1 || (flush && flush_bytes == 0))
+      throw EotError{EOT_ERR_INVALID_ARG, "u, v, ms_out required; kind in 0..3; iters >= 1; flush_bytes > 0"};
     cudaStream_t st = (cudaStream_t)stream;
-    *ms_out = is_f64(prob) ? run_sweep_bench<double>(h, prob, u, v, gamma, kind, iters, st)
-                           : run_sweep_bench<float>(h, prob, u, v, gamma, kind, iters, st);
+    *ms_out = is_f64(prob) ? run_sweep_bench<double>(h, prob, u, v, gamma, kind, iters, flush, flush_bytes, st)
+                           : run_sweep_bench<float>(h, prob, u, v, gamma, kind, iters, flush, flush_bytes, st);
   });
 }
 

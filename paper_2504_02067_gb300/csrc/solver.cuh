@@ -17,6 +17,7 @@
 #include "handle.cuh"
 #include "sweep_pts.cuh"
 #include "sweep_tc.cuh"
+#include "sweep_bulk.cuh"
 #include "cg_persistent.cuh"
 
 namespace eot {
@@ -30,12 +31,18 @@ struct SolveCounters {
 
 enum class CgMode { kHost, kBatch, kWhile };
 
+// Default: one graph launch per linear CG solve, its WHILE node re-evaluated
+// every kWhileBody iterations (no host round trip inside the solve); "batch":
+// graph launches of six iterations with a host check of the stop flag after
+// each (measured 4% slower on the 64 x 64 grid workload); "none": direct
+// launches, four iterations per check.
+constexpr int kWhileBody = 8;
 inline CgMode cg_mode_from_env() {
   const char* e = std::getenv("EOT_CG_GRAPH");
-  if (!e) return CgMode::kBatch;
-  if (!std::strcmp(e, "while")) return CgMode::kWhile;
+  if (!e) return CgMode::kWhile;
+  if (!std::strcmp(e, "batch")) return CgMode::kBatch;
   if (!std::strcmp(e, "none")) return CgMode::kHost;
-  return CgMode::kBatch;
+  return CgMode::kWhile;
 }
 
 template <class T>
@@ -87,6 +94,128 @@ struct Solver {
     rg = row_grid(n);
     geo = col_geo(h, n, m, V);
     sweep_bucket = &cnt.sweeps_other;
+    if constexpr (sizeof(T) == 4) {
+      if (!points) setup_bulk();
+    }
+  }
+
+  // ---- bulk-copy sweeps (dense FP32 cost, 16-byte rows, large enough) ----
+  bool bulk_rows = false, bulk_cols = false;
+  int bulk_rg = 0;                 // row sweep: CTAs
+  int bulk_br = 0, bulk_R = 0;     // column sweep: rows per block, blocks
+  int64_t bulk_S = 0;              // column sweep: strips of kColSW columns
+  int bulk_stages = 0;             // column sweep: ring stages
+  CUtensorMap bulk_map;            // column sweep: the cost as an m x n tensor of kColSW x kColRB boxes
+  // Opt-in (EOT_BULK=1): on the 64 x 64 grid workload these sweeps measured
+  // slower than the register-load kernels (CG halves 17.7 / 16.5 us against
+  // 13.1 / 14.7 us back to back, solve 0.118 s against 0.091 s), so they are not
+  // the default.
+  static bool bulk_enabled() {
+    const char* e = std::getenv("EOT_BULK");
+    return e && e[0] == '1';
+  }
+  static void bulk_attr(const void* kernel) {
+    EOT_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  bulk::kSmemOptIn - bulk::kBarBytes));
+  }
+  // cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link)
+  typedef CUresult (*EncodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  static EncodeTiled encode_tiled() {
+    static EncodeTiled fn = [] {
+      void* f = nullptr;
+      cudaDriverEntryPointQueryResult q;
+      if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+              cudaSuccess ||
+          q != cudaDriverEntryPointSuccess)
+        f = nullptr;
+      return (EncodeTiled)f;
+    }();
+    return fn;
+  }
+  void setup_bulk() {
+    if (!bulk_enabled() || V != VEC || n * m < bulk::kMinEntries || m < 128) return;
+    bulk_rg = (int)std::min<int64_t>(std::min<int64_t>(h->sms, n), h->dot_slots);
+    bulk_rows = true;
+    // column strips of kColSW columns x row blocks (multiples of kColRB rows)
+    // filling the SMs once
+    const int64_t S = (m + bulk::kColSW - 1) / bulk::kColSW;
+    int64_t R = std::min<int64_t>(std::min<int64_t>(h->sms / std::max<int64_t>(S, 1), (n + bulk::kColRB - 1) / bulk::kColRB),
+                                  h->max_rowblk);
+    EncodeTiled enc = encode_tiled();
+    if (S <= h->sms && S <= h->max_strips && S <= h->dot_slots && R >= 1 && enc) {
+      int64_t BR = (n + R - 1) / R;
+      BR = (BR + bulk::kColRB - 1) / bulk::kColRB * bulk::kColRB;
+      R = (n + BR - 1) / BR;
+      const int64_t room = bulk::kSmemOptIn - 1024 - bulk::kBarBytes - 3 * BR * 4;
+      const int stages = (int)std::min<int64_t>(bulk::kColMaxStages, room / bulk::kStageBytes);
+      const cuuint64_t dims[2] = {(cuuint64_t)m, (cuuint64_t)n};
+      const cuuint64_t strides[1] = {(cuuint64_t)ldc * sizeof(float)};
+      const cuuint32_t box[2] = {(cuuint32_t)bulk::kColSW, (cuuint32_t)bulk::kColRB};
+      const cuuint32_t estr[2] = {1, 1};
+      if (stages >= 4 &&
+          enc(&bulk_map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)C, dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS) {
+        bulk_S = S;
+        bulk_R = (int)R;
+        bulk_br = (int)BR;
+        bulk_stages = stages;
+        bulk_cols = true;
+      }
+    }
+    static bool attrs = false;
+    if (!attrs) {
+      // every instantiation, before any graph capture
+      bulk_attr((const void*)bulk::row_bulk_kernel<12, 1, 1, true, 0, RowLseEpi>);
+      bulk_attr((const void*)bulk::row_bulk_kernel<8, 1, 1, true, 0, RowLseEpi>);
+      bulk_attr((const void*)bulk::row_bulk_kernel<12, 1, 3, false, 2, SetupRowEpi>);
+      bulk_attr((const void*)bulk::row_bulk_kernel<8, 1, 3, false, 2, SetupRowEpi>);
+      bulk_attr((const void*)bulk::row_bulk_kernel<12, 1, 1, false, 0, CgRowEpi>);
+      bulk_attr((const void*)bulk::row_bulk_kernel<8, 1, 1, false, 0, CgRowEpi>);
+      bulk_attr((const void*)bulk::col_bulk_kernel<1, true, ColLseEpi>);
+      bulk_attr((const void*)bulk::col_bulk_kernel<2, false, SetupColEpi<float>>);
+      bulk_attr((const void*)bulk::col_bulk_kernel<1, false, CgColEpi<float>>);
+      bulk_attr((const void*)bulk::col_bulk_kernel<1, false, DvColEpi>);
+      attrs = true;
+    }
+  }
+  // Bulk row sweep when eligible: twelve one-stage consumer warps when the
+  // column vectors fit beside their 192 KB ring, else eight; false: use the
+  // register-load kernel.
+  template <int NR, bool LSE, int SQM, class Epi>
+  bool launch_row_bulk(cudaStream_t s, const SweepArgs<T>& a, const Epi& e) {
+    if constexpr (sizeof(T) != 4) {
+      return false;
+    } else {
+      if (!bulk_rows) return false;
+      constexpr int NV = 1 + (LSE ? 1 : NR);
+      const size_t s12 = bulk::row_smem_bytes(12, NV, m), s8 = bulk::row_smem_bytes(8, NV, m);
+      if (s12 + 1024 <= (size_t)bulk::kSmemOptIn)
+        launch_kd(bulk::row_bulk_kernel<12, 1, NR, LSE, SQM, Epi>, dim3(bulk_rg), dim3(13 * 32), s12, s, a, e);
+      else if (s8 + 1024 <= (size_t)bulk::kSmemOptIn)
+        launch_kd(bulk::row_bulk_kernel<8, 1, NR, LSE, SQM, Epi>, dim3(bulk_rg), dim3(9 * 32), s8, s, a, e);
+      else
+        return false;
+      return true;
+    }
+  }
+  template <int NC, bool LSE, class Epi>
+  bool launch_col_bulk(cudaStream_t s, const SweepArgs<T>& a, const Epi& e) {
+    if constexpr (sizeof(T) != 4) {
+      return false;
+    } else {
+      if (!bulk_cols) return false;
+      SweepArgs<T> b = a;
+      b.rows_per_block = bulk_br;
+      b.nrowblk = bulk_R;
+      b.stages = bulk_stages;
+      const size_t smem = (size_t)bulk::kBarBytes + (size_t)bulk_stages * bulk::kStageBytes + 3 * (size_t)bulk_br * 4;
+      launch_kd(bulk::col_bulk_kernel<NC, LSE, Epi>, dim3((unsigned)bulk_S, (unsigned)bulk_R),
+                dim3(bulk::kColThreads), smem, s, b, e, bulk_map);
+      return true;
+    }
   }
 
   // ---- point-cloud geometry: own blocks of 256 RO elements x S chunks ----
@@ -281,6 +410,7 @@ struct Solver {
     a.d = d;
     a.sC = sC;
     a.chunk = 0;
+    a.err = h->status;
     return a;
   }
 
@@ -297,11 +427,12 @@ struct Solver {
 
   // Read every device scalar and the status word (synchronises the stream).
   // Lost CG curvature (kStatCurv) is handled by the caller, not thrown.
-  const double* read() {
+  // Status bits in `tolerated` are left for the caller to inspect (status_bits()).
+  const double* read(int tolerated = 0) {
     EOT_CUDA(cudaMemcpyAsync(h->h_sc, h->sc, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, st));
     EOT_CUDA(cudaMemcpyAsync(h->h_status, h->status, sizeof(int), cudaMemcpyDeviceToHost, st));
     EOT_CUDA(cudaStreamSynchronize(st));
-    const int s = *h->h_status;
+    const int s = *h->h_status & ~tolerated;
     if (s & kStatNonfinite) throw EotError{EOT_ERR_NONFINITE, "non-finite potential or marginal" + ctx};
     if (s & kStatCgNan) throw EotError{EOT_ERR_NONFINITE, "non-finite CG residual" + ctx};
     if (s & kStatRange) throw EotError{EOT_ERR_RANGE, "|potential| >= 2^19 (mixed-precision split)" + ctx};
@@ -371,6 +502,7 @@ struct Solver {
   template <int NR, bool LSE, int SQM, class Epi>
   void launch_row(cudaStream_t s, const SweepArgs<T>& a, const Epi& e) {
     if (points) launch_pts<NR, LSE, SQM, true>(s, a, e);
+    else if (launch_row_bulk<NR, LSE, SQM>(s, a, e)) return;
     else if (V == VEC) launch_k(row_sweep_kernel<T, VEC, NR, LSE, SQM, Epi>, dim3(rg), dim3(kThreads), s, a, e);
     else launch_k(row_sweep_kernel<T, 1, NR, LSE, SQM, Epi>, dim3(rg), dim3(kThreads), s, a, e);
   }
@@ -380,6 +512,9 @@ struct Solver {
       if constexpr (NR == 0) launch_pts<NC, LSE, 0, false>(s, a, e);
       else throw EotError{EOT_ERR_UNSUPPORTED, "fused two-sided sweep needs a dense cost"};
       return;
+    }
+    if constexpr (NR == 0) {
+      if (launch_col_bulk<NC, LSE>(s, a, e)) return;
     }
     const dim3 grid((unsigned)geo.S, (unsigned)geo.R);
     if (V == VEC) launch_k(col_sweep_kernel<T, VEC, NC, LSE, NR, Epi>, grid, dim3(kThreads), s, a, e);
@@ -507,6 +642,11 @@ struct Solver {
         h->launches++;
         const double* s = read();
         const double it = s[SC_ITERS], rl1 = s[SC_RESL1], chk = s[SC_CHK];
+        if (mode == CgMode::kWhile && pcg_geo().G == 0) {
+          // passes of the WHILE body: the one whose update kernel stopped CG is the last
+          const int64_t passes = std::max<int64_t>(1, ((int64_t)it + kWhileBody - 1) / kWhileBody);
+          h->launches += 4 * kWhileBody * passes;
+        }
         cnt.cg_iters += (int64_t)it;
         cnt.sweeps_cg += 2 * (int64_t)it + ((status_bits() & kStatCurv) ? 2 : 0);
         cnt.cg_solves++;
@@ -570,8 +710,9 @@ struct Solver {
   }
 
   CgGraph& get_graph(CgMode mode) {
-    const int B = mode == CgMode::kWhile ? 1 : 6;
-    const CgKey key{(int)sizeof(T) + (points ? 100 * d : 0), V, mode == CgMode::kWhile ? 1 : 0, n, m,
+    const int B = mode == CgMode::kWhile ? kWhileBody : 6;  // CG iterations per launch / per pass
+    const CgKey key{(int)sizeof(T) + (points ? 100 * d : 0) + (bulk_rows ? 1000 : 0) + (bulk_cols ? 2000 : 0), V,
+                    mode == CgMode::kWhile ? B : 0, n, m,
                     ldc, points ? (uintptr_t)X ^ ((uintptr_t)Y << 1) : (uintptr_t)C};
     auto it = h->graphs.find(key);
     if (it != h->graphs.end()) return it->second;
@@ -592,7 +733,9 @@ struct Solver {
       cudaGraph_t body = np.conditional.phGraph_out[0];
       EOT_CUDA(cudaStreamBeginCaptureToGraph(h->cap_stream, body, nullptr, nullptr, 0,
                                              cudaStreamCaptureModeRelaxed));
-      cg_iteration(h->cap_stream, cond);
+      // B iterations per pass: the condition is re-evaluated every B iterations;
+      // iterations past the stop are no-ops (device stop flag)
+      for (int b = 0; b < B; ++b) cg_iteration(h->cap_stream, cond);
       cudaGraph_t out;
       EOT_CUDA(cudaStreamEndCapture(h->cap_stream, &out));
     } else {
@@ -712,8 +855,7 @@ struct Solver {
     }
     CgGraph& g = get_graph(mode);
     if (mode == CgMode::kWhile) {
-      EOT_CUDA(cudaGraphLaunch(g.exec, st));
-      h->launches += 1;
+      EOT_CUDA(cudaGraphLaunch(g.exec, st));  // its kernels are counted once the iterations are known
       return;
     }
     const int maxl = (max_cg + g.iters_per_launch - 1) / g.iters_per_launch + 1;
@@ -841,11 +983,9 @@ struct Solver {
         col_lse(u, h->du, v, h->dv, alpha, logct, h->logcP, 0, SC_LHS, 1.0);
         // A trial point outside the split range (|u + a d_u| >= 2^19) has a plan
         // whose mass overflows, so it fails the Armijo test: reject it.
-        EOT_CUDA(cudaMemcpyAsync(h->h_status, h->status, sizeof(int), cudaMemcpyDeviceToHost, st));
-        EOT_CUDA(cudaStreamSynchronize(st));
-        const bool out_of_range = (*h->h_status & kStatRange) != 0;
+        s = read(kStatRange);
+        const bool out_of_range = (status_bits() & kStatRange) != 0;
         if (out_of_range) clear_status();
-        s = read();
         cnt.ls_trials++;
         if (trace)
           std::fprintf(stderr, "[eot]   trial alpha %.4g lhs %.6e lhs0 %.6e slope %.6e range %d\n", alpha,
@@ -897,7 +1037,7 @@ void run_solve(eot_handle h, const eot_problem* P, const eot_params* prm, double
                eot_stats* stats, cudaStream_t st);
 template <class T>
 double run_sweep_bench(eot_handle h, const eot_problem* P, const double* u, const double* v,
-                       double gamma, int kind, int iters, cudaStream_t st);
+                       double gamma, int kind, int iters, void* flush, size_t flush_bytes, cudaStream_t st);
 template <class T>
 void run_backward_dense(eot_handle h, const eot_problem* P, const double* u, const double* v,
                         double gamma, double scale, float* dC, cudaStream_t st);

@@ -14,7 +14,7 @@ template void run_solve<float>(eot_handle, const eot_problem*, const eot_params*
 template void run_backward_dense<float>(eot_handle, const eot_problem*, const double*, const double*,
                                         double, double, float*, cudaStream_t);
 template double run_sweep_bench<float>(eot_handle, const eot_problem*, const double*, const double*,
-                                      double, int, int, cudaStream_t);
+                                      double, int, int, void*, size_t, cudaStream_t);
 template void run_backward_points<float>(eot_handle, const eot_problem*, const double*, const double*,
                                            double, double, float*, float*, cudaStream_t);
 template void run_round<float>(eot_handle, const eot_problem*, const double*, const double*, double, double*,

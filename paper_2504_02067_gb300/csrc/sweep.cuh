@@ -46,7 +46,9 @@ struct SweepArgs {
   const float* Y;           // [m][d]
   int d;
   double sC;
-  int64_t chunk;            // other-side elements per chunk (grid.y)
+  int64_t chunk;            // other-side elements per chunk (grid.y); strip width of a bulk column sweep
+  int* err;                 // status word of bounded waits (bulk-copy sweeps)
+  int stages;               // ring stages of a bulk-copy sweep
 };
 
 template <int N>
@@ -112,6 +114,80 @@ __device__ __forceinline__ void cta_dot_finish(double (&wd)[ND > 0 ? ND : 1], in
         epi.finish(tot.v);
       }
     }
+  }
+}
+
+// ----------------------------------------------------------------------------
+// FP32 result of one row held by a warp: the lanes' compensated pairs are
+// combined in FP32 (the FP64 pipe is narrow) and lane 0 hands the row's FP64
+// result to the epilogue. LSE: common max of the lanes (1/8 grid: exact), one
+// rescale per lane.
+// ----------------------------------------------------------------------------
+template <int NA, bool LSE, int ND, class Epi>
+__device__ __forceinline__ void row_result_f32(int64_t i, int lane, const float (&S)[NA], const float (&Cc)[NA],
+                                               float mx, bool mx_set, Epi& epi, double (&wd)[ND > 0 ? ND : 1]) {
+  if constexpr (!LSE) {
+    double tot[NA];
+#pragma unroll
+    for (int k = 0; k < NA; ++k) {
+      float s0 = S[k], c0 = Cc[k];
+      warp_sum_pair(s0, c0);
+      tot[k] = (double)s0 + (double)c0;
+    }
+    if (lane == 0) {
+      DotArr<ND> d;
+      epi.row(i, tot, d.v);  // tot: [NA] sums
+#pragma unroll
+      for (int k = 0; k < ND; ++k) wd[k] += d.v[k];
+    }
+  } else {
+    const float M = warp_max_f(mx_set ? mx : -INFINITY);
+    const float f = mx_set ? expT(mx - M) : 0.f;
+    float s0 = S[0] * f, c0 = Cc[0] * f;
+    warp_sum_pair(s0, c0);
+    if (lane == 0) {
+      DotArr<ND> d;
+      epi.row_lse(i, (double)M, (double)s0 + (double)c0, d.v);
+#pragma unroll
+      for (int k = 0; k < ND; ++k) wd[k] += d.v[k];
+    }
+  }
+}
+
+// FP32 column result: combine the R compensated partial pairs of column jj in
+// fixed order (LSE: the (max, 0) pairs of slot 0 and the sums of slot 1) and
+// hand the FP64 result to the epilogue.
+template <int NC, bool LSE, class Epi>
+__device__ __forceinline__ void col_combine_f32(const float2* cp2, int R, int64_t m, int64_t jj, Epi& epi,
+                                                double* dv) {
+  if constexpr (!LSE) {
+    double s[NC];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+      float s0 = 0.f, c0 = 0.f;
+      for (int r = 0; r < R; ++r) {
+        const float2 q = __ldcg(cp2 + ((int64_t)k * R + r) * m + jj);
+        kadd(s0, c0, q.x);
+        c0 += q.y;
+      }
+      s[k] = (double)s0 + (double)c0;
+    }
+    epi.col(jj, s, dv);
+  } else {
+    float M = -INFINITY;
+    for (int r = 0; r < R; ++r) {
+      const float2 qs = __ldcg(cp2 + ((int64_t)R + r) * m + jj);
+      if (qs.x != 0.f || qs.y != 0.f) M = fmaxf(M, __ldcg(cp2 + (int64_t)r * m + jj).x);
+    }
+    float s0 = 0.f, c0 = 0.f;
+    for (int r = 0; r < R; ++r) {
+      const float2 qs = __ldcg(cp2 + ((int64_t)R + r) * m + jj);
+      if (qs.x == 0.f && qs.y == 0.f) continue;
+      const float f = expT(__ldcg(cp2 + (int64_t)r * m + jj).x - M);
+      kadd(s0, c0, qs.x * f);
+      c0 += qs.y * f;
+    }
+    epi.col_lse(jj, (double)M, (double)s0 + (double)c0, dv);
   }
 }
 
@@ -276,35 +352,7 @@ __global__ void __launch_bounds__(kThreads, 4) row_sweep_kernel(SweepArgs<T> a, 
   pdl_trigger();
   if (rv) {
     if constexpr (sizeof(T) == 4) {
-      // FP32 path: the lanes' compensated pairs are combined in FP32 (the FP64
-      // pipe is narrow); only lane 0 converts the row's result to FP64
-      if constexpr (!LSE) {
-        double tot[NR];
-#pragma unroll
-        for (int k = 0; k < NR; ++k) {
-          float s0 = S[k], c0 = Cc[k];
-          warp_sum_pair(s0, c0);
-          tot[k] = (double)s0 + (double)c0;
-        }
-        if (lane == 0) {
-          DotArr<ND> d;
-          epi.row(i, tot, d.v);  // tot: [NR] sums
-#pragma unroll
-          for (int k = 0; k < ND; ++k) wd[k] += d.v[k];
-        }
-      } else {
-        // common max of the lanes (1/8 grid: exact), one rescale per lane
-        const float M = warp_max_f(mx_set ? (float)mx : -INFINITY);
-        const float f = mx_set ? (float)expT((T)(mx - (T)M)) : 0.f;
-        float s0 = (float)S[0] * f, c0 = (float)Cc[0] * f;
-        warp_sum_pair(s0, c0);
-        if (lane == 0) {
-          DotArr<ND> d;
-          epi.row_lse(i, (double)M, (double)s0 + (double)c0, d.v);
-#pragma unroll
-          for (int k = 0; k < ND; ++k) wd[k] += d.v[k];
-        }
-      }
+      row_result_f32<NA, LSE, ND>(i, lane, S, Cc, mx, mx_set, epi, wd);
     } else {
       if constexpr (!LSE) {
         double tot[NR];
@@ -600,36 +648,7 @@ __global__ void __launch_bounds__(kThreads, kColCtasPerSm) col_sweep_kernel(Swee
       if (jj >= a.m) continue;
       DotArr<ND> d;
       if constexpr (sizeof(T) == 4) {
-        const float2* cp2 = reinterpret_cast<const float2*>(a.colpart);
-        if constexpr (!LSE) {
-          double s[NC];
-#pragma unroll
-          for (int k = 0; k < NC; ++k) {
-            float s0 = 0.f, c0 = 0.f;
-            for (int r = 0; r < R; ++r) {
-              const float2 q = __ldcg(cp2 + ((int64_t)k * R + r) * a.m + jj);
-              kadd(s0, c0, q.x);
-              c0 += q.y;
-            }
-            s[k] = (double)s0 + (double)c0;
-          }
-          epi.col(jj, s, d.v);
-        } else {
-          float M = -INFINITY;
-          for (int r = 0; r < R; ++r) {
-            const float2 qs = __ldcg(cp2 + ((int64_t)R + r) * a.m + jj);
-            if (qs.x != 0.f || qs.y != 0.f) M = fmaxf(M, __ldcg(cp2 + (int64_t)r * a.m + jj).x);
-          }
-          float s0 = 0.f, c0 = 0.f;
-          for (int r = 0; r < R; ++r) {
-            const float2 qs = __ldcg(cp2 + ((int64_t)R + r) * a.m + jj);
-            if (qs.x == 0.f && qs.y == 0.f) continue;
-            const float f = (float)expT((T)(__ldcg(cp2 + (int64_t)r * a.m + jj).x - M));
-            kadd(s0, c0, qs.x * f);
-            c0 += qs.y * f;
-          }
-          epi.col_lse(jj, (double)M, (double)s0 + (double)c0, d.v);
-        }
+        col_combine_f32<NC, LSE>(reinterpret_cast<const float2*>(a.colpart), R, a.m, jj, epi, d.v);
       } else if constexpr (!LSE) {
         double s[NC];
 #pragma unroll

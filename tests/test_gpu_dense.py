@@ -268,3 +268,41 @@ def test_persistent_cg_kernel_matches_graph_path(H, monkeypatch):
         assert np.abs(diff - diff.mean()).sum() <= 1e-5 * np.abs(ref_du).sum()
         assert abs(it - ref.cg_iters) <= 1 + ref.cg_solves
     assert out["1"][1] == out["0"][1]
+
+
+def test_cg_graph_modes_agree(monkeypatch):
+    """The linear CG of Alg. 2 run as one WHILE-node graph per solve (default), as
+    graph launches of six iterations with host checks ("batch") and as direct
+    launches ("none") issues the same kernels in the same order: the Newton
+    directions and iteration counts are identical."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2504_02067_gb300 import Handle, Problem
+    n, m = 600, 512
+    rng = np.random.default_rng(41)
+    C = rng.uniform(0, 1, size=(n, m)).astype(np.float32)
+    C64 = C.astype(np.float64)
+    gamma = 64.0
+    u, v, r, c = near_feasible(42, n, m, gamma, C64)
+    rP = O.row_sum(O.plan(u, v, gamma, C64))
+    rt = rP * (1 + 0.02 * rng.normal(size=n))
+    rt /= rt.sum()
+    gl1 = np.abs(rP - rt).sum()
+    eta = max(gl1, 0.8 * 1e-4 / gl1)
+    out = {}
+    for mode in ("", "batch", "none"):
+        if mode:
+            monkeypatch.setenv("EOT_CG_GRAPH", mode)
+        else:
+            monkeypatch.delenv("EOT_CG_GRAPH", raising=False)
+        h = Handle(0, 64, 64)
+        try:
+            prob = Problem(t(C, torch.float32), precision="mixed")
+            du, dv, rho, it = h.newton_solve(prob, t(u), t(v), gamma, t(rt), eta, 0.0)
+            out[mode] = (du.cpu().numpy(), dv.cpu().numpy(), rho, it)
+        finally:
+            h.close()
+    for mode in ("batch", "none"):
+        assert out[mode][2] == out[""][2] and out[mode][3] == out[""][3]
+        assert np.array_equal(out[mode][0], out[""][0])
+        assert np.array_equal(out[mode][1], out[""][1])
