@@ -147,6 +147,23 @@ __device__ __forceinline__ void ld_vec_smem(const T* p, T (&c)[V]) {
   }
 }
 
+// 16-byte vector type of an element type, and packing V = 16 / sizeof(T) elements
+template <class T>
+struct VecOf;
+template <>
+struct VecOf<float> {
+  typedef float4 type;
+};
+template <>
+struct VecOf<double> {
+  typedef double2 type;
+};
+template <class T>
+__device__ __forceinline__ typename VecOf<T>::type pack(const T (&x)[16 / sizeof(T)]) {
+  if constexpr (sizeof(T) == 4) return make_float4(x[0], x[1], x[2], x[3]);
+  else return make_double2(x[0], x[1]);
+}
+
 __device__ __forceinline__ double warp_sum(double x) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);

@@ -284,7 +284,8 @@ template <class T, int V, int NR, bool LSE, int SQM, class Epi>
 __global__ void __launch_bounds__(kThreads, 4) row_sweep_kernel(SweepArgs<T> a, Epi epi) {
   constexpr int U = 4;                               // chunks per batch (two batches in flight)
   constexpr int NV = 1 + (LSE ? 1 : NR);             // staged column vectors
-  constexpr int TW = (sizeof(T) == 4 ? 8192 : 4096) / NV;  // tile width (<= 32 KB smem)
+  // tile width (<= 32 KB smem), a multiple of 128 so that tiles and rows of sv stay 16-byte aligned
+  constexpr int TW = ((sizeof(T) == 4 ? 8192 : 4096) / NV) / 128 * 128;
   constexpr int ND = Epi::kDot;
   constexpr int NA = LSE ? 1 : NR;
   constexpr int STEP = 32 * V * U;
@@ -314,10 +315,25 @@ __global__ void __launch_bounds__(kThreads, 4) row_sweep_kernel(SweepArgs<T> a, 
   for (int64_t t0 = 0; t0 < a.m; t0 += TW) {
     const int tw = (int)min((int64_t)TW, a.m - t0);
     __syncthreads();
-    for (int q = threadIdx.x; q < tw; q += kThreads) {
-      sv[0][q] = a.Bh[t0 + q];
+    if constexpr (V > 1) {
+      // 16-byte rows (V > 1): t0, tw and the workspace vectors are 16-byte aligned
+#pragma unroll 1
+      for (int q = threadIdx.x * V; q < tw; q += kThreads * V) {
+        T x[V];
+        ld_vec<V>(a.Bh + t0 + q, x);
+        *reinterpret_cast<typename VecOf<T>::type*>(&sv[0][q]) = pack<T>(x);
 #pragma unroll
-      for (int k = 0; k < NV - 1; ++k) sv[1 + k][q] = a.wc[k][t0 + q];
+        for (int k = 0; k < NV - 1; ++k) {
+          ld_vec<V>(a.wc[k] + t0 + q, x);
+          *reinterpret_cast<typename VecOf<T>::type*>(&sv[1 + k][q]) = pack<T>(x);
+        }
+      }
+    } else {
+      for (int q = threadIdx.x; q < tw; q += kThreads) {
+        sv[0][q] = a.Bh[t0 + q];
+#pragma unroll
+        for (int k = 0; k < NV - 1; ++k) sv[1 + k][q] = a.wc[k][t0 + q];
+      }
     }
     __syncthreads();
     if (!rv) continue;
