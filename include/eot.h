@@ -99,11 +99,24 @@ typedef struct {
 
 enum { EOT_PROJECT_NEWTON = 0, EOT_PROJECT_SINKHORN = 1 };
 
+/* One stage t of Alg. 1 in eot_solve: the temperature, the tolerance of its
+ * Bregman projection, AdjustSchedule's input and output (Sec. 3.3, Eq. delta_k-
+ * ratio: delta_min is the smallest ratio of actual to predicted reduction of
+ * ||grad g||_1 over the stage's Newton steps, +inf with none) and its work. */
+typedef struct {
+  double gamma;             /* gamma^(t) */
+  double eps;               /* tolerance of the projection, eps_d / 2 (Alg. 1) */
+  double delta_min;         /* min_k delta_k of the stage */
+  double q_next;            /* q^(t+1) chosen by AdjustSchedule */
+  int32_t newton_steps, cg_iters, ls_trials, sinkhorn_iters;  /* of this stage */
+  int64_t sweeps;           /* O(nm) sweeps of this stage */
+} eot_stage_record;
+
 typedef struct {       /* host-side counters of one eot_solve call */
   int64_t sweeps_cg;        /* O(nm) sweeps inside linear CG (2 per CG iteration) */
   int64_t sweeps_newton;    /* other NewtonSolve sweeps (setup, d_v) */
-  int64_t sweeps_linesearch;
-  int64_t sweeps_sinkhorn;  /* LSE sweeps of ChiSinkhorn and the column/row fixes */
+  int64_t sweeps_linesearch; /* Armijo trials (Alg. 4 lines 8-13, with the alpha = 0 reference) and line 16 */
+  int64_t sweeps_sinkhorn;  /* LSE sweeps of ChiSinkhorn (Alg. 3) or of the Sinkhorn projector */
   int64_t sweeps_total;
   int32_t stages, newton_steps, cg_iters, cg_solves, ls_trials, sinkhorn_iters;
   int32_t curvature_stops;  /* CG solves stopped because <p, F_r p> <= 0 in finite precision */
@@ -113,6 +126,10 @@ typedef struct {       /* host-side counters of one eot_solve call */
   double grad_l1;           /* ||r~ - r(P)||_1 at the end of the last projection */
   double marg_err_l1;       /* ||r(P) - r||_1 + ||c(P) - c||_1 of the output (unsmoothed r, c) */
   double seconds;           /* wall time of the call */
+  int64_t sweeps_stage;     /* Alg. 4 lines 1-2 at the start of each projection (column and row fixes) */
+  eot_stage_record* stage_records; /* in: host array for one record per stage (nullable; eot_solve only) */
+  int32_t stage_records_cap;       /* in: its capacity */
+  int32_t stage_records_len;       /* out: records written, min(stages, capacity) */
 } eot_stats;
 
 typedef struct eot_handle_s* eot_handle;
@@ -177,7 +194,9 @@ eot_status eot_round(eot_handle h, const eot_problem* prob, const double* u, con
 /* Full solve: MDOT (Alg. 1) with adaptive q and asymmetric smoothing, each
  * stage projected by TruncatedNewtonProject (Alg. 4 with Alg. 2 and Alg. 3).
  * u: device [n], v: device [m]: outputs (the last projected potentials at gamma_f).
- * stats: host, nullable. Errors: any. Synchronises. */
+ * stats: host, nullable; with stats->stage_records set (and stats->stage_records_cap
+ * > 0) one eot_stage_record per stage of Alg. 1 is written there. Errors: any.
+ * Synchronises. */
 eot_status eot_solve(eot_handle h, const eot_problem* prob, const eot_params* params, double* u,
                      double* v, eot_stats* stats, void* stream);
 
@@ -196,7 +215,7 @@ eot_status eot_solve(eot_handle h, const eot_problem* prob, const eot_params* pa
  * u, v: host arrays [nprob] of device pointers to the outputs ([n_k], [m_k]).
  * status_out: host [nprob], nullable: each problem's eot_status.
  * stats: host [nprob], nullable (sweeps_total only among the sweep counters;
- *   seconds = the whole call).
+ *   seconds = the whole call; each struct is overwritten, stage_records included).
  * Returns EOT_OK when every problem succeeded, else the status of the first
  * failing problem (in input order); a failure of the launch itself (a group
  * barrier wait bounded at 2 s ran out) returns EOT_ERR_CUDA. Synchronises. */

@@ -460,6 +460,7 @@ class SolveResult:
     ls_trials: int
     gammas: list
     ok: bool
+    records: list = field(default_factory=list)  # one dict per stage (Alg. 1 loop)
 
 
 def mdot(C, r, c, gamma_i=2.0 ** 4, gamma_f=2.0 ** 12, p=1.5, q1=2.0, w_r=0.45,
@@ -513,6 +514,7 @@ def mdot(C, r, c, gamma_i=2.0 ** 4, gamma_f=2.0 ** 12, p=1.5, q1=2.0, w_r=0.45,
     t = 1
     totals = dict(newton=0, cg=0, sk=0, ls=0)
     gammas = []
+    records = []
     ok = True
     while True:
         done = gamma == gamma_f
@@ -538,6 +540,9 @@ def mdot(C, r, c, gamma_i=2.0 ** 4, gamma_f=2.0 ** 12, p=1.5, q1=2.0, w_r=0.45,
         z = (u, v)
         dmin = min(st.deltas) if st.deltas else math.inf
         q = adjust_schedule(q, dmin)
+        records.append(dict(gamma=gamma, eps=eps_d / 2.0, delta_min=dmin, q_next=q,
+                            newton_steps=st.newton_steps, cg_iters=st.cg_iters,
+                            ls_trials=st.ls_trials, sinkhorn_iters=st.sinkhorn_iters))
         gamma_next = rg(min(q * gamma, gamma_f))
         ratio = (gamma_next - gamma) / (gamma - gamma_prev)
         z_next = (z[0] + ratio * (z[0] - z_prev[0]), z[1] + ratio * (z[1] - z_prev[1]))
@@ -548,7 +553,7 @@ def mdot(C, r, c, gamma_i=2.0 ** 4, gamma_f=2.0 ** 12, p=1.5, q1=2.0, w_r=0.45,
         gamma_prev, gamma = gamma, gamma_next
         t += 1
     return SolveResult(z[0], z[1], gamma, t, totals["newton"], totals["cg"], totals["sk"],
-                       totals["ls"], gammas, ok)
+                       totals["ls"], gammas, ok, records)
 
 
 # --------------------------------------------------------------------------

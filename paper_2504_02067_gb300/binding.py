@@ -43,6 +43,16 @@ class EotParams(ctypes.Structure):
 PROJECT_NEWTON, PROJECT_SINKHORN = 0, 1
 
 
+class EotStageRecord(ctypes.Structure):
+    _fields_ = [("gamma", ctypes.c_double), ("eps", ctypes.c_double), ("delta_min", ctypes.c_double),
+                ("q_next", ctypes.c_double), ("newton_steps", ctypes.c_int32),
+                ("cg_iters", ctypes.c_int32), ("ls_trials", ctypes.c_int32),
+                ("sinkhorn_iters", ctypes.c_int32), ("sweeps", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class EotStats(ctypes.Structure):
     _fields_ = [("sweeps_cg", ctypes.c_int64), ("sweeps_newton", ctypes.c_int64),
                 ("sweeps_linesearch", ctypes.c_int64), ("sweeps_sinkhorn", ctypes.c_int64),
@@ -52,10 +62,15 @@ class EotStats(ctypes.Structure):
                 ("sinkhorn_iters", ctypes.c_int32), ("curvature_stops", ctypes.c_int32),
                 ("reserved", ctypes.c_int32), ("final_gamma", ctypes.c_double),
                 ("final_rho", ctypes.c_double), ("grad_l1", ctypes.c_double),
-                ("marg_err_l1", ctypes.c_double), ("seconds", ctypes.c_double)]
+                ("marg_err_l1", ctypes.c_double), ("seconds", ctypes.c_double),
+                ("sweeps_stage", ctypes.c_int64), ("stage_records", ctypes.POINTER(EotStageRecord)),
+                ("stage_records_cap", ctypes.c_int32), ("stage_records_len", ctypes.c_int32)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "stage_records"}
+        if self.stage_records:
+            d["stage_records"] = [self.stage_records[i].as_dict() for i in range(self.stage_records_len)]
+        return d
 
 
 EXPORTS = ["eot_create", "eot_destroy", "eot_last_error", "eot_status_string",
@@ -224,8 +239,14 @@ class Handle:
                                              ctypes.byref(it), _stream(stream)))
         return rho.value, it.value
 
-    def eot_solve(self, prob, params, u, v, stream=None):
+    def eot_solve(self, prob, params, u, v, stream=None, stage_records=256):
+        """Returns the call's EotStats; with stage_records > 0 it also carries up to
+        that many per-stage records of Alg. 1 (stats.as_dict()["stage_records"])."""
         stats = EotStats()
+        if stage_records > 0:
+            stats._records = (EotStageRecord * stage_records)()  # kept alive with stats
+            stats.stage_records = ctypes.cast(stats._records, ctypes.POINTER(EotStageRecord))
+            stats.stage_records_cap = stage_records
         self.check(self.lib.eot_solve(self.h, prob.ref(), ctypes.byref(params), _p(u), _p(v),
                                       ctypes.byref(stats), _stream(stream)))
         return stats

@@ -23,7 +23,7 @@
 namespace eot {
 
 struct SolveCounters {
-  int64_t sweeps_cg = 0, sweeps_newton = 0, sweeps_ls = 0, sweeps_sk = 0, sweeps_other = 0;
+  int64_t sweeps_cg = 0, sweeps_newton = 0, sweeps_ls = 0, sweeps_sk = 0, sweeps_stage = 0, sweeps_other = 0;
   int64_t cg_iters = 0, cg_solves = 0, newton_steps = 0, ls_trials = 0, sk_iters = 0;
   int64_t curvature_stops = 0;
   double rho_last = 0.0;
@@ -876,9 +876,10 @@ struct Solver {
     double* rt = h->rt;
     double* logrt = h->logrt;
     double* logct = h->logct;
-    sweep_bucket = &cnt.sweeps_sk;
+    sweep_bucket = &cnt.sweeps_stage;
     col_lse(u, nullptr, v, nullptr, 0.0, logct, v, 1, SC_AUX0, 0.0);
     row_lse(u, v, logrt, h->logrP, h->rowmax, rt);
+    sweep_bucket = &cnt.sweeps_sk;
     set_scalar(SC_AUX1, 0.0);
     const int64_t max_it = prm.max_sinkhorn > 0 ? prm.max_sinkhorn : 1000000;
     double gl1 = read()[SC_GL1];
@@ -919,7 +920,7 @@ struct Solver {
     double* rt = h->rt;
     double* logrt = h->logrt;
     double* logct = h->logct;
-    sweep_bucket = &cnt.sweeps_sk;
+    sweep_bucket = &cnt.sweeps_stage;
     // line 1: v <- log c~ - LSE_c(u 1^T - gamma C)   (column fix)
     col_lse(u, nullptr, v, nullptr, 0.0, logct, v, 1, SC_AUX0, 0.0);
     // line 2: log r(P) <- u + LSE_r(1 v^T - gamma C)

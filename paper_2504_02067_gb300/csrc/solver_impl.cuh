@@ -185,6 +185,7 @@ void run_solve(eot_handle h, const eot_problem* P, const eot_params* prm_in, dou
     }
     S.set_scalar(SC_GAMMA, gamma);
     double dmin = INFINITY;
+    const SolveCounters c0 = S.cnt;
     if (prm.projector == EOT_PROJECT_SINKHORN) {
       if (!S.project_sinkhorn(u, v, eps_d / 2.0, prm, &gl1))
         throw EotError{EOT_ERR_MAXNEWTON, "Sinkhorn projection exceeded max_sinkhorn"};
@@ -194,6 +195,22 @@ void run_solve(eot_handle h, const eot_problem* P, const eot_params* prm_in, dou
     // AdjustSchedule (Sec. 3.3); a stage without Newton steps has delta_min = +inf
     if (dmin > 0.95) q = std::min(2.0, q * q);
     else if (dmin < 0.8) q = std::sqrt(q);
+    if (stats && stats->stage_records && t - 1 < stats->stage_records_cap) {
+      const SolveCounters& c1 = S.cnt;
+      eot_stage_record& rec = stats->stage_records[t - 1];
+      rec.gamma = gamma;
+      rec.eps = eps_d / 2.0;
+      rec.delta_min = dmin;
+      rec.q_next = q;
+      rec.newton_steps = (int32_t)(c1.newton_steps - c0.newton_steps);
+      rec.cg_iters = (int32_t)(c1.cg_iters - c0.cg_iters);
+      rec.ls_trials = (int32_t)(c1.ls_trials - c0.ls_trials);
+      rec.sinkhorn_iters = (int32_t)(c1.sk_iters - c0.sk_iters);
+      rec.sweeps = (c1.sweeps_cg + c1.sweeps_newton + c1.sweeps_ls + c1.sweeps_sk + c1.sweeps_stage +
+                    c1.sweeps_other) -
+                   (c0.sweeps_cg + c0.sweeps_newton + c0.sweeps_ls + c0.sweeps_sk + c0.sweeps_stage +
+                    c0.sweeps_other);
+    }
     const double gamma_next = round_gamma<T>(std::min(q * gamma, gamma_f));
     if (done) break;
     if (t >= prm.max_stages) throw EotError{EOT_ERR_MAXSTAGES, "gamma_f not reached within max_stages"};
@@ -227,7 +244,9 @@ void run_solve(eot_handle h, const eot_problem* P, const eot_params* prm_in, dou
     stats->sweeps_newton = c.sweeps_newton;
     stats->sweeps_linesearch = c.sweeps_ls;
     stats->sweeps_sinkhorn = c.sweeps_sk;
-    stats->sweeps_total = c.sweeps_cg + c.sweeps_newton + c.sweeps_ls + c.sweeps_sk + c.sweeps_other;
+    stats->sweeps_total = c.sweeps_cg + c.sweeps_newton + c.sweeps_ls + c.sweeps_sk + c.sweeps_stage + c.sweeps_other;
+    stats->sweeps_stage = c.sweeps_stage;
+    stats->stage_records_len = stats->stage_records ? std::min<int32_t>(t, stats->stage_records_cap) : 0;
     stats->stages = t;
     stats->newton_steps = (int32_t)c.newton_steps;
     stats->cg_iters = (int32_t)c.cg_iters;

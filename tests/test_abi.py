@@ -53,4 +53,34 @@ def test_library_loads_and_binding_matches(libpath):
     assert L.eot_status_string(3) == b"EOT_ERR_CG_MAXITER"
     assert ctypes.sizeof(binding.EotProblem) == 88
     assert ctypes.sizeof(binding.EotParams) == 72
-    assert ctypes.sizeof(binding.EotStats) == 112
+    assert ctypes.sizeof(binding.EotStats) == 136
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """Every field offset of the ctypes structures equals the C compiler's offsetof
+    for the structures of include/eot.h (the binding marshals them by layout)."""
+    if not shutil.which("gcc"):
+        pytest.skip("gcc not available")
+    from paper_2504_02067_gb300 import binding
+    structs = {"eot_problem": binding.EotProblem, "eot_params": binding.EotParams,
+               "eot_stats": binding.EotStats, "eot_stage_record": binding.EotStageRecord}
+    lines = []
+    for cname, cls in structs.items():
+        lines.append('  printf("%s size %%zu\\n", sizeof(%s));' % (cname, cname))
+        for f, _ in cls._fields_:
+            lines.append('  printf("%s %s %%zu\\n", offsetof(%s, %s));' % (cname, f, cname, f))
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "eot.h"\nint main(void) {\n'
+                   + "\n".join(lines) + "\n  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        parts = line.split()
+        if len(parts) == 3:
+            got[(parts[0], parts[1])] = int(parts[2])
+    for cname, cls in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(cls), cname
+        for f, _ in cls._fields_:
+            assert got[(cname, f)] == getattr(cls, f).offset, (cname, f)

@@ -306,3 +306,46 @@ def test_cg_graph_modes_agree(monkeypatch):
         assert out[mode][2] == out[""][2] and out[mode][3] == out[""][3]
         assert np.array_equal(out[mode][0], out[""][0])
         assert np.array_equal(out[mode][1], out[""][1])
+
+
+def test_stage_records_match_oracle_and_schedule(H):
+    """Per-stage records of eot_solve (Alg. 1's loop) against the oracle's mdot on
+    the same FP64 problem: the same temperatures, tolerances, Newton steps and CG
+    iterations per stage and the same delta_min (Eq. delta_k-ratio); and, from the
+    records alone, AdjustSchedule's rule (Sec. 3.3: q <- min(2, q^2) above 0.95,
+    sqrt(q) below 0.8) and gamma^(t+1) = min(q gamma^(t), gamma_f) (Alg. 1)."""
+    from paper_2504_02067_gb300 import Problem, default_params
+    rng = np.random.default_rng(23)
+    n, m = 120, 100
+    C = rng.uniform(0, 1, size=(n, m))
+    r, c = rng.dirichlet(np.ones(n)), rng.dirichlet(np.ones(m))
+    gi, gf = 16.0, 4096.0
+    ref = O.mdot(C, r, c, gamma_i=gi, gamma_f=gf, tol_final=1e-8)
+    prob = Problem(t(C), t(r), t(c))
+    u, v, st = H.solve(prob, default_params(gamma_i=gi, gamma_f=gf, tol_final=1e-8))
+    recs = st["stage_records"]
+    assert len(recs) == st["stages"] == ref.stages == len(ref.records)
+    for g, o in zip(recs, ref.records):
+        assert g["gamma"] == o["gamma"]
+        assert g["eps"] == pytest.approx(o["eps"], rel=1e-12)
+        assert g["newton_steps"] == o["newton_steps"] and abs(g["ls_trials"] - o["ls_trials"]) <= 1
+        assert abs(g["cg_iters"] - o["cg_iters"]) <= 2  # a CG stop moved by summation rounding
+        if math.isinf(o["delta_min"]):
+            assert math.isinf(g["delta_min"])
+        else:
+            assert g["delta_min"] == pytest.approx(o["delta_min"], rel=1e-6, abs=1e-9)
+        assert g["q_next"] == o["q_next"]
+    q = 2.0
+    for k, g in enumerate(recs):
+        d = g["delta_min"]
+        q = min(2.0, q * q) if d > 0.95 else (math.sqrt(q) if d < 0.8 else q)
+        assert g["q_next"] == q
+        if k + 1 < len(recs):
+            assert recs[k + 1]["gamma"] == min(q * g["gamma"], gf)
+    assert recs[0]["gamma"] == gi and recs[-1]["gamma"] == gf
+    assert sum(g["cg_iters"] for g in recs) == st["cg_iters"]
+    assert sum(g["newton_steps"] for g in recs) == st["newton_steps"]
+    # every sweep is in one stage except the final marginal evaluation (a row and a column LSE)
+    assert sum(g["sweeps"] for g in recs) + 2 == st["sweeps_total"]
+    assert st["sweeps_total"] == (st["sweeps_cg"] + st["sweeps_newton"] + st["sweeps_linesearch"]
+                                  + st["sweeps_sinkhorn"] + st["sweeps_stage"] + 2)
