@@ -303,7 +303,14 @@ eot_status eot_solve(eot_handle h, const eot_problem* prob, const eot_params* pa
         !(prm.tol_final > 0.0) || prm.max_stages < 1 || prm.max_newton < 1 || prm.max_ls < 1 ||
         (prm.projector != EOT_PROJECT_NEWTON && prm.projector != EOT_PROJECT_SINKHORN) || prm.max_sinkhorn < 0)
       throw EotError{EOT_ERR_INVALID_ARG, "invalid eot_params"};
-    if (stats) std::memset(stats, 0, sizeof(*stats));
+    if (stats) {
+      // outputs cleared; the caller's record array (an input) kept
+      eot_stage_record* recs = stats->stage_records;
+      const int32_t cap = stats->stage_records_cap;
+      std::memset(stats, 0, sizeof(*stats));
+      stats->stage_records = recs;
+      stats->stage_records_cap = recs ? cap : 0;
+    }
     cudaStream_t st = (cudaStream_t)stream;
     if (is_f64(prob)) run_solve<double>(h, prob, &prm, u, v, stats, st);
     else run_solve<float>(h, prob, &prm, u, v, stats, st);
