@@ -227,7 +227,9 @@ void run_solve(eot_handle h, const eot_problem* P, const eot_params* prm_in, dou
     ++t;
   }
 
-  // marginal L1 error of the output against the unsmoothed r, c
+  // marginal L1 error of the output against the unsmoothed r, c, at gamma_f (set
+  // here too: the one-row / one-column closed form runs no stage that sets it)
+  S.set_scalar(SC_GAMMA, gamma);
   S.sweep_bucket = &S.cnt.sweeps_other;
   S.row_lse(u, v, nullptr, h->logrP, nullptr, P->r, SC_GL1, SC_CHI2);
   S.col_lse(u, nullptr, v, nullptr, 0.0, nullptr, h->logcP, 0, SC_AUX0, 0.0);
