@@ -258,6 +258,59 @@ def newton_solve(P, grad_u, grad_l1, eta, rho0=0.0, max_cg=None):
     return NewtonResult(d_u, rho_last, total, solves, rhos, True)
 
 
+def discounted_hessian_apply(P, rho, du, dv):
+    """The discounted Hessian of Eq. discounted-hessian (off-diagonal blocks
+    scaled by sqrt(rho)) applied to (du, dv), Sec. 3.1."""
+    s = np.sqrt(rho)
+    return row_sum(P) * du + s * (P @ dv), s * (P.T @ du) + col_sum(P) * dv
+
+
+def newton_solve_full(P, grad_u, grad_l1, eta, rho0=0.0, max_cg=None):
+    """NewtonSolve with each linear solve on the full discounted system.
+
+    The outer loop is Algorithm 2's (rho annealed 1 - rho <- (1 - rho) / 4, the
+    same test ||F_r(1) d_u + grad_u g||_1 <= eta ||grad g||_1, Sec. 3.1), but
+    each LinearCGSolve runs PCG on the (n + m)-variable system of the discounted
+    Hessian (Eq. discounted-hessian),
+        [D(r(P)) d_u + sqrt(rho) P d_v ; sqrt(rho) P^T d_u + D(c(P)) d_v] = [-grad_u g ; 0],
+    with the diagonal preconditioner (r(P), c(P)), from 0, to an L1 residual
+    <= (eta / 4) ||grad g||_1, and keeps its u-block. Eliminating d_v from the
+    second block row leaves F_r(rho) d_u = -grad_u g (the Schur complement,
+    Eq. matrix-definitions), so in exact arithmetic both solves give the same
+    d_u; each iteration applies one two-sided product (one pass over P) where
+    Alg. 2's CG applies F_r(rho) (two passes). A different Krylov iteration, to
+    be measured against Algorithm 2, not substituted for it.
+    """
+    n, m = P.shape
+    if max_cg is None:
+        max_cg = 4 * (n + m)
+    rP, cP = row_sum(P), col_sum(P)
+    rho = rho0
+    rho_last = rho0
+    d_u = -grad_u / rP
+    total = 0
+    solves = 0
+    rhos = []
+    b = np.concatenate([-grad_u, np.zeros(m)])
+    M = np.concatenate([rP, cP])
+    while np.abs(F_r_apply(P, 1.0, d_u) + grad_u).sum() > eta * grad_l1:
+        def apply_H(x, rho=rho):
+            hu, hv = discounted_hessian_apply(P, rho, x[:n], x[n:])
+            return np.concatenate([hu, hv])
+        res = pcg(apply_H, b, M, (eta / 4.0) * grad_l1, max_cg)
+        d_u = res.x[:n]
+        total += res.iters
+        solves += 1
+        rhos.append(rho)
+        rho_last = rho
+        if not res.converged:
+            return NewtonResult(d_u, rho_last, total, solves, rhos, False)
+        rho = 1.0 - (1.0 - rho) / 4.0
+        if solves > 60:
+            return NewtonResult(d_u, rho_last, total, solves, rhos, False)
+    return NewtonResult(d_u, rho_last, total, solves, rhos, True)
+
+
 def next_rho0(rho_last):
     """rho_0^new = max(0, 1 - 4 (1 - rho^old))  (Appx. B, Eq. for rho_0^new)."""
     return max(0.0, 1.0 - 4.0 * (1.0 - rho_last))
@@ -336,7 +389,7 @@ def armijo_lhs(u, v, d_u, d_v, alpha, gamma, C):
 
 
 def truncated_newton_project(u, v, gamma, C, r, c, eps, rho_last=0.0,
-                             max_newton=200, max_ls=40, max_cg=None):
+                             max_newton=200, max_ls=40, max_cg=None, newton=None):
     """Algorithm 4 (TruncatedNewtonProject), Sec. 3.2, projecting onto U(r, c) to tolerance eps.
 
     Line 1:  v <- log c - LSE_c(u 1^T - gamma C)            (so c(P) = c)
@@ -353,7 +406,9 @@ def truncated_newton_project(u, v, gamma, C, r, c, eps, rho_last=0.0,
     Line 18: u <- u + log r - log r(P)   (one last row step)
     rho_last carries the adaptive discount of Appx. B between NewtonSolve calls
     (0 before the first call). Reading: a NewtonSolve call that runs no CG solve
-    leaves rho_last unchanged.
+    leaves rho_last unchanged. newton: the NewtonSolve used at line 6
+    (newton_solve, Algorithm 2, by default; newton_solve_full for the variant
+    whose linear solves run on the full discounted system).
     delta_k (Eq. delta_k-ratio) is recorded for every Newton step.
     """
     st = ProjectStats(rho_last=rho_last)
@@ -374,7 +429,7 @@ def truncated_newton_project(u, v, gamma, C, r, c, eps, rho_last=0.0,
             break
         eta = max(grad_l1, 0.8 * eps / grad_l1)
         P = plan(u, v, gamma, C)
-        nres = newton_solve(P, grad_u, grad_l1, eta, next_rho0(st.rho_last), max_cg)
+        nres = (newton or newton_solve)(P, grad_u, grad_l1, eta, next_rho0(st.rho_last), max_cg)
         st.cg_iters += nres.cg_iters
         if nres.cg_solves:
             st.rho_last = nres.rho
@@ -465,7 +520,7 @@ class SolveResult:
 
 def mdot(C, r, c, gamma_i=2.0 ** 4, gamma_f=2.0 ** 12, p=1.5, q1=2.0, w_r=0.45,
          tol_final=1e-6, round_gamma=None, max_stages=200, max_newton=200, max_cg=None,
-         projector="newton"):
+         projector="newton", newton=None):
     """Algorithm 1 (MDOT) driving Algorithm 4, Sec. 2.2 and Sec. 3.
 
     Line 1:  t <- 1, gamma^(1) <- min(gamma_i, gamma_f), q^(1) <- q, gamma^(0) <- 0
@@ -529,7 +584,8 @@ def mdot(C, r, c, gamma_i=2.0 ** 4, gamma_f=2.0 ** 12, p=1.5, q1=2.0, w_r=0.45,
             u, v, st = sinkhorn_project(z[0], z[1], gamma, C, rs, cs, eps_d / 2.0)
         else:
             u, v, st = truncated_newton_project(z[0], z[1], gamma, C, rs, cs, eps_d / 2.0,
-                                                rho_last, max_newton=max_newton, max_cg=max_cg)
+                                                rho_last, max_newton=max_newton, max_cg=max_cg,
+                                                newton=newton)
         rho_last = st.rho_last
         ok = ok and st.ok
         totals["newton"] += st.newton_steps

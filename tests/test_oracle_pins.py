@@ -259,6 +259,76 @@ def test_newton_solve_meets_forcing_and_descends():
     assert O.next_rho0(0.5) == 0.0
 
 
+def test_discounted_hessian_apply_matches_assembled_matrix():
+    """discounted_hessian_apply = the assembled Eq. discounted-hessian (off-diagonal
+    blocks times sqrt(rho)); SPD for rho < 1, singular along (1, -1) at rho = 1."""
+    C, u, v, g = rand_problem(41, 9, 7)
+    P = O.plan(u, v, g, C)
+    rng = np.random.default_rng(42)
+    du, dv = rng.normal(size=9), rng.normal(size=7)
+    for rho in (0.0, 0.3, 0.9375, 1.0):
+        H = O.hessian_matrix(P, math.sqrt(rho))
+        hu, hv = O.discounted_hessian_apply(P, rho, du, dv)
+        np.testing.assert_allclose(np.concatenate([hu, hv]), H @ np.concatenate([du, dv]),
+                                   rtol=1e-12, atol=1e-15)
+        lam = np.linalg.eigvalsh(H)
+        if rho < 1.0:
+            assert lam.min() > 0.0
+    hu, hv = O.discounted_hessian_apply(P, 1.0, np.ones(9), -np.ones(7))
+    assert np.abs(hu).max() + np.abs(hv).max() <= 1e-14
+
+
+def test_full_system_newton_step_equals_schur_solve():
+    """PCG on the full discounted system, run tight, gives the u-block of the dense
+    solve of F_r(rho) d_u = -grad_u g (Schur complement, Eq. matrix-definitions)
+    and the v-block -sqrt(rho) D(c(P))^-1 P^T d_u (second block row)."""
+    C, u, v, g = rand_problem(43, 24, 20, gamma=12.0)
+    P = O.plan(u, v, g, C)
+    rP, cP = O.row_sum(P), O.col_sum(P)
+    rng = np.random.default_rng(44)
+    grad_u = rP * 0.05 * rng.normal(size=24)
+    grad_u -= grad_u.mean()
+    for rho in (0.0, 0.75, 0.984375):
+        d_u = np.linalg.solve(O.F_r_matrix(P, rho), -grad_u)
+
+        def apply_H(x, rho=rho):
+            hu, hv = O.discounted_hessian_apply(P, rho, x[:24], x[24:])
+            return np.concatenate([hu, hv])
+        res = O.pcg(apply_H, np.concatenate([-grad_u, np.zeros(20)]), np.concatenate([rP, cP]),
+                    1e-14 * np.abs(grad_u).sum(), 2000)
+        assert res.converged
+        np.testing.assert_allclose(res.x[:24], d_u, rtol=1e-8, atol=1e-10 * np.abs(d_u).max())
+        np.testing.assert_allclose(res.x[24:], -math.sqrt(rho) * (P.T @ d_u) / cP,
+                                   rtol=1e-8, atol=1e-10 * np.abs(d_u).max())
+
+
+def test_newton_solve_full_meets_forcing_like_alg2():
+    """The full-system variant keeps Alg. 2's outer loop: same rho sequence, the
+    forcing test met, a descent direction, and a direction within the CG
+    tolerances of Alg. 2's (both approximate F_r(rho)^-1 (-grad_u g))."""
+    C, u, v, g = rand_problem(19, 30, 30, gamma=20.0)
+    P = O.plan(u, v, g, C)
+    rP = O.row_sum(P)
+    r = rP * (1 + 0.05 * np.random.default_rng(20).normal(size=30))
+    r = r / r.sum() * rP.sum()
+    grad_u = rP - r
+    gl1 = np.abs(grad_u).sum()
+    for eta in (0.5, 0.1, 0.01):
+        full = O.newton_solve_full(P, grad_u, gl1, eta, 0.0)
+        ref = O.newton_solve(P, grad_u, gl1, eta, 0.0)
+        assert full.converged
+        assert np.abs(O.F_r_apply(P, 1.0, full.d_u) + grad_u).sum() <= eta * gl1
+        assert -grad_u @ full.d_u > 0
+        for k, rho in enumerate(full.rhos):
+            assert rho == pytest.approx(1 - 4.0 ** -k, abs=1e-15)
+        # both meet the same forcing test, so they differ by at most the sum of
+        # their residuals mapped through F_r(1)'s inverse on the complement of 1
+        diff = full.d_u - ref.d_u
+        diff -= (rP @ diff) / rP.sum()
+        scale = np.abs(ref.d_u - (rP @ ref.d_u) / rP.sum()).sum()
+        assert np.abs(diff).sum() <= 2 * eta * scale + 1e-12
+
+
 def test_armijo_simplification_equals_full_test():
     """K9 (Lemma sufficient-decrease): with c = c(P) and d_v = -P_c d_u,
     g(z + a d) - g(z) - c1 a <grad g, d> == lhs(a) - (1 - c1) a <-grad_u g, d_u>."""
