@@ -418,6 +418,40 @@ def test_smoothing_and_schedule():
     assert O.adjust_schedule(1.5, math.inf) == 2.0
 
 
+def test_mdot_stage_records_follow_alg1():
+    """The per-stage records of mdot restate Alg. 1's schedule, checked here from
+    the paper's rules: gamma^(1) = min(gamma_i, gamma_f); eps_d = min(H(r), H(c)) /
+    gamma^p (line 4) and the projection tolerance eps_d / 2 (line 7), with the
+    final stage's eps_d capped at 2 tol / 3 (reading); q from delta_min by the
+    rule of Sec. 3.3; gamma^(t+1) = min(q gamma^(t), gamma_f) (line 9); and the
+    per-stage counts add up to the totals."""
+    rng = np.random.default_rng(61)
+    n, m = 40, 30
+    C = rng.uniform(0, 1, size=(n, m))
+    r, c = rng.dirichlet(np.ones(n)), rng.dirichlet(np.ones(m))
+    gi, gf, p, tol = 16.0, 2048.0, 1.5, 1e-7
+    res = O.mdot(C, r, c, gamma_i=gi, gamma_f=gf, p=p, tol_final=tol)
+    H = min(-(r * np.log(r)).sum(), -(c * np.log(c)).sum())
+    recs = res.records
+    assert len(recs) == res.stages and res.ok
+    assert recs[0]["gamma"] == min(gi, gf) and recs[-1]["gamma"] == gf
+    q = 2.0
+    for k, rec in enumerate(recs):
+        eps_d = H / rec["gamma"] ** p
+        if rec["gamma"] == gf:
+            eps_d = min(eps_d, 2 * tol / 3)
+        assert rec["eps"] == pytest.approx(eps_d / 2, rel=1e-12)
+        d = rec["delta_min"]
+        q = min(2.0, q * q) if d > 0.95 else (math.sqrt(q) if d < 0.8 else q)
+        assert rec["q_next"] == pytest.approx(q, rel=1e-15)
+        if k + 1 < len(recs):
+            assert recs[k + 1]["gamma"] == pytest.approx(min(q * rec["gamma"], gf), rel=1e-15)
+    assert sum(rec["newton_steps"] for rec in recs) == res.newton_steps
+    assert sum(rec["cg_iters"] for rec in recs) == res.cg_iters
+    assert sum(rec["ls_trials"] for rec in recs) == res.ls_trials
+    assert O.marginal_l1_error(res.u, res.v, gf, C, r, c) <= tol
+
+
 def test_mdot_reaches_tolerance_and_matches_sinkhorn():
     rng = np.random.default_rng(28)
     n = 40
