@@ -6,7 +6,7 @@ kernels: the shapes below cover a ragged
 last column strip, rows longer than one 16 KB stage, fewer rows than SMs (idle
 consumer warps), column vectors too large for six ring warps (four-warp
 variant) and for any ring (register-load fallback inside the same solve).
-Tolerances are the benchmark spec's: marginal L1 <= 1e-6 in mixed precision."""
+Tolerance: marginal L1 <= 1e-6 in mixed precision, as for the other sweeps."""
 import numpy as np
 import pytest
 

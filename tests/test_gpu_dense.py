@@ -1,6 +1,6 @@
 """GPU parity of the dense-cost path against the FP64 oracle, through the C ABI.
 
-Tolerances (the benchmark spec): marginal L1 <= 1e-6, relative transport cost <= 1e-6;
+Tolerances: marginal L1 <= 1e-6, relative transport cost <= 1e-6;
 the FP64 path is held to ~1e-12 on single sweeps. Inputs are seeded and come
 from workloads/ or the oracle, never from the CUDA path."""
 import math
