@@ -42,7 +42,7 @@ typedef enum {
   EOT_ERR_INVALID_ARG = 1,    /* bad pointer, size, kind, precision or parameter */
   EOT_ERR_NONFINITE = 2,      /* NaN/Inf met in potentials, marginals or CG scalars */
   EOT_ERR_CG_MAXITER = 3,     /* a linear CG solve hit max_cg iterations (Alg. 2) */
-  EOT_ERR_LINESEARCH = 4,     /* backtracking hit max_ls halvings (Alg. 4 lines 8-13) */
+  EOT_ERR_LINESEARCH = 4,     /* backtracking hit max_ls halvings (Alg. 4's line search) */
   EOT_ERR_MAXSTAGES = 5,      /* Alg. 1 did not reach gamma_f within max_stages */
   EOT_ERR_MAXNEWTON = 6,      /* Alg. 4 did not reach its tolerance within max_newton */
   EOT_ERR_RANGE = 7,          /* |potential| >= 2^19: outside the mixed-precision split */
@@ -80,9 +80,9 @@ typedef struct {
 } eot_problem;
 
 typedef struct {
-  double gamma_i;      /* initial gamma (Alg. 1 line 1); default 2^4 (Table 3 caption) */
+  double gamma_i;      /* initial gamma (Alg. 1); default 2^4 (Table 3 caption) */
   double gamma_f;      /* final gamma; default 2^12 */
-  double p;            /* eps_d = min(H(r), H(c)) / gamma^p (Alg. 1 line 4); default 1.5 */
+  double p;            /* eps_d = min(H(r), H(c)) / gamma^p (Alg. 1); default 1.5 */
   double q1;           /* initial decay factor q^(1) (Sec. 3.3); default 2 */
   double w_r;          /* row smoothing weight, w_c = 1/2 - w_r (Sec. 3.4); default 0.45 */
   double tol_final;    /* target marginal L1 error at gamma_f; the last stage uses
@@ -115,7 +115,7 @@ typedef struct {
 typedef struct {       /* host-side counters of one eot_solve call */
   int64_t sweeps_cg;        /* O(nm) sweeps inside linear CG (2 per CG iteration) */
   int64_t sweeps_newton;    /* other NewtonSolve sweeps (setup, d_v) */
-  int64_t sweeps_linesearch; /* Armijo trials (Alg. 4 lines 8-13, with the alpha = 0 reference) and line 16 */
+  int64_t sweeps_linesearch; /* Armijo trials of Alg. 4 (with the alpha = 0 reference) and its row LSE after each update */
   int64_t sweeps_sinkhorn;  /* LSE sweeps of ChiSinkhorn (Alg. 3) or of the Sinkhorn projector */
   int64_t sweeps_total;
   int32_t stages, newton_steps, cg_iters, cg_solves, ls_trials, sinkhorn_iters;
@@ -126,7 +126,7 @@ typedef struct {       /* host-side counters of one eot_solve call */
   double grad_l1;           /* ||r~ - r(P)||_1 at the end of the last projection */
   double marg_err_l1;       /* ||r(P) - r||_1 + ||c(P) - c||_1 of the output (unsmoothed r, c) */
   double seconds;           /* wall time of the call */
-  int64_t sweeps_stage;     /* Alg. 4 lines 1-2 at the start of each projection (column and row fixes) */
+  int64_t sweeps_stage;     /* the column fix and row LSE that open each projection of Alg. 4 */
   eot_stage_record* stage_records; /* in: host array for one record per stage (nullable; eot_solve only) */
   int32_t stage_records_cap;       /* in: its capacity */
   int32_t stage_records_len;       /* out: records written, min(stages, capacity) */
@@ -167,7 +167,7 @@ eot_status eot_hvp(eot_handle h, const eot_problem* prob, const double* u, const
  * -grad_u g with Jacobi-preconditioned CG from 0 to ||res||_1 <= (eta/4)||grad g||_1,
  * until ||F_r(1) d_u + grad_u g||_1 <= eta ||grad g||_1; d_u is then taken
  * modulo the gauge (d_u - k 1 with <r(P), d_u - k 1> = 0: the same plans, since
- * F_r(1) 1 = 0 and P_c 1 = 1) and d_v = -P_c d_u (Eq. bellman2 with Alg. 4 line 7). grad_u g = r(P) - r_target, ||grad g||_1 =
+ * F_r(1) 1 = 0 and P_c 1 = 1) and d_v = -P_c d_u (Eq. bellman2 with Alg. 4's d_v step). grad_u g = r(P) - r_target, ||grad g||_1 =
  * ||grad_u g||_1 (assumes c(P) = c, as Alg. 4 maintains).
  * r_target: device [n]. du_out: device [n]; dv_out: device [m] (nullable).
  * rho_out, cg_iters_out: host, nullable (rho of the last CG solve, Appx. B).

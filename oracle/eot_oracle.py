@@ -223,10 +223,10 @@ def newton_solve(P, grad_u, grad_l1, eta, rho0=0.0, max_cg=None):
     grad_u   = r(P) - r (the u-block of the dual gradient);
     grad_l1  = ||grad g||_1 (equals ||grad_u g||_1 when c(P) = c, Alg. 4);
     eta      = forcing parameter.
-    Line 1: rho <- rho0, d_u <- -D(r(P))^-1 grad_u g.
-    Line 2: while ||F_r(1) d_u + grad_u g||_1 > eta ||grad g||_1:
-    Line 3:     d_u <- LinearCGSolve(F_r(rho), -grad_u g, eta / 4), CG from 0;
-    Line 4:     rho <- 1 - (1 - rho) / 4.
+    The discount starts at rho0 and the direction at -D(r(P))^-1 grad_u g; while
+    the undiscounted residual ||F_r(1) d_u + grad_u g||_1 exceeds eta ||grad g||_1,
+    d_u is replaced by a linear CG solve of F_r(rho) d_u = -grad_u g (from 0, to
+    tolerance eta / 4) and 1 - rho is divided by 4.
     Reading: the CG tolerance eta/4 is relative, ||res||_1 <= (eta/4)||grad g||_1
     (Thm. residual uses the same scale). Reading (Appx. B): the returned rho is
     the one the last CG solve used, so that the next call starts from
@@ -392,21 +392,17 @@ def truncated_newton_project(u, v, gamma, C, r, c, eps, rho_last=0.0,
                              max_newton=200, max_ls=40, max_cg=None, newton=None):
     """Algorithm 4 (TruncatedNewtonProject), Sec. 3.2, projecting onto U(r, c) to tolerance eps.
 
-    Line 1:  v <- log c - LSE_c(u 1^T - gamma C)            (so c(P) = c)
-    Line 2:  log r(P) <- u + LSE_r(1 v^T - gamma C)
-    Line 3:  while ||grad g||_1 = ||r - r(P)||_1 > eps:
-    Line 4:      ChiSinkhorn with eps_chi = eps^(2/5)
-    Line 5:      eta <- max(||grad g||_1, 0.8 eps / ||grad g||_1)
-    Line 6:      d_u <- NewtonSolve(grad_u g, P_rc, r(P), eta)
-    Line 7:      d_v <- -P_c d_u
-    Lines 8-13:  backtracking line search on the Armijo test, factor 0.5, c_1 = 0.01
-    Line 14:     u <- u + alpha d_u, v <- v + alpha d_v
-    Line 15:     v <- v + log c - log c(P)
-    Line 16:     log r(P) <- u + LSE_r(1 v^T - gamma C)
-    Line 18: u <- u + log r - log r(P)   (one last row step)
+    Opening: the column fix v <- log c - LSE_c(u 1^T - gamma C) (so c(P) = c), then
+    log r(P) <- u + LSE_r(1 v^T - gamma C). While ||grad g||_1 = ||r - r(P)||_1 > eps:
+    ChiSinkhorn with eps_chi = eps^(2/5); the forcing parameter
+    eta <- max(||grad g||_1, 0.8 eps / ||grad g||_1); d_u <- NewtonSolve(grad_u g,
+    P_rc, r(P), eta) and d_v <- -P_c d_u; a backtracking line search on the Armijo
+    test (factor 0.5, c_1 = 0.01); the update u <- u + alpha d_u, v <- v + alpha d_v
+    and the column fix v <- v + log c - log c(P); log r(P) at the new point.
+    Closing: one last row step u <- u + log r - log r(P).
     rho_last carries the adaptive discount of Appx. B between NewtonSolve calls
     (0 before the first call). Reading: a NewtonSolve call that runs no CG solve
-    leaves rho_last unchanged. newton: the NewtonSolve used at line 6
+    leaves rho_last unchanged. newton: the NewtonSolve used for d_u
     (newton_solve, Algorithm 2, by default; newton_solve_full for the variant
     whose linear solves run on the full discounted system).
     delta_k (Eq. delta_k-ratio) is recorded for every Newton step.
@@ -443,7 +439,7 @@ def truncated_newton_project(u, v, gamma, C, r, c, eps, rho_last=0.0,
         d_v = -(P.T @ d_u) / col_sum(P)
         slope = float(-grad_u @ d_u)  # <-grad_u g, d_u>
         # Reading: the test's left side is taken relative to its computed value at
-        # alpha = 0, which is 0 in exact arithmetic (c(P) = c after lines 1 / 15,
+        # alpha = 0, which is 0 in exact arithmetic (c(P) = c after the column fixes,
         # sum c = 1); measuring it removes the rounding offset of sum P - 1, which
         # near the final tolerance can exceed the sufficient decrease itself.
         lhs0, _ = armijo_lhs(u, v, d_u, d_v, 0.0, gamma, C)
@@ -523,16 +519,13 @@ def mdot(C, r, c, gamma_i=2.0 ** 4, gamma_f=2.0 ** 12, p=1.5, q1=2.0, w_r=0.45,
          projector="newton", newton=None):
     """Algorithm 1 (MDOT) driving Algorithm 4, Sec. 2.2 and Sec. 3.
 
-    Line 1:  t <- 1, gamma^(1) <- min(gamma_i, gamma_f), q^(1) <- q, gamma^(0) <- 0
-    Line 3:  done <- gamma^(t) = gamma_f
-    Line 4:  eps_d <- min(H(r), H(c)) / gamma^p
-    Line 5:  r~, c~ <- SmoothMarginals(r, c, eps_d)
-    Line 6:  at t = 1: z^(0) <- (log r~, log c~), z^(1) <- z^(0)
-    Line 7:  z^(t) <- BregmanProject(z^(t), gamma, C, r~, c~, eps_d / 2)
-    Line 8:  q <- AdjustSchedule(q)
-    Line 9:  gamma^(t+1) <- min(q gamma^(t), gamma_f)
-    Line 10: z^(t+1) <- z^(t) + (gamma^(t+1) - gamma^(t)) / (gamma^(t) - gamma^(t-1)) (z^(t) - z^(t-1))
-    Output:  (u, v) <- the last projected z.
+    It starts at gamma^(1) = min(gamma_i, gamma_f) with q^(1) = q and gamma^(0) = 0.
+    Each stage t: done when gamma^(t) = gamma_f; eps_d = min(H(r), H(c)) / gamma^p;
+    r~, c~ = SmoothMarginals(r, c, eps_d); at t = 1 the potentials start at
+    (log r~, log c~); z^(t) <- BregmanProject(z^(t), gamma, C, r~, c~, eps_d / 2);
+    q <- AdjustSchedule(q); gamma^(t+1) = min(q gamma^(t), gamma_f); the next stage
+    starts from the extrapolation z^(t) + (gamma^(t+1) - gamma^(t)) /
+    (gamma^(t) - gamma^(t-1)) (z^(t) - z^(t-1)). Output: the last projected z.
     Reading: in the final stage eps_d <- min(eps_d, 2 tol_final / 3). Smoothing
     moves r and c by at most 2 (w_r + w_c) eps_d = eps_d in L1, and the projection
     to eps_d / 2 followed by the last row step leaves ||c(P) - c~||_1 <= eps_d / 2,

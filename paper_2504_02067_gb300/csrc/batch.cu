@@ -867,7 +867,7 @@ struct Dev {
         err = EOT_ERR_MAXSTAGES;
         return false;
       }
-      // Alg. 1 line 10: z <- z + ratio (z - z_prev), z_prev <- z
+      // Alg. 1's extrapolated warm start: z <- z + ratio (z - z_prev), z_prev <- z
       const double ratio = (gamma_next - gamma) / (gamma - gamma_prev);
       for (int64_t i = gp.gt; i < n; i += gp.GT) {
         const double ui = ldv(u + i);

@@ -79,7 +79,7 @@ struct CgRowEpi {
 
 // Newton-step setup, row half: y0 = P (P^T d_u0 / c(P)) and the Jacobi sums
 // sum_j P_ij^2 / c(P)_j (Lemma condition-number). check = ||y0||_1, which is
-// ||F_r(1) d_u0 + grad_u g||_1 for d_u0 = -D(r(P))^-1 grad_u g (Alg. 2 line 2).
+// ||F_r(1) d_u0 + grad_u g||_1 for d_u0 = -D(r(P))^-1 grad_u g (Alg. 2's outer test).
 // The operator F_r uses the row sums rPs of this very factorised plan (so that
 // F_r(1) 1 = 0 holds to summation rounding); grad_u g and d_u0 use r(P) from the
 // row LSE, as Alg. 4 defines them.
@@ -146,7 +146,7 @@ struct SetupColEpi {
   __device__ void finish(const double*) {}
 };
 
-// d_v = -P_c d_u = -(P^T d_u) / c(P)  (Alg. 4 line 7).
+// d_v = -P_c d_u = -(P^T d_u) / c(P)  (Alg. 4's d_v step).
 struct DvColEpi {
   static constexpr int kDot = 0;
   const double *colfac, *cP;
@@ -157,7 +157,7 @@ struct DvColEpi {
 
 // Column LSE: lse_j = Bl_j + M + log S.
 //  mode 0: out_j = base_j + lse_j           (log c(P) given the column shift base)
-//  mode 1: out_j = out_j - lse_j            (column fix, Alg. 4 lines 1 and 15)
+//  mode 1: out_j = out_j - lse_j            (the column fixes of Alg. 4)
 // Dot: sum_j exp(base_j + lse_j) (the total mass, for the Armijo test).
 struct ColLseEpi {
   static constexpr int kDot = 1;
@@ -315,8 +315,8 @@ struct CgUpdateFinish {
   }
 };
 
-// Newton-step preparation: r(P) = exp(log r(P)), d_u0 = r~ / r(P) - 1 (Alg. 2
-// line 1), row weights of the setup column sweep.
+// Newton-step preparation: r(P) = exp(log r(P)), d_u0 = r~ / r(P) - 1 (Alg. 2's
+// initial direction), row weights of the setup column sweep.
 template <class T>
 __global__ void prep_setup_kernel(int64_t n, const double* logrP, const double* rt,
                                   const double* rowfac, double* rP, double* du0, T* xw0, T* xw1) {
@@ -410,7 +410,7 @@ __global__ void cg_pupdate_kernel(int64_t n, const double* z, const double* rowf
 
 // Undiscounted Newton residual of the CG iterate: F_r(1) x + grad_u g
 // = -(res + (1 - rho) Yx), with Yx = P D(c)^-1 P^T x accumulated along the CG
-// steps. chk = ||.||_1 (Alg. 2 line 2).
+// steps. chk = ||.||_1 (Alg. 2's outer test).
 static __global__ void cg_check_kernel(int64_t n, const double* res, const double* Yx, double* sc,
                                 double* dotpart, int* cnt) {
   pdl_wait();

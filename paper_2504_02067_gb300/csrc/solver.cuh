@@ -921,9 +921,9 @@ struct Solver {
     double* logrt = h->logrt;
     double* logct = h->logct;
     sweep_bucket = &cnt.sweeps_stage;
-    // line 1: v <- log c~ - LSE_c(u 1^T - gamma C)   (column fix)
+    // opening column fix: v <- log c~ - LSE_c(u 1^T - gamma C)
     col_lse(u, nullptr, v, nullptr, 0.0, logct, v, 1, SC_AUX0, 0.0);
-    // line 2: log r(P) <- u + LSE_r(1 v^T - gamma C)
+    // then log r(P) <- u + LSE_r(1 v^T - gamma C)
     row_lse(u, v, logrt, h->logrP, h->rowmax, rt);
     const double* s = read();
     double gl1 = s[SC_GL1], chi2 = s[SC_CHI2];
@@ -953,15 +953,15 @@ struct Solver {
         if (++sk > 2000) throw EotError{EOT_ERR_MAXNEWTON, "ChiSinkhorn did not converge"};
       }
       if (gl1 <= eps) break;
-      // line 5: forcing parameter
+      // forcing parameter
       const double eta = std::fmax(gl1, 0.8 * eps / gl1);
-      // line 6-7: NewtonSolve and d_v = -P_c d_u
+      // NewtonSolve and d_v = -P_c d_u
       bool ran;
       const double rho0 = std::fmax(0.0, 1.0 - 4.0 * (1.0 - cnt.rho_last));
       const double rho = newton(u, v, rt, gl1, eta, rho0, max_cg, mode, &ran);
       if (ran) cnt.rho_last = rho;
       cnt.newton_steps++;
-      // lines 8-13: backtracking on the simplified Armijo test, whose left side
+      // backtracking on the simplified Armijo test, whose left side
       // (sum P(alpha) - 1) is taken relative to its computed value at alpha = 0
       // (0 in exact arithmetic, since c(P) = c~): this removes the rounding
       // offset of the mass, which near the final tolerance can exceed the
@@ -995,10 +995,10 @@ struct Solver {
         if (++trials > prm.max_ls) throw EotError{EOT_ERR_LINESEARCH, "Armijo backtracking exhausted"};
         alpha *= 0.5;
       }
-      // lines 14-15: u += a d_u; v += a d_v + log c~ - log c(P(a))
+      // update and column fix: u += a d_u; v += a d_v + log c~ - log c(P(a))
       axpy(n, u, 1.0, h->du, alpha);
       axpy(m, v, 1.0, h->dv, alpha, logct, 1.0, h->logcP, -1.0);
-      // line 16: log r(P)
+      // log r(P) at the new point
       sweep_bucket = &cnt.sweeps_ls;
       row_lse(u, v, logrt, h->logrP, h->rowmax, rt);
       s = read();
@@ -1013,7 +1013,7 @@ struct Solver {
       gl1 = new_gl1;
       steps++;
     }
-    // line 18: u <- u + log r~ - log r(P)
+    // closing row step: u <- u + log r~ - log r(P)
     axpy(n, u, 1.0, logrt, 1.0, h->logrP, -1.0);
     *gl1_out = gl1;
     return ok;

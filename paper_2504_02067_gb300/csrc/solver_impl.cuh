@@ -132,7 +132,7 @@ void run_solve(eot_handle h, const eot_problem* P, const eot_params* prm_in, dou
     }
   } release_guard{S};
 
-  // H(r), H(c) and the masses (Alg. 1 line 4 needs min(H(r), H(c)))
+  // H(r), H(c) and the masses (Alg. 1's eps_d needs min(H(r), H(c)))
   launch_k(vec_stats_kernel, dim3(S.vg_n), dim3(kThreads), st, n, P->r, nullptr, 0, h->sc, SC_AUX0, SC_AUX1,
                                                  h->dotpart, h->cnt_dot, h->status);
   EOT_LAUNCH_CHECK();
@@ -214,7 +214,7 @@ void run_solve(eot_handle h, const eot_problem* P, const eot_params* prm_in, dou
     const double gamma_next = round_gamma<T>(std::min(q * gamma, gamma_f));
     if (done) break;
     if (t >= prm.max_stages) throw EotError{EOT_ERR_MAXSTAGES, "gamma_f not reached within max_stages"};
-    // Alg. 1 line 10: z <- z + ratio (z - z_prev), z_prev <- z
+    // Alg. 1's extrapolated warm start: z <- z + ratio (z - z_prev), z_prev <- z
     const double ratio = (gamma_next - gamma) / (gamma - gamma_prev);
     S.copy(h->nt1, u, n);
     S.axpy(n, u, 1.0 + ratio, h->nt0, -ratio);

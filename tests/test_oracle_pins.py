@@ -252,7 +252,7 @@ def test_newton_solve_meets_forcing_and_descends():
         assert res.converged
         assert np.abs(O.F_r_apply(P, 1.0, res.d_u) + grad_u).sum() <= eta * gl1
         assert -grad_u @ res.d_u > 0
-        # rho follows 0, 3/4, 15/16, ... (Alg. 2 line 4)
+        # rho follows 0, 3/4, 15/16, ... (Alg. 2's annealing)
         for k, rho in enumerate(res.rhos):
             assert rho == pytest.approx(1 - 4.0 ** -k, abs=1e-15)
     assert O.next_rho0(0.9375) == pytest.approx(0.75)
@@ -421,10 +421,10 @@ def test_smoothing_and_schedule():
 def test_mdot_stage_records_follow_alg1():
     """The per-stage records of mdot restate Alg. 1's schedule, checked here from
     the paper's rules: gamma^(1) = min(gamma_i, gamma_f); eps_d = min(H(r), H(c)) /
-    gamma^p (line 4) and the projection tolerance eps_d / 2 (line 7), with the
-    final stage's eps_d capped at 2 tol / 3 (reading); q from delta_min by the
-    rule of Sec. 3.3; gamma^(t+1) = min(q gamma^(t), gamma_f) (line 9); and the
-    per-stage counts add up to the totals."""
+    gamma^p and the projection tolerance eps_d / 2, with the final stage's eps_d
+    capped at 2 tol / 3 (reading); q from delta_min by the rule of Sec. 3.3;
+    gamma^(t+1) = min(q gamma^(t), gamma_f); and the per-stage counts add up to
+    the totals."""
     rng = np.random.default_rng(61)
     n, m = 40, 30
     C = rng.uniform(0, 1, size=(n, m))
