@@ -649,8 +649,8 @@ def primal_value(P, C, gamma):
 
 
 def round_to_polytope(F, r, c):
-    """Round(F, r, c): Algorithm 2 of Altschuler, Weed and Rigollet (2017), cited in
-    Alg. 1's last line. Scales rows down to r, then columns down to c, then adds
+    """Round(F, r, c): Algorithm 2 of Altschuler, Weed and Rigollet (2017), which
+    Alg. 1 applies to its output. Scales rows down to r, then columns down to c, then adds
     the rank-one correction err_r err_c^T / ||err_r||_1."""
     x = np.minimum(r / row_sum(F), 1.0)
     F = F * x[:, None]
