@@ -23,7 +23,8 @@
  *    Calls are stream-ordered. Calls with host outputs synchronise the stream.
  *  - Return value: EOT_OK or an error code; the handle keeps a message that
  *    eot_last_error() returns. No call aborts the process. After
- *    EOT_ERR_CUDA the handle should be destroyed.
+ *    EOT_ERR_CUDA the handle should be destroyed; after any other error it
+ *    stays usable.
  *  - Results are bit-reproducible for a fixed handle, problem and stream (all
  *    reductions have a fixed order; no floating-point atomics).
  */
@@ -46,8 +47,12 @@ typedef enum {
   EOT_ERR_MAXSTAGES = 5,      /* Alg. 1 did not reach gamma_f within max_stages */
   EOT_ERR_MAXNEWTON = 6,      /* Alg. 4 did not reach its tolerance within max_newton */
   EOT_ERR_RANGE = 7,          /* |potential| >= 2^19: outside the mixed-precision split */
-  EOT_ERR_CUDA = 8,           /* a CUDA runtime call failed */
-  EOT_ERR_UNSUPPORTED = 9     /* combination of cost kind and precision not built */
+  EOT_ERR_CUDA = 8,           /* a CUDA runtime call failed; destroy the handle */
+  EOT_ERR_UNSUPPORTED = 9,    /* combination of cost kind and precision not built */
+  EOT_ERR_DEVICE_TIMEOUT = 10 /* a bounded device-side wait (an mbarrier of the tensor-core
+                                 sweeps or a group barrier of eot_solve_batched) ran out:
+                                 the kernel recorded it and returned, its outputs are not
+                                 valid, and the handle stays usable */
 } eot_status;
 
 typedef enum {
@@ -135,8 +140,13 @@ typedef struct {       /* host-side counters of one eot_solve call */
 typedef struct eot_handle_s* eot_handle;
 
 /* Create a handle on `device` with workspace for problems up to max_n x max_m
- * (grown on demand by later calls). Allocates device memory; not stream-ordered. */
-eot_status eot_create(eot_handle* out, int device, int64_t max_n, int64_t max_m);
+ * and point dimension max_d (grown on demand by later calls, which then allocate
+ * and synchronise the device). max_d = 0: no point workspace is reserved; max_d
+ * in [1, 64]: the per-point buffers of the point sweeps (for d >= 17 on the
+ * mixed path, the tensor-core digit slices) are reserved now for max_n, max_m
+ * points. Allocates device memory; not stream-ordered. Errors: INVALID_ARG
+ * (max_n, max_m < 1 or max_d outside [0, 64]), CUDA. */
+eot_status eot_create(eot_handle* out, int device, int64_t max_n, int64_t max_m, int64_t max_d);
 /* Free the handle and its workspace. Synchronises the handle's device. */
 eot_status eot_destroy(eot_handle h);
 /* Message of the last error on this handle (never NULL; valid until the next call). */
@@ -194,6 +204,9 @@ eot_status eot_round(eot_handle h, const eot_problem* prob, const double* u, con
 /* Full solve: MDOT (Alg. 1) with adaptive q and asymmetric smoothing, each
  * stage projected by TruncatedNewtonProject (Alg. 4 with Alg. 2 and Alg. 3).
  * u: device [n], v: device [m]: outputs (the last projected potentials at gamma_f).
+ * When a cap (CG_MAXITER, LINESEARCH, MAXNEWTON, MAXSTAGES), a non-finite value
+ * or the split range stops the solve, u and v still receive the last iterate (of
+ * the stage in progress), which does not meet the requested tolerance.
  * stats: host, nullable; with stats->stage_records set (and stats->stage_records_cap
  * > 0) one eot_stage_record per stage of Alg. 1 is written there. Errors: any.
  * Synchronises. */
@@ -217,8 +230,9 @@ eot_status eot_solve(eot_handle h, const eot_problem* prob, const eot_params* pa
  * stats: host [nprob], nullable (sweeps_total only among the sweep counters;
  *   seconds = the whole call; each struct is overwritten, stage_records included).
  * Returns EOT_OK when every problem succeeded, else the status of the first
- * failing problem (in input order); a failure of the launch itself (a group
- * barrier wait bounded at 2 s ran out) returns EOT_ERR_CUDA. Synchronises. */
+ * failing problem (in input order). A group barrier whose bounded wait (2 s)
+ * ran out returns EOT_ERR_DEVICE_TIMEOUT for the whole call (the kernel records
+ * it and every CTA returns); a failed launch returns EOT_ERR_CUDA. Synchronises. */
 eot_status eot_solve_batched(eot_handle h, int32_t nprob, const eot_problem* probs,
                              const eot_params* params, double* const* u, double* const* v,
                              int32_t* status_out, eot_stats* stats, void* stream);
@@ -227,20 +241,61 @@ eot_status eot_solve_batched(eot_handle h, int32_t nprob, const eot_problem* pro
  * out3[1] = own elements per thread and round, out3[2] = groups. Host pointer. */
 eot_status eot_batch_last_config(eot_handle h, int32_t* out3);
 
+/* The EOT value at the potentials (u, v), from the dual (Sec. 2.1, Eq. sinkhorn-dual):
+ *   value = ( <r, u> + <c, v> - sum_ij P_ij + 1 ) / gamma,   P = P(u, v; gamma),
+ * which equals the primal value F* = <P*, C> - H(P*) / gamma at the optimum and is
+ * stationary in (u, v) there, so potentials solved to a marginal tolerance give it
+ * to second order in that tolerance. prob->r and prob->c are required.
+ * value_out: device FP64 scalar. One row log-sum-exp sweep and two O(n) dot
+ * products; asynchronous on `stream` (no host readback).
+ * Errors: INVALID_ARG, NONFINITE, RANGE, CUDA (NONFINITE / RANGE are detected at
+ * the next call that synchronises; the value is then not finite). */
+eot_status eot_value(eot_handle h, const eot_problem* prob, const double* u, const double* v,
+                     double gamma, double* value_out, void* stream);
+
 /* Gradients of the EOT value F* = <P*, C> - H(P*) / gamma at the potentials (u, v)
- * (envelope theorem on the Lagrangian, Appx. A; not stated in the paper):
- *   dC = grad_scale * P                          (dense; device n x m FP32, ld m)
- *   dX_i = grad_scale * 2 s_C sum_j P_ij (x_i - y_j)  (points; device n x d FP32)
- *   dY_j = grad_scale * 2 s_C sum_i P_ij (y_j - x_i)  (points; device m x d FP32)
- *   dr = grad_scale * u / gamma, dc = grad_scale * v / gamma (device FP64)
+ * (envelope theorem on the Lagrangian, Appx. A; not stated in the paper), with
+ * s = grad_scale * (*grad_scale_dev when given):
+ *   dC = s * P                          (dense; device n x m FP32, ld m)
+ *   dX_i = s * 2 s_C sum_j P_ij (x_i - y_j)  (points; device n x d FP32)
+ *   dY_j = s * 2 s_C sum_i P_ij (y_j - x_i)  (points; device m x d FP32)
+ *   dr = s * u / gamma, dc = s * v / gamma (device FP64)
+ * grad_scale_dev: device FP64 scalar, nullable (e.g. the incoming gradient of an
+ * autograd graph, read on the device so that no host synchronisation is needed).
  * Each output nullable. s_C is the problem's cost scale, held constant. P is
  * formed with each side shifted by its own log-marginal, so (u + k, v - k) gives
  * the same outputs for any k. dC needs a dense problem, dX / dY a point problem
  * (EOT_ERR_UNSUPPORTED otherwise). Outputs below the FP32 range flush to zero.
  * Errors: INVALID_ARG, UNSUPPORTED, NONFINITE, CUDA. Synchronises. */
 eot_status eot_backward(eot_handle h, const eot_problem* prob, const double* u, const double* v,
-                        double gamma, double grad_scale, float* dC, float* dX, float* dY,
-                        double* dr, double* dc, void* stream);
+                        double gamma, double grad_scale, const double* grad_scale_dev, float* dC,
+                        float* dX, float* dY, double* dr, double* dc, void* stream);
+
+/* Integer outputs of the plan P = P(u, v; gamma) (Sec. 2.1, Eq. lagrangian-closed-form),
+ * bit-exact by construction: every decision is taken in FP64 on an exponent
+ * formed in a fixed order of correctly rounded operations, with no fused
+ * multiply-add, so any IEEE-754 implementation of the same order agrees:
+ *   C_ij  = (double)C_ij for dense costs (exact); for points
+ *           C_ij = s_C * D_ij, D_ij = (...((x_i0 - y_j0)^2 + (x_i1 - y_j1)^2) + ...),
+ *           the coordinates promoted to FP64 and summed in coordinate order,
+ *           each difference, square, sum and the product with s_C rounded;
+ *   gC_ij = gamma * C_ij (rounded), gamma used as given (not rounded to FP32).
+ *
+ * Row argmax: idx_out[i] = the smallest j maximising P_ij, i.e. maximising
+ * t_ij = v_j - gC_ij (u_i is constant along the row and exp is increasing);
+ * ties go to the lowest index. v: device [m]; idx_out: device int64 [n].
+ * Errors: INVALID_ARG, CUDA. Asynchronous on `stream`. */
+eot_status eot_plan_argmax(eot_handle h, const eot_problem* prob, const double* v, double gamma,
+                           int64_t* idx_out, void* stream);
+
+/* Plan support: the entries with P_ij > tau, decided as
+ *   (u_i + v_j) - gC_ij > log_tau      (log_tau = log(tau), given by the caller),
+ * counted per row into row_counts_out (device int64 [n], nullable) and in total
+ * into total_out (device int64 scalar, nullable). u: device [n], v: device [m].
+ * Errors: INVALID_ARG, CUDA. Asynchronous on `stream`. */
+eot_status eot_plan_support(eot_handle h, const eot_problem* prob, const double* u, const double* v,
+                            double gamma, double log_tau, int64_t* row_counts_out, int64_t* total_out,
+                            void* stream);
 
 /* Measurement aid: times `iters` launches of one sweep kernel at (u, v) with CUDA
  * events recorded on `stream` (after an untimed set-up at the same point):

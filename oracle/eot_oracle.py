@@ -739,6 +739,43 @@ def eot_grads_points(u, v, gamma, X, Y, s_C):
 
 
 # --------------------------------------------------------------------------
+# Integer outputs of the plan: row argmax and support (Reading G12 of the
+# readings list: lowest index on ties, compared bit-exactly). The decisions are
+# taken on the FP64 exponent in a fixed order of rounded operations.
+# --------------------------------------------------------------------------
+
+
+def sqeuclid_ordered(X, Y):
+    """D_ij = sum_k (x_ik - y_jk)^2 in float64 with the coordinates added in order
+    k = 0, 1, ..., d - 1, every difference, square and partial sum rounded on its
+    own (numpy elementwise operations: no fused multiply-add, no pairwise
+    reordering). This is the fixed evaluation order of the integer outputs."""
+    X = np.asarray(X, dtype=np.float64)
+    Y = np.asarray(Y, dtype=np.float64)
+    D = np.zeros((X.shape[0], Y.shape[0]))
+    for k in range(X.shape[1]):
+        diff = X[:, k][:, None] - Y[:, k][None, :]
+        D = D + diff * diff
+    return D
+
+
+def plan_row_argmax(v, gamma, C):
+    """argmax_j P_ij for every row i, P = P(u, v; gamma) (Eq. lagrangian-closed-form).
+    u_i is constant along row i and exp is increasing, so the argmax is that of
+    t_ij = v_j - gamma C_ij (the product and the difference each rounded).
+    Ties go to the lowest index (np.argmax returns the first occurrence)."""
+    t = v[None, :] - gamma * C
+    return np.argmax(t, axis=1).astype(np.int64)
+
+
+def plan_support_counts(u, v, gamma, C, log_tau):
+    """#{j : P_ij > tau} for every row i, decided on the exponent:
+    (u_i + v_j) - gamma C_ij > log tau (each operation rounded, in that order)."""
+    t = (u[:, None] + v[None, :]) - gamma * C
+    return (t > log_tau).sum(axis=1).astype(np.int64)
+
+
+# --------------------------------------------------------------------------
 # Brute force (Birkhoff: the LP optimum over U(1/n, 1/n) is a permutation)
 # --------------------------------------------------------------------------
 

@@ -1,6 +1,7 @@
 """The entropic OT value as a differentiable torch function.
 
-Forward: eot_solve (Alg. 1) to the potentials (u, v) at gamma_f, then
+Forward: eot_solve (Alg. 1) to the potentials (u, v) at gamma_f, then eot_value,
+which returns on the device
     F* = (<r, u> + <c, v> - sum P + 1) / gamma_f,
 the dual value at (u, v). At the optimum it equals the primal value
 <P*, C> - H(P*) / gamma_f with H(P) = -sum P log P (strong duality, Sec. 2.1),
@@ -11,11 +12,11 @@ Backward: eot_backward at the saved potentials (envelope theorem on the
 Lagrangian, Appx. A; s_C held constant):
     dC = P,   dx_i = 2 s_C sum_j P_ij (x_i - y_j),   dy_j = 2 s_C sum_i P_ij (y_j - x_i),
     dr = u / gamma_f,   dc = v / gamma_f,
-each scaled by the incoming gradient. The gradients with respect to r and c are
-defined up to a constant vector (only simplex-tangent directions are admissible).
+each scaled by the incoming gradient, which eot_backward reads on the device
+(no host synchronisation). The gradients with respect to r and c are defined up
+to a constant vector (only simplex-tangent directions are admissible).
 
-All arithmetic runs in libeot.so; this module marshals tensors and the three
-O(n) dot products of the value.
+All arithmetic runs in libeot.so; this module only marshals tensors.
 """
 import torch
 
@@ -36,8 +37,8 @@ class EOTFunction(torch.autograd.Function):
         prob = Problem(C=C, X=X, Y=Y, r=r, c=c, precision=precision, cost_scale=cost_scale)
         u, v, stats = handle.solve(prob, params)
         gamma = float(params.gamma_f)
-        _, _, _, _, tot = handle.marginals(prob, u, v, gamma)
-        value = (torch.dot(r, u) + torch.dot(c, v) - tot.reshape(()) + 1.0) / gamma
+        value = torch.empty((), dtype=torch.float64, device=u.device)
+        handle.eot_value(prob, u, v, gamma, value)
         ctx.handle, ctx.prob, ctx.gamma, ctx.stats = handle, prob, gamma, stats
         ctx.save_for_backward(u, v)
         ctx.mark_non_differentiable(u, v)
@@ -60,8 +61,11 @@ class EOTFunction(torch.autograd.Function):
             dr = torch.empty(prob.n, dtype=torch.float64, device=dev)
         if need[5]:
             dc = torch.empty(prob.m, dtype=torch.float64, device=dev)
-        scale = float(g_value) if g_value is not None else 0.0
-        ctx.handle.eot_backward(prob, u, v, ctx.gamma, scale, dC=dC, dX=dX, dY=dY, dr=dr, dc=dc)
+        if g_value is None:
+            g_value = torch.zeros((), dtype=torch.float64, device=dev)
+        g = g_value.detach().to(device=dev, dtype=torch.float64).contiguous()
+        ctx.handle.eot_backward(prob, u, v, ctx.gamma, 1.0, dC=dC, dX=dX, dY=dY, dr=dr, dc=dc,
+                                grad_scale_dev=g)
         if dC is not None and prob.C is not None and prob.C.dtype != torch.float32:
             dC = dC.to(prob.C.dtype)
         return None, dC, dX, dY, dr, dc, None, None, None

@@ -17,7 +17,7 @@ EOT_OK = 0
 STATUS_NAMES = {0: "EOT_OK", 1: "EOT_ERR_INVALID_ARG", 2: "EOT_ERR_NONFINITE",
                 3: "EOT_ERR_CG_MAXITER", 4: "EOT_ERR_LINESEARCH", 5: "EOT_ERR_MAXSTAGES",
                 6: "EOT_ERR_MAXNEWTON", 7: "EOT_ERR_RANGE", 8: "EOT_ERR_CUDA",
-                9: "EOT_ERR_UNSUPPORTED"}
+                9: "EOT_ERR_UNSUPPORTED", 10: "EOT_ERR_DEVICE_TIMEOUT"}
 
 COST_DENSE_F32, COST_DENSE_F64, COST_SQEUCLID_POINTS = 0, 1, 2
 PRECISIONS = {"fp64": 0, "mixed": 1, "plain_fp32": 2}
@@ -76,7 +76,8 @@ class EotStats(ctypes.Structure):
 EXPORTS = ["eot_create", "eot_destroy", "eot_last_error", "eot_status_string",
            "eot_params_default", "eot_marginals", "eot_hvp", "eot_newton_solve", "eot_solve",
            "eot_backward", "eot_sweep_bench", "eot_marginals_noalloc", "eot_kernel_launches",
-           "eot_solve_batched", "eot_batch_last_config", "eot_round"]
+           "eot_solve_batched", "eot_batch_last_config", "eot_round", "eot_value",
+           "eot_plan_argmax", "eot_plan_support"]
 
 _LIB = None
 
@@ -93,7 +94,7 @@ def load_library(path=None):
     L = ctypes.CDLL(path)
     vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
     P = ctypes.POINTER(EotProblem)
-    L.eot_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, i64, i64]
+    L.eot_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, i64, i64, i64]
     L.eot_destroy.argtypes = [vp]
     L.eot_last_error.argtypes = [vp]
     L.eot_last_error.restype = ctypes.c_char_p
@@ -105,7 +106,10 @@ def load_library(path=None):
     L.eot_newton_solve.argtypes = [vp, P, vp, vp, dbl, vp, dbl, dbl, i32, vp, vp,
                                    ctypes.POINTER(dbl), ctypes.POINTER(i32), vp]
     L.eot_solve.argtypes = [vp, P, ctypes.POINTER(EotParams), vp, vp, ctypes.POINTER(EotStats), vp]
-    L.eot_backward.argtypes = [vp, P, vp, vp, dbl, dbl, vp, vp, vp, vp, vp, vp]
+    L.eot_backward.argtypes = [vp, P, vp, vp, dbl, dbl, vp, vp, vp, vp, vp, vp, vp]
+    L.eot_value.argtypes = [vp, P, vp, vp, dbl, vp, vp]
+    L.eot_plan_argmax.argtypes = [vp, P, vp, dbl, vp, vp]
+    L.eot_plan_support.argtypes = [vp, P, vp, vp, dbl, dbl, vp, vp, vp]
     L.eot_sweep_bench.argtypes = [vp, P, vp, vp, dbl, i32, i32, vp, ctypes.c_size_t, ctypes.POINTER(dbl), vp]
     L.eot_marginals_noalloc.argtypes = [P, vp, vp, dbl, vp, vp, vp, vp]
     L.eot_marginals_noalloc.restype = ctypes.c_int
@@ -118,7 +122,8 @@ def load_library(path=None):
     L.eot_kernel_launches.argtypes = [vp]
     L.eot_kernel_launches.restype = i64
     for f in ("eot_create", "eot_destroy", "eot_marginals", "eot_hvp", "eot_newton_solve",
-              "eot_solve", "eot_backward", "eot_sweep_bench", "eot_solve_batched", "eot_round"):
+              "eot_solve", "eot_backward", "eot_sweep_bench", "eot_solve_batched", "eot_round",
+              "eot_value", "eot_plan_argmax", "eot_plan_support"):
         getattr(L, f).restype = ctypes.c_int
     if path == _build.LIBPATH:
         _LIB = L
@@ -179,11 +184,11 @@ class Problem:
 class Handle:
     """Owns an eot_handle (device workspace)."""
 
-    def __init__(self, device=0, max_n=1, max_m=1):
+    def __init__(self, device=0, max_n=1, max_m=1, max_d=0):
         self.lib = load_library()
         self.h = ctypes.c_void_p()
         self.device = device
-        st = self.lib.eot_create(ctypes.byref(self.h), device, max_n, max_m)
+        st = self.lib.eot_create(ctypes.byref(self.h), device, max_n, max_m, max_d)
         if st != EOT_OK:
             raise EotError(st, "eot_create failed")
 
@@ -252,10 +257,27 @@ class Handle:
         return stats
 
     def eot_backward(self, prob, u, v, gamma, grad_scale=1.0, dC=None, dX=None, dY=None,
-                     dr=None, dc=None, stream=None):
+                     dr=None, dc=None, grad_scale_dev=None, stream=None):
         self.check(self.lib.eot_backward(self.h, prob.ref(), _p(u), _p(v), float(gamma),
-                                         float(grad_scale), _p(dC), _p(dX), _p(dY), _p(dr),
-                                         _p(dc), _stream(stream)))
+                                         float(grad_scale), _p(grad_scale_dev), _p(dC), _p(dX),
+                                         _p(dY), _p(dr), _p(dc), _stream(stream)))
+
+    def eot_value(self, prob, u, v, gamma, value_out, stream=None):
+        """The dual value (<r, u> + <c, v> - sum P + 1) / gamma into a device FP64 scalar."""
+        self.check(self.lib.eot_value(self.h, prob.ref(), _p(u), _p(v), float(gamma), _p(value_out),
+                                      _stream(stream)))
+
+    def eot_plan_argmax(self, prob, v, gamma, idx_out, stream=None):
+        """Row argmax of the plan (lowest index on ties) into a device int64 tensor [n]."""
+        self.check(self.lib.eot_plan_argmax(self.h, prob.ref(), _p(v), float(gamma), _p(idx_out),
+                                            _stream(stream)))
+
+    def eot_plan_support(self, prob, u, v, gamma, log_tau, row_counts_out=None, total_out=None,
+                         stream=None):
+        """Counts of plan entries above exp(log_tau), per row and in total (device int64)."""
+        self.check(self.lib.eot_plan_support(self.h, prob.ref(), _p(u), _p(v), float(gamma),
+                                             float(log_tau), _p(row_counts_out), _p(total_out),
+                                             _stream(stream)))
 
     def eot_sweep_bench(self, prob, u, v, gamma, kind, iters, flush=None, stream=None):
         """Milliseconds per launch of sweep kind `kind`; with `flush` (a device

@@ -1061,7 +1061,7 @@ double launch_batch(eot_handle h, const std::vector<Prob>& probs, const std::vec
   unsigned char* b = (unsigned char*)h->bt_mem;
   for (Out& o : outs) {
     std::memset(&o, 0, sizeof(Out));
-    o.status = EOT_ERR_CUDA;  // stays so if the launch is abandoned before the problem ends
+    o.status = EOT_ERR_DEVICE_TIMEOUT;  // stays so if a barrier wait ran out before the problem ended
   }
   EOT_CUDA(cudaMemcpyAsync(b + Lo.probs, probs.data(), sizeof(Prob) * nprob, cudaMemcpyHostToDevice, st));
   EOT_CUDA(cudaMemcpyAsync(b + Lo.outs, outs.data(), sizeof(Out) * nprob, cudaMemcpyHostToDevice, st));
@@ -1105,7 +1105,7 @@ double launch_batch(eot_handle h, const std::vector<Prob>& probs, const std::vec
   h->bt_last[0] = G;
   h->bt_last[1] = ro;
   h->bt_last[2] = groups;
-  if (abort_flag) throw EotError{EOT_ERR_CUDA, "batched kernel: a group barrier wait ran out"};
+  if (abort_flag) throw EotError{EOT_ERR_DEVICE_TIMEOUT, "batched kernel: a group barrier wait ran out"};
   return ms;
 }
 
@@ -1224,6 +1224,7 @@ extern "C" eot_status eot_solve_batched(eot_handle h, int32_t nprob, const eot_p
                                         int32_t* status_out, eot_stats* stats, void* stream) {
   if (!h) return EOT_ERR_INVALID_ARG;
   try {
+    cudaGetLastError();  // a failed earlier call must not surface in this call's checks
     EOT_CUDA(cudaSetDevice(h->device));
     if (nprob < 0 || (nprob > 0 && (!probs || !params || !u || !v)))
       throw EotError{EOT_ERR_INVALID_ARG, "nprob >= 0; probs, params, u, v required"};

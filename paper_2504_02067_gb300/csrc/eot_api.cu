@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "plan_int.cuh"
 #include "solver.cuh"
 
 using namespace eot;
@@ -37,9 +38,9 @@ void ensure_capacity(eot_handle h, int64_t n, int64_t m) {
   const int64_t L = std::max(N, Mm);
   h->max_strips = (Mm + 31) / 32 + 1;
   h->dot_slots = std::max<int64_t>(std::max<int64_t>((N + kWarps - 1) / kWarps + 1, h->max_strips), kVecCtas);
-  EOT_CUDA(cudaHostAlloc((void**)&h->h_sc, (SC_COUNT + 1) * sizeof(double), cudaHostAllocDefault));
+  EOT_CUDA(cudaHostAlloc((void**)&h->h_sc, (SC_TOTAL + 1) * sizeof(double), cudaHostAllocDefault));
   EOT_CUDA(cudaHostAlloc((void**)&h->h_status, sizeof(int), cudaHostAllocDefault));
-  h->sc = (double*)dev_alloc(h, SC_COUNT * sizeof(double));
+  h->sc = (double*)dev_alloc(h, SC_TOTAL * sizeof(double));
   h->status = (int*)dev_alloc(h, sizeof(int));
   h->cnt_strip = (int*)dev_alloc(h, h->max_strips * sizeof(int));
   h->rowblk_slots = std::max<int64_t>(h->max_rowblk, L / 128 + 2);  // 128-point blocks of the tensor-core sweeps
@@ -47,7 +48,7 @@ void ensure_capacity(eot_handle h, int64_t n, int64_t m) {
   h->maxbuf_len = L / 256 + 8 * (int64_t)h->sms + 64;
   h->maxbuf = (double*)dev_alloc(h, h->maxbuf_len * sizeof(double));
   h->cnt_dot = (int*)dev_alloc(h, sizeof(int));
-  EOT_CUDA(cudaMemset(h->sc, 0, SC_COUNT * sizeof(double)));
+  EOT_CUDA(cudaMemset(h->sc, 0, SC_TOTAL * sizeof(double)));
   EOT_CUDA(cudaMemset(h->status, 0, sizeof(int)));
   EOT_CUDA(cudaMemset(h->cnt_strip, 0, h->max_strips * sizeof(int)));
   EOT_CUDA(cudaMemset(h->cnt_rowblk, 0, h->rowblk_slots * sizeof(int)));
@@ -56,9 +57,9 @@ void ensure_capacity(eot_handle h, int64_t n, int64_t m) {
   h->dotpart = (double*)dev_alloc(h, 2 * h->dot_slots * sizeof(double));
   double** nv[] = {&h->Al, &h->rowfac, &h->rP, &h->logrP, &h->rowmax, &h->rt, &h->logrt,
                    &h->du, &h->x, &h->res, &h->z, &h->p, &h->q, &h->y, &h->Yx, &h->M,
-                   &h->diag, &h->y0, &h->du0, &h->nt0, &h->nt1, &h->rPs, &h->p2};
+                   &h->diag, &h->y0, &h->du0, &h->nt0, &h->nt1, &h->rPs, &h->U};
   for (double** p : nv) *p = (double*)dev_alloc(h, N * sizeof(double));
-  double** mv[] = {&h->Bl, &h->colfac, &h->cP, &h->logcP, &h->ct, &h->logct, &h->dv, &h->mt0, &h->mt1};
+  double** mv[] = {&h->Bl, &h->colfac, &h->cP, &h->logcP, &h->ct, &h->logct, &h->dv, &h->mt0, &h->mt1, &h->V};
   for (double** p : mv) *p = (double*)dev_alloc(h, Mm * sizeof(double));
   void** ev[] = {&h->Ah, &h->Bh, &h->xw0, &h->xw1, &h->zf, &h->wsq, &h->ewr, &h->ewc};
   for (void** p : ev) *p = dev_alloc(h, L * sizeof(double));
@@ -96,6 +97,7 @@ eot_status guarded(eot_handle h, F&& f) {
   if (!h) return EOT_ERR_INVALID_ARG;
   try {
     EOT_CUDA(cudaSetDevice(h->device));
+    cudaGetLastError();  // a failed earlier call must not surface in this call's launch checks
     f();
     h->err = "no error";
     return EOT_OK;
@@ -160,10 +162,38 @@ bool is_f64(const eot_problem* P) {
 
 }  // namespace
 
+namespace {
+// Row argmax (MODE 0) or support counts (MODE 1) of the plan; see plan_int.cuh.
+template <int MODE>
+void run_plan_int(eot_handle h, const eot_problem* P, const double* u, const double* v, double gamma,
+                  double log_tau, int64_t* idx_out, int64_t* counts, int64_t* total, cudaStream_t st) {
+  unsigned long long* tot = reinterpret_cast<unsigned long long*>(total);
+  if (tot) EOT_CUDA(cudaMemsetAsync(tot, 0, sizeof(unsigned long long), st));
+  const dim3 grid((unsigned)((P->n + pint::kWarps - 1) / pint::kWarps));
+  if (P->kind == EOT_COST_SQEUCLID_POINTS) {
+    double sC = P->cost_scale;
+    if (!(sC > 0.0)) {
+      Solver<double> S(h, P, st);  // computes s_C = 1 / max |x_i - y_j|^2 as the solver does
+      sC = S.sC;
+    }
+    launch_k(pint::plan_int_points_kernel<MODE>, grid, dim3(pint::kThreads), st, P->n, P->m, (int)P->d, P->X, P->Y,
+             sC, u, v, gamma, log_tau, idx_out, counts, tot);
+  } else if (P->kind == EOT_COST_DENSE_F64) {
+    launch_k(pint::plan_int_dense_kernel<double, MODE>, grid, dim3(pint::kThreads), st, P->n, P->m,
+             (const double*)P->C, P->ldc, u, v, gamma, log_tau, idx_out, counts, tot);
+  } else {
+    launch_k(pint::plan_int_dense_kernel<float, MODE>, grid, dim3(pint::kThreads), st, P->n, P->m,
+             (const float*)P->C, P->ldc, u, v, gamma, log_tau, idx_out, counts, tot);
+  }
+  EOT_LAUNCH_CHECK();
+  h->launches++;
+}
+}  // namespace
+
 extern "C" {
 
-eot_status eot_create(eot_handle* out, int device, int64_t max_n, int64_t max_m) {
-  if (!out || max_n < 1 || max_m < 1) return EOT_ERR_INVALID_ARG;
+eot_status eot_create(eot_handle* out, int device, int64_t max_n, int64_t max_m, int64_t max_d) {
+  if (!out || max_n < 1 || max_m < 1 || max_d < 0 || max_d > 64) return EOT_ERR_INVALID_ARG;
   *out = nullptr;
   eot_handle h = new eot_handle_s();
   h->device = device;
@@ -174,6 +204,10 @@ eot_status eot_create(eot_handle* out, int device, int64_t max_n, int64_t max_m)
     EOT_CUDA(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, device));
     h->l2_bytes = l2;
     ensure_capacity(h, max_n, max_m);
+    if (max_d > 0) {
+      reserve_points(h, max_n, max_m, (int)max_d, nullptr);
+      EOT_CUDA(cudaDeviceSynchronize());
+    }
   } catch (const EotError& e) {
     free_all(h);
     delete h;
@@ -190,9 +224,9 @@ eot_status eot_destroy(eot_handle h) {
   free_all(h);
   if (h->bt_mem) cudaFree(h->bt_mem);
   if (h->tc_mem) cudaFree(h->tc_mem);
-  if (h->pcg_mem) cudaFree(h->pcg_mem);
   if (h->rd_mem) cudaFree(h->rd_mem);
-  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  for (cudaStream_t& s : h->cap_streams)
+    if (s) cudaStreamDestroy(s);
   delete h;
   return EOT_OK;
 }
@@ -211,6 +245,7 @@ const char* eot_status_string(eot_status s) {
     case EOT_ERR_RANGE: return "EOT_ERR_RANGE";
     case EOT_ERR_CUDA: return "EOT_ERR_CUDA";
     case EOT_ERR_UNSUPPORTED: return "EOT_ERR_UNSUPPORTED";
+    case EOT_ERR_DEVICE_TIMEOUT: return "EOT_ERR_DEVICE_TIMEOUT";
   }
   return "unknown status";
 }
@@ -318,8 +353,8 @@ eot_status eot_solve(eot_handle h, const eot_problem* prob, const eot_params* pa
 }
 
 eot_status eot_backward(eot_handle h, const eot_problem* prob, const double* u, const double* v,
-                        double gamma, double grad_scale, float* dC, float* dX, float* dY,
-                        double* dr, double* dc, void* stream) {
+                        double gamma, double grad_scale, const double* grad_scale_dev, float* dC,
+                        float* dX, float* dY, double* dr, double* dc, void* stream) {
   return guarded(h, [&] {
     check_problem(h, prob, false);
     check_gamma(gamma);
@@ -329,23 +364,60 @@ eot_status eot_backward(eot_handle h, const eot_problem* prob, const double* u, 
     if (dC && pts) throw EotError{EOT_ERR_UNSUPPORTED, "dC needs a dense cost (points: use dX / dY)"};
     cudaStream_t st = (cudaStream_t)stream;
     if (dC) {
-      if (is_f64(prob)) run_backward_dense<double>(h, prob, u, v, gamma, grad_scale, dC, st);
-      else run_backward_dense<float>(h, prob, u, v, gamma, grad_scale, dC, st);
+      if (is_f64(prob)) run_backward_dense<double>(h, prob, u, v, gamma, grad_scale, grad_scale_dev, dC, st);
+      else run_backward_dense<float>(h, prob, u, v, gamma, grad_scale, grad_scale_dev, dC, st);
     }
     if (dX || dY) {
-      if (is_f64(prob)) run_backward_points<double>(h, prob, u, v, gamma, grad_scale, dX, dY, st);
-      else run_backward_points<float>(h, prob, u, v, gamma, grad_scale, dX, dY, st);
+      if (is_f64(prob)) run_backward_points<double>(h, prob, u, v, gamma, grad_scale, grad_scale_dev, dX, dY, st);
+      else run_backward_points<float>(h, prob, u, v, gamma, grad_scale, grad_scale_dev, dX, dY, st);
     }
     const double a = grad_scale / gamma;
     if (dr) {
-      launch_k(axpy4_kernel, dim3(vec_grid(prob->n)), dim3(kThreads), st, prob->n, dr, 0.0, u, a, nullptr, 0.0, nullptr, 0.0);
-      h->launches++;
+      launch_k(axpy4_kernel, dim3(vec_grid(prob->n)), dim3(kThreads), st, prob->n, dr, 0.0, u, a, (const double*)nullptr, (const double*)nullptr, 0.0, (const double*)nullptr, 0.0);
+      launch_k(scale_by_dev_kernel, dim3(vec_grid(prob->n)), dim3(kThreads), st, prob->n, dr, grad_scale_dev);
+      h->launches += 2;
     }
     if (dc) {
-      launch_k(axpy4_kernel, dim3(vec_grid(prob->m)), dim3(kThreads), st, prob->m, dc, 0.0, v, a, nullptr, 0.0, nullptr, 0.0);
-      h->launches++;
+      launch_k(axpy4_kernel, dim3(vec_grid(prob->m)), dim3(kThreads), st, prob->m, dc, 0.0, v, a, (const double*)nullptr, (const double*)nullptr, 0.0, (const double*)nullptr, 0.0);
+      launch_k(scale_by_dev_kernel, dim3(vec_grid(prob->m)), dim3(kThreads), st, prob->m, dc, grad_scale_dev);
+      h->launches += 2;
     }
     EOT_LAUNCH_CHECK();
+  });
+}
+
+eot_status eot_value(eot_handle h, const eot_problem* prob, const double* u, const double* v,
+                     double gamma, double* value_out, void* stream) {
+  return guarded(h, [&] {
+    check_problem(h, prob, true);
+    check_gamma(gamma);
+    if (!u || !v || !value_out) throw EotError{EOT_ERR_INVALID_ARG, "u, v and value_out are required"};
+    cudaStream_t st = (cudaStream_t)stream;
+    if (is_f64(prob)) run_value<double>(h, prob, u, v, gamma, value_out, st);
+    else run_value<float>(h, prob, u, v, gamma, value_out, st);
+  });
+}
+
+
+eot_status eot_plan_argmax(eot_handle h, const eot_problem* prob, const double* v, double gamma,
+                           int64_t* idx_out, void* stream) {
+  return guarded(h, [&] {
+    check_problem(h, prob, false);
+    if (!(gamma >= 0.0) || !std::isfinite(gamma)) throw EotError{EOT_ERR_INVALID_ARG, "gamma must be finite and >= 0"};
+    if (!v || !idx_out) throw EotError{EOT_ERR_INVALID_ARG, "v and idx_out are required"};
+    run_plan_int<0>(h, prob, nullptr, v, gamma, 0.0, idx_out, nullptr, nullptr, (cudaStream_t)stream);
+  });
+}
+
+eot_status eot_plan_support(eot_handle h, const eot_problem* prob, const double* u, const double* v,
+                            double gamma, double log_tau, int64_t* row_counts_out, int64_t* total_out,
+                            void* stream) {
+  return guarded(h, [&] {
+    check_problem(h, prob, false);
+    if (!(gamma >= 0.0) || !std::isfinite(gamma)) throw EotError{EOT_ERR_INVALID_ARG, "gamma must be finite and >= 0"};
+    if (!u || !v) throw EotError{EOT_ERR_INVALID_ARG, "u and v are required"};
+    if (std::isnan(log_tau)) throw EotError{EOT_ERR_INVALID_ARG, "log_tau is NaN"};
+    run_plan_int<1>(h, prob, u, v, gamma, log_tau, nullptr, row_counts_out, total_out, (cudaStream_t)stream);
   });
 }
 

@@ -33,12 +33,17 @@ struct EotError {
       throw EotError{EOT_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e_)}; \
   } while (0)
 
-// captured CG iteration graph, keyed by everything baked into its kernel arguments
-typedef std::tuple<int, int, int, int64_t, int64_t, int64_t, uintptr_t> CgKey;
-struct CgGraph {
+// A captured device-controlled program (one stage of Alg. 1, or one NewtonSolve),
+// keyed by everything baked into its kernel arguments. The kernels of its top
+// level and of each conditional body are counted at capture time, so that the
+// kernels a launch ran follow from the device's loop counters.
+typedef std::tuple<int, int, int, int64_t, int64_t, int64_t, uintptr_t> ProgKey;
+constexpr int kProgBodies = 8;
+struct ProgGraph {
   cudaGraphExec_t exec = nullptr;
   cudaGraph_t graph = nullptr;
-  int iters_per_launch = 0;
+  int64_t top_kernels = 0;
+  int64_t body_kernels[kProgBodies] = {};
 };
 
 struct eot_handle_s {
@@ -51,8 +56,8 @@ struct eot_handle_s {
   std::vector<void*> allocs;
 
   // scalars and status
-  double* sc = nullptr;     // device [SC_COUNT]
-  double* h_sc = nullptr;   // pinned host [SC_COUNT + 1] (last slot: status as double)
+  double* sc = nullptr;     // device [SC_TOTAL]
+  double* h_sc = nullptr;   // pinned host [SC_TOTAL + 1]
   int* status = nullptr;    // device
   int* h_status = nullptr;  // pinned host
   // sweep scratch
@@ -67,21 +72,20 @@ struct eot_handle_s {
   double *z = nullptr, *p = nullptr, *q = nullptr, *y = nullptr, *Yx = nullptr, *M = nullptr;
   double *diag = nullptr, *y0 = nullptr, *du0 = nullptr, *nt0 = nullptr, *nt1 = nullptr;
   double* rPs = nullptr;  // row sums of the factorised plan used inside F_r
-  double* p2 = nullptr;   // second p buffer of the persistent CG kernel
+  double* U = nullptr;    // working potentials of the device-controlled programs
   // FP64 m-vectors
   double *Bl = nullptr, *colfac = nullptr, *cP = nullptr, *logcP = nullptr, *ct = nullptr;
   double *logct = nullptr, *dv = nullptr, *mt0 = nullptr, *mt1 = nullptr;
+  double* V = nullptr;
   // element-type vectors (8 bytes per entry, used as float or double)
   void *Ah = nullptr, *Bh = nullptr, *xw0 = nullptr, *xw1 = nullptr, *zf = nullptr;
   void *wsq = nullptr, *ewr = nullptr, *ewc = nullptr;
 
-  std::map<CgKey, CgGraph> graphs;
-  cudaStream_t cap_stream = nullptr;
+  std::map<ProgKey, ProgGraph> graphs;
+  cudaStream_t cap_streams[8] = {};  // one capture stream per nesting depth of a program
 
   // eot_solve_batched: its own device block (not in `allocs`: growing the
   // single-problem buffers must not free it) and the autotuner's choices
-  void* pcg_mem = nullptr;  // persistent CG kernel: CTA partials, barrier counter (own block)
-  size_t pcg_bytes = 0;
   void* rd_mem = nullptr;  // Round: FP64 vectors and column partials (own block)
   size_t rd_bytes = 0;
   void* tc_mem = nullptr;  // tensor-core point path: digit slices and row data (own block)
@@ -97,13 +101,21 @@ namespace eot {
 // Kernel launch with programmatic stream serialisation (PDL): the kernel may
 // begin while its predecessor in the stream drains; every kernel of this
 // library calls pdl_wait() before touching data of earlier kernels.
-// EOT_PDL=0 in the environment turns the attribute off.
+// EOT_PDL=0 in the environment turns the attribute off. A captured launch that
+// directly follows a conditional graph node gets a plain edge (programmatic
+// edges join kernel nodes only): the capture sets pdl_skip_next.
 inline bool pdl_enabled() {
   static const bool on = [] {
     const char* e = std::getenv("EOT_PDL");
     return !(e && e[0] == '0');
   }();
   return on;
+}
+inline thread_local bool pdl_skip_next = false;
+inline unsigned pdl_attrs() {
+  const bool on = pdl_enabled() && !pdl_skip_next;
+  pdl_skip_next = false;
+  return on ? 1u : 0u;
 }
 // launch_k with dynamic shared memory
 template <typename... KArgs, typename... Args>
@@ -118,7 +130,7 @@ inline void launch_kd(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t sm
   at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   at[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
-  cfg.numAttrs = pdl_enabled() ? 1 : 0;
+  cfg.numAttrs = pdl_attrs();
   const cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
   if (e != cudaSuccess)
     throw EotError{EOT_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e)};
@@ -134,7 +146,7 @@ inline void launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream
   at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   at[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
-  cfg.numAttrs = pdl_enabled() ? 1 : 0;
+  cfg.numAttrs = pdl_attrs();
   const cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
   if (e != cudaSuccess)
     throw EotError{EOT_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e)};

@@ -5,6 +5,8 @@
 // Device scalars live in one FP64 array `sc` indexed by the Sc enum, so that
 // captured CUDA graphs stay valid when rho, gamma or tolerances change.
 #pragma once
+#include <algorithm>
+
 #include "sweep.cuh"
 
 namespace eot {
@@ -13,7 +15,8 @@ enum Sc : int {
   SC_RZ = 0, SC_PQ, SC_ALPHA, SC_BETA, SC_RESL1, SC_TOL, SC_RHO, SC_ITERS, SC_ACTIVE, SC_MAXIT,
   SC_CHECK, SC_GL1, SC_CHI2, SC_LHS, SC_SLOPE, SC_MASS, SC_CHK, SC_GAMMA, SC_AUX0, SC_AUX1,
   SC_GRD, SC_GMASS,  // <r(P), d_u> and sum r(P): the gauge component of d_u
-  SC_COUNT = 32
+  SC_COUNT = 32,     // the slots the sweeps and O(n) kernels use (eot_marginals_noalloc keeps these)
+  SC_TOTAL = 64      // with the stage control's slots (control.cuh): the handle's array
 };
 
 // ----------------------------------------------------------------------------
@@ -217,21 +220,35 @@ struct HvpEpi {
 // O(n) kernels
 // ----------------------------------------------------------------------------
 
-constexpr int kVecCtas = 64;  // fixed grid of the O(n) kernels (deterministic sums)
+constexpr int kVecCtas = 64;  // fixed grid of the O(n) kernels of eot_marginals_noalloc
 
 inline int vec_grid(int64_t n) {
   int64_t g = (n + kThreads - 1) / kThreads;
   return (int)(g < 1 ? 1 : (g > kVecCtas ? kVecCtas : g));
 }
 
+// The solver's O(n) kernels run one warp per CTA, spread over all SMs: their
+// cost is FP64 instructions (the exponent splits, the CG vectors and dots), and
+// this GPU's FP64 pipe retires about two lanes per SM and clock, so a CTA of
+// eight warps on one SM would serialise eight warps' FP64 work. With the grid
+// at most four CTAs per SM (and at most `slots` CTAs, the deterministic
+// reduction's partial slots) each element is usually one thread's work.
+constexpr int kOnThreads = 32;
+constexpr int kOnWarps = kOnThreads / 32;
+inline int on_grid(int64_t n, int sms, int64_t slots) {
+  int64_t g = (n + kOnThreads - 1) / kOnThreads;
+  const int64_t cap = std::min<int64_t>(4 * (int64_t)sms, slots);
+  if (g > cap) g = cap;
+  return (int)(g < 1 ? 1 : g);
+}
+
 // Split A = x + alpha*y - z into a high part h (multiple of 1/8, exact in T)
 // and a low FP64 part l; optional ew = (T)exp(l), fac = exp(fshift + l).
 // plain != 0: round A to T directly and drop the remainder (plain FP32 path).
 template <class T>
-__global__ void split_kernel(int64_t n, const double* x, const double* y, double alpha,
-                             const double* z, int plain, T* h, double* l, T* ew, double* fac,
-                             const double* fshift, int* status) {
-  pdl_wait();
+__device__ __forceinline__ void split_range(int64_t n, const double* x, const double* y, double alpha,
+                                            const double* z, int plain, T* h, double* l, T* ew, double* fac,
+                                            const double* fshift, int* status) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     double A = x[i];
@@ -259,15 +276,31 @@ __global__ void split_kernel(int64_t n, const double* x, const double* y, double
     if (fac) fac[i] = exp((fshift ? fshift[i] : 0.0) + ll);
   }
 }
+template <class T>
+__global__ void split_kernel(int64_t n, const double* x, const double* y, double alpha,
+                             const double* z, int plain, T* h, double* l, T* ew, double* fac,
+                             const double* fshift, int* status) {
+  pdl_wait();
+  split_range<T>(n, x, y, alpha, z, plain, h, l, ew, fac, fshift, status);
+}
+// The same split with alpha read on the device (a line-search step decided there).
+template <class T>
+__global__ void split_dev_kernel(int64_t n, const double* x, const double* y, const double* alpha,
+                                 const double* z, int plain, T* h, double* l, T* ew, double* fac,
+                                 const double* fshift, int* status) {
+  pdl_wait();
+  split_range<T>(n, x, y, *alpha, z, plain, h, l, ew, fac, fshift, status);
+}
 
 // Deterministic grid reduction of up to two per-thread values: warp sums, then
-// cta_dot_finish (fixed CTA order). Epi::finish receives the totals.
+// cta_dot_finish (fixed CTA order). Epi::finish receives the totals. Kernels that
+// call it are launched with kOnThreads threads per CTA.
 template <int ND, class Epi>
 __device__ __forceinline__ void vec_finish(double (&v)[2], double* dotpart, int* cnt, Epi& epi) {
   double wd[ND > 0 ? ND : 1];
 #pragma unroll
   for (int k = 0; k < ND; ++k) wd[k] = warp_sum(v[k]);
-  cta_dot_finish<ND>(wd, blockIdx.x, gridDim.x, dotpart, cnt, epi);
+  cta_dot_finish<ND, Epi, kOnWarps>(wd, blockIdx.x, gridDim.x, dotpart, cnt, epi);
 }
 
 struct SlotFinish {
@@ -284,12 +317,15 @@ struct SlotFinish {
 struct CgInitFinish {
   static constexpr int kDot = 2;
   double* sc;
+  cudaGraphConditionalHandle cond;  // the CG loop's conditional node (0: none)
   __device__ void finish(const double* t) {
     sc[SC_RZ] = t[0];
     sc[SC_RESL1] = t[1];
     sc[SC_ITERS] = 0.0;
     sc[SC_BETA] = 0.0;
-    sc[SC_ACTIVE] = (t[1] > sc[SC_TOL] && isfinite(t[0])) ? 1.0 : 0.0;
+    const bool go = t[1] > sc[SC_TOL] && isfinite(t[0]);
+    sc[SC_ACTIVE] = go ? 1.0 : 0.0;
+    if (cond) cudaGraphSetConditional(cond, go ? 1u : 0u);
   }
 };
 
@@ -341,7 +377,7 @@ template <class T>
 __global__ void cg_init_kernel(int64_t n, const double* rP, const double* rPs, const double* rt,
                                const double* diag, const double* rowfac, double* M, double* x,
                                double* res, double* z, double* p, double* Yx, T* xw, double* sc,
-                               double* dotpart, int* cnt) {
+                               double* dotpart, int* cnt, cudaGraphConditionalHandle cond) {
   pdl_wait();
   const double rho = sc[SC_RHO];
   double v[2] = {0.0, 0.0};
@@ -360,7 +396,7 @@ __global__ void cg_init_kernel(int64_t n, const double* rP, const double* rPs, c
     v[0] += b * zi;
     v[1] += fabs(b);
   }
-  CgInitFinish f{sc};
+  CgInitFinish f{sc, cond};
   vec_finish<2>(v, dotpart, cnt, f);
 }
 
@@ -457,10 +493,12 @@ __global__ void prep_dv_kernel(int64_t n, double* du, const double* rowfac, cons
   vec_finish<1>(v, dotpart, cnt, f);
 }
 
-// y = a*x + b*y + c*z (+ d*w): small FP64 vector updates of the outer loops.
+// y = a*x + b*y + c*z (+ d*w): small FP64 vector updates of the outer loops;
+// a_dev (nullable) multiplies a by a device scalar (a line-search step).
 static __global__ void axpy4_kernel(int64_t n, double* y, double b, const double* x, double a,
-                             const double* z, double c, const double* w, double d) {
+                                    const double* a_dev, const double* z, double c, const double* w, double d) {
   pdl_wait();
+  if (a_dev) a *= *a_dev;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     double t = b == 0.0 ? 0.0 : b * y[i];
@@ -609,6 +647,37 @@ static __global__ void exp_kernel(int64_t n, const double* x, double* y) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     y[i] = exp(x[i]);
+}
+
+// y *= *s (nullable s: no-op): applies a device-resident scale, e.g. the
+// incoming gradient of an autograd graph, without a host round trip.
+static __global__ void scale_by_dev_kernel(int64_t n, double* y, const double* s) {
+  pdl_wait();
+  if (!s) return;
+  const double f = *s;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i] *= f;
+}
+
+// <a, b> into sc[slot] (deterministic grid reduction).
+static __global__ void dot_kernel(int64_t n, const double* a, const double* b, double* sc, int slot,
+                                  double* dotpart, int* cnt) {
+  pdl_wait();
+  double v[2] = {0.0, 0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    v[0] += a[i] * b[i];
+  SlotFinish f{sc, slot, -1, 0.0, 0.0};
+  vec_finish<1>(v, dotpart, cnt, f);
+}
+
+// The dual value (<r, u> + <c, v> - sum P + 1) / gamma from the device scalars
+// of the two dot products and the plan's mass (Eq. sinkhorn-dual).
+static __global__ void dual_value_kernel(const double* sc, int s_ru, int s_cv, int s_mass, double gamma,
+                                         double* out) {
+  pdl_wait();
+  *out = (sc[s_ru] + sc[s_cv] - sc[s_mass] + 1.0) / gamma;
 }
 
 static __global__ void set_scalar_kernel(double* sc, int slot, double v) {

@@ -1,12 +1,12 @@
-// Host orchestration of the truncated-Newton EOT solver over the sweep kernels.
-//   Alg. 1 (MDOT, adaptive q, smoothing)  -> run_solve
-//   Alg. 4 (TruncatedNewtonProject)       -> Solver::project
-//   Alg. 3 (ChiSinkhorn)                  -> inside Solver::project
-//   Alg. 2 (NewtonSolve) + Jacobi PCG     -> Solver::newton
-// Control flow stays on the host; every test reads a few FP64 scalars that the
-// kernels reduced on the device. The CG iterations of one linear solve run as a
-// captured CUDA graph of several iterations whose kernels turn into no-ops once
-// the device-side stop flag is cleared (or, optionally, as a graph WHILE node).
+// Orchestration of the truncated-Newton EOT solver over the sweep kernels.
+//   Alg. 1 (MDOT, adaptive q, smoothing)  -> run_solve (host: one iteration per stage)
+//   Alg. 4 (TruncatedNewtonProject)       -> Solver::emit_stage / Solver::project
+//   Alg. 3 (ChiSinkhorn)                  -> inside emit_stage
+//   Alg. 2 (NewtonSolve) + Jacobi PCG     -> Solver::emit_newton
+// Alg. 1's schedule stays on the host; each stage is one device-controlled
+// program (control.cuh): its loops and branches are decided on the device from
+// the FP64 scalars the sweeps reduce, and it runs as one CUDA graph launch with
+// conditional nodes, followed by one read of the device scalars.
 #pragma once
 #include <chrono>
 #include <cmath>
@@ -14,35 +14,87 @@
 #include <cstring>
 #include <vector>
 
+#include "control.cuh"
 #include "handle.cuh"
 #include "sweep_pts.cuh"
 #include "sweep_tc.cuh"
-#include "sweep_bulk.cuh"
-#include "cg_persistent.cuh"
 
 namespace eot {
 
+// host-side totals of one call
 struct SolveCounters {
   int64_t sweeps_cg = 0, sweeps_newton = 0, sweeps_ls = 0, sweeps_sk = 0, sweeps_stage = 0, sweeps_other = 0;
   int64_t cg_iters = 0, cg_solves = 0, newton_steps = 0, ls_trials = 0, sk_iters = 0;
   int64_t curvature_stops = 0;
-  double rho_last = 0.0;
 };
 
-enum class CgMode { kHost, kBatch, kWhile };
-
-// Default: one graph launch per linear CG solve, its WHILE node re-evaluated
-// every kWhileBody iterations (no host round trip inside the solve); "batch":
-// graph launches of six iterations with a host check of the stop flag after
-// each (measured 4% slower on the 64 x 64 grid workload); "none": direct
-// launches, four iterations per check.
-constexpr int kWhileBody = 8;
-inline CgMode cg_mode_from_env() {
-  const char* e = std::getenv("EOT_CG_GRAPH");
-  if (!e) return CgMode::kWhile;
-  if (!std::strcmp(e, "batch")) return CgMode::kBatch;
-  if (!std::strcmp(e, "none")) return CgMode::kHost;
-  return CgMode::kWhile;
+// ---- point-cloud geometry: own blocks of 256 RO elements x S chunks ----
+struct PtsGeo {
+  int64_t B, S, chunk;
+};
+inline int pts_ro(int d) { return d <= 4 ? 4 : (d <= 16 ? 2 : 1); }
+inline PtsGeo pts_geo_of(eot_handle h, int64_t n_own, int64_t n_oth, int d) {
+  PtsGeo g;
+  g.B = (n_own + (int64_t)kThreads * pts_ro(d) - 1) / ((int64_t)kThreads * pts_ro(d));
+  int64_t S = (2 * (int64_t)h->sms + g.B - 1) / g.B;
+  S = std::max<int64_t>(1, std::min<int64_t>(S, (n_oth + 31) / 32));
+  g.chunk = ((n_oth + S - 1) / S + 31) / 32 * 32;
+  g.S = (n_oth + g.chunk - 1) / g.chunk;
+  return g;
+}
+// tensor-core sweeps: own blocks of 128 points x S chunks of the other side
+// (multiples of 48), S chosen so that B S fills whole waves of one-CTA-per-SM blocks
+struct TcGeo {
+  int64_t B, S, chunk;
+};
+inline TcGeo tc_geo_of(eot_handle h, int64_t n_own, int64_t n_oth) {
+  TcGeo g;
+  g.B = (n_own + tc::kM - 1) / tc::kM;
+  double best = -1.0;
+  g.S = 1;
+  g.chunk = (n_oth + tc::kN - 1) / tc::kN * tc::kN;
+  for (int64_t S = 1; S <= 128; ++S) {
+    const int64_t chunk = ((n_oth + S - 1) / S + tc::kN - 1) / tc::kN * tc::kN;
+    const int64_t Sr = (n_oth + chunk - 1) / chunk;
+    if (Sr != S) continue;
+    if (S > 1 && chunk < 2 * tc::kN) break;
+    const int64_t ctas = g.B * S, waves = (ctas + h->sms - 1) / h->sms;
+    const double eff = (double)ctas / (double)(waves * h->sms) - 0.002 * (double)S;  // prefer fewer chunks
+    if (eff > best) {
+      best = eff;
+      g.S = S;
+      g.chunk = chunk;
+    }
+  }
+  return g;
+}
+// digit slices and per-point data of both clouds for the tensor-core sweeps
+inline size_t tc_mem_bytes(int64_t n, int64_t m) {
+  auto side = [](int64_t np) { return (size_t)np * (tc::kSlices * 64 * 2 + 3 * 4) + 1024; };
+  return side(tc::pad_rows(n)) + side(tc::pad_rows(m));
+}
+inline void ensure_tc_mem(eot_handle h, int64_t n, int64_t m, cudaStream_t st) {
+  const size_t need = tc_mem_bytes(n, m);
+  if (need <= h->tc_bytes) return;
+  EOT_CUDA(cudaStreamSynchronize(st));
+  free_graphs(h);  // captured programs hold pointers into the old block
+  if (h->tc_mem) cudaFree(h->tc_mem);
+  h->tc_mem = nullptr;
+  h->tc_bytes = 0;
+  EOT_CUDA(cudaMalloc(&h->tc_mem, need));
+  h->tc_bytes = need;
+}
+// Reserves every buffer a point problem of n x m points in dimension d needs
+// (the FP64 partials of both sweep orientations; for d >= tc::kMinD also the
+// tensor-core slices), so that later calls on such problems do not allocate.
+inline void reserve_points(eot_handle h, int64_t n, int64_t m, int d, cudaStream_t st) {
+  ensure_rowpart_elems(h, kPtsMaxPartials * pts_geo_of(h, n, m, d).S * n);
+  ensure_rowpart_elems(h, kPtsMaxPartials * pts_geo_of(h, m, n, d).S * m);
+  if (d >= tc::kMinD) {
+    ensure_tc_mem(h, n, m, st);
+    ensure_rowpart_elems(h, kPtsMaxPartials * tc_geo_of(h, n, m).S * n);
+    ensure_rowpart_elems(h, kPtsMaxPartials * tc_geo_of(h, m, n).S * m);
+  }
 }
 
 template <class T>
@@ -89,150 +141,15 @@ struct Solver {
       const bool aligned = ((uintptr_t)C % 16) == 0;
       V = (aligned && (m % VEC) == 0 && (ldc % VEC) == 0) ? VEC : 1;
     }
-    vg_n = vec_grid(n);
-    vg_m = vec_grid(m);
+    vg_n = on_grid(n, h->sms, h->dot_slots);
+    vg_m = on_grid(m, h->sms, h->dot_slots);
     rg = row_grid(n);
     geo = col_geo(h, n, m, V);
     sweep_bucket = &cnt.sweeps_other;
-    if constexpr (sizeof(T) == 4) {
-      if (!points) setup_bulk();
-    }
   }
 
-  // ---- bulk-copy sweeps (dense FP32 cost, 16-byte rows, large enough) ----
-  bool bulk_rows = false, bulk_cols = false;
-  int bulk_rg = 0;                 // row sweep: CTAs
-  int bulk_br = 0, bulk_R = 0;     // column sweep: rows per block, blocks
-  int64_t bulk_S = 0;              // column sweep: strips of kColSW columns
-  int bulk_stages = 0;             // column sweep: ring stages
-  CUtensorMap bulk_map;            // column sweep: the cost as an m x n tensor of kColSW x kColRB boxes
-  // Opt-in (EOT_BULK=1): on the 64 x 64 grid workload these sweeps measured
-  // slower than the register-load kernels (CG halves 17.7 / 16.5 us against
-  // 13.1 / 14.7 us back to back, solve 0.118 s against 0.091 s), so they are not
-  // the default.
-  static bool bulk_enabled() {
-    const char* e = std::getenv("EOT_BULK");
-    return e && e[0] == '1';
-  }
-  static void bulk_attr(const void* kernel) {
-    EOT_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  bulk::kSmemOptIn - bulk::kBarBytes));
-  }
-  // cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link)
-  typedef CUresult (*EncodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-  static EncodeTiled encode_tiled() {
-    static EncodeTiled fn = [] {
-      void* f = nullptr;
-      cudaDriverEntryPointQueryResult q;
-      if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
-              cudaSuccess ||
-          q != cudaDriverEntryPointSuccess)
-        f = nullptr;
-      return (EncodeTiled)f;
-    }();
-    return fn;
-  }
-  void setup_bulk() {
-    if (!bulk_enabled() || V != VEC || n * m < bulk::kMinEntries || m < 128) return;
-    bulk_rg = (int)std::min<int64_t>(std::min<int64_t>(h->sms, n), h->dot_slots);
-    bulk_rows = true;
-    // column strips of kColSW columns x row blocks (multiples of kColRB rows)
-    // filling the SMs once
-    const int64_t S = (m + bulk::kColSW - 1) / bulk::kColSW;
-    int64_t R = std::min<int64_t>(std::min<int64_t>(h->sms / std::max<int64_t>(S, 1), (n + bulk::kColRB - 1) / bulk::kColRB),
-                                  h->max_rowblk);
-    EncodeTiled enc = encode_tiled();
-    if (S <= h->sms && S <= h->max_strips && S <= h->dot_slots && R >= 1 && enc) {
-      int64_t BR = (n + R - 1) / R;
-      BR = (BR + bulk::kColRB - 1) / bulk::kColRB * bulk::kColRB;
-      R = (n + BR - 1) / BR;
-      const int64_t room = bulk::kSmemOptIn - 1024 - bulk::kBarBytes - 3 * BR * 4;
-      const int stages = (int)std::min<int64_t>(bulk::kColMaxStages, room / bulk::kStageBytes);
-      const cuuint64_t dims[2] = {(cuuint64_t)m, (cuuint64_t)n};
-      const cuuint64_t strides[1] = {(cuuint64_t)ldc * sizeof(float)};
-      const cuuint32_t box[2] = {(cuuint32_t)bulk::kColSW, (cuuint32_t)bulk::kColRB};
-      const cuuint32_t estr[2] = {1, 1};
-      if (stages >= 4 &&
-          enc(&bulk_map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)C, dims, strides, box, estr,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS) {
-        bulk_S = S;
-        bulk_R = (int)R;
-        bulk_br = (int)BR;
-        bulk_stages = stages;
-        bulk_cols = true;
-      }
-    }
-    static bool attrs = false;
-    if (!attrs) {
-      // every instantiation, before any graph capture
-      bulk_attr((const void*)bulk::row_bulk_kernel<12, 1, 1, true, 0, RowLseEpi>);
-      bulk_attr((const void*)bulk::row_bulk_kernel<8, 1, 1, true, 0, RowLseEpi>);
-      bulk_attr((const void*)bulk::row_bulk_kernel<12, 1, 3, false, 2, SetupRowEpi>);
-      bulk_attr((const void*)bulk::row_bulk_kernel<8, 1, 3, false, 2, SetupRowEpi>);
-      bulk_attr((const void*)bulk::row_bulk_kernel<12, 1, 1, false, 0, CgRowEpi>);
-      bulk_attr((const void*)bulk::row_bulk_kernel<8, 1, 1, false, 0, CgRowEpi>);
-      bulk_attr((const void*)bulk::col_bulk_kernel<1, true, ColLseEpi>);
-      bulk_attr((const void*)bulk::col_bulk_kernel<2, false, SetupColEpi<float>>);
-      bulk_attr((const void*)bulk::col_bulk_kernel<1, false, CgColEpi<float>>);
-      bulk_attr((const void*)bulk::col_bulk_kernel<1, false, DvColEpi>);
-      attrs = true;
-    }
-  }
-  // Bulk row sweep when eligible: twelve one-stage consumer warps when the
-  // column vectors fit beside their 192 KB ring, else eight; false: use the
-  // register-load kernel.
-  template <int NR, bool LSE, int SQM, class Epi>
-  bool launch_row_bulk(cudaStream_t s, const SweepArgs<T>& a, const Epi& e) {
-    if constexpr (sizeof(T) != 4) {
-      return false;
-    } else {
-      if (!bulk_rows) return false;
-      constexpr int NV = 1 + (LSE ? 1 : NR);
-      const size_t s12 = bulk::row_smem_bytes(12, NV, m), s8 = bulk::row_smem_bytes(8, NV, m);
-      if (s12 + 1024 <= (size_t)bulk::kSmemOptIn)
-        launch_kd(bulk::row_bulk_kernel<12, 1, NR, LSE, SQM, Epi>, dim3(bulk_rg), dim3(13 * 32), s12, s, a, e);
-      else if (s8 + 1024 <= (size_t)bulk::kSmemOptIn)
-        launch_kd(bulk::row_bulk_kernel<8, 1, NR, LSE, SQM, Epi>, dim3(bulk_rg), dim3(9 * 32), s8, s, a, e);
-      else
-        return false;
-      return true;
-    }
-  }
-  template <int NC, bool LSE, class Epi>
-  bool launch_col_bulk(cudaStream_t s, const SweepArgs<T>& a, const Epi& e) {
-    if constexpr (sizeof(T) != 4) {
-      return false;
-    } else {
-      if (!bulk_cols) return false;
-      SweepArgs<T> b = a;
-      b.rows_per_block = bulk_br;
-      b.nrowblk = bulk_R;
-      b.stages = bulk_stages;
-      const size_t smem = (size_t)bulk::kBarBytes + (size_t)bulk_stages * bulk::kStageBytes + 3 * (size_t)bulk_br * 4;
-      launch_kd(bulk::col_bulk_kernel<NC, LSE, Epi>, dim3((unsigned)bulk_S, (unsigned)bulk_R),
-                dim3(bulk::kColThreads), smem, s, b, e, bulk_map);
-      return true;
-    }
-  }
-
-  // ---- point-cloud geometry: own blocks of 256 RO elements x S chunks ----
-  struct PtsGeo {
-    int64_t B, S, chunk;
-  };
-  static int pts_ro(int d) { return d <= 4 ? 4 : (d <= 16 ? 2 : 1); }
-  PtsGeo pts_geo(bool rows) const {
-    const int64_t n_own = rows ? n : m, n_oth = rows ? m : n;
-    PtsGeo g;
-    g.B = (n_own + (int64_t)kThreads * pts_ro(d) - 1) / ((int64_t)kThreads * pts_ro(d));
-    int64_t S = (2 * (int64_t)h->sms + g.B - 1) / g.B;
-    S = std::max<int64_t>(1, std::min<int64_t>(S, (n_oth + 31) / 32));
-    g.chunk = ((n_oth + S - 1) / S + 31) / 32 * 32;
-    g.S = (n_oth + g.chunk - 1) / g.chunk;
-    return g;
-  }
+  // ---- point-cloud geometry (pts_geo_of / tc_geo_of above the class) ----
+  PtsGeo pts_geo(bool rows) const { return pts_geo_of(h, rows ? n : m, rows ? m : n, d); }
   // ---- tensor-core point path (mixed precision, d >= tc::kMinD) ----
   bool tc_on = false;
   tc::TcArgs targs{};
@@ -240,33 +157,7 @@ struct Solver {
     const char* e = std::getenv("EOT_TC");
     return !(e && e[0] == '0');
   }
-  struct TcGeo {
-    int64_t B, S, chunk;
-  };
-  // own blocks of 128 points x S chunks of the other side (multiples of 48),
-  // S chosen so that B S fills whole waves of one-CTA-per-SM blocks
-  TcGeo tc_geo(bool rows) const {
-    const int64_t n_own = rows ? n : m, n_oth = rows ? m : n;
-    TcGeo g;
-    g.B = (n_own + tc::kM - 1) / tc::kM;
-    double best = -1.0;
-    g.S = 1;
-    g.chunk = (n_oth + tc::kN - 1) / tc::kN * tc::kN;
-    for (int64_t S = 1; S <= 128; ++S) {
-      const int64_t chunk = ((n_oth + S - 1) / S + tc::kN - 1) / tc::kN * tc::kN;
-      const int64_t Sr = (n_oth + chunk - 1) / chunk;
-      if (Sr != S) continue;
-      if (S > 1 && chunk < 2 * tc::kN) break;
-      const int64_t ctas = g.B * S, waves = (ctas + h->sms - 1) / h->sms;
-      const double eff = (double)ctas / (double)(waves * h->sms) - 0.002 * (double)S;  // prefer fewer chunks
-      if (eff > best) {
-        best = eff;
-        g.S = S;
-        g.chunk = chunk;
-      }
-    }
-    return g;
-  }
+  TcGeo tc_geo(bool rows) const { return tc_geo_of(h, rows ? n : m, rows ? m : n); }
   template <int NR, bool LSE, int SQM, bool ROWS, class Epi>
   static void tc_attr() {
     static bool done = false;
@@ -277,16 +168,7 @@ struct Solver {
   }
   void setup_tc() {
     const int64_t npX = tc::pad_rows(n), npY = tc::pad_rows(m);
-    auto side_bytes = [](int64_t np) { return (size_t)np * (tc::kSlices * 64 * 2 + 3 * 4) + 1024; };
-    const size_t need = side_bytes(npX) + side_bytes(npY);
-    if (need > h->tc_bytes) {
-      EOT_CUDA(cudaStreamSynchronize(st));
-      if (h->tc_mem) cudaFree(h->tc_mem);
-      h->tc_mem = nullptr;
-      h->tc_bytes = 0;
-      EOT_CUDA(cudaMalloc(&h->tc_mem, need));
-      h->tc_bytes = need;
-    }
+    ensure_tc_mem(h, n, m, st);
     unsigned char* b = (unsigned char*)h->tc_mem;
     auto carve = [&](tc::Side& sd, int64_t np, const float* P, int64_t len) {
       __nv_bfloat16* sl = (__nv_bfloat16*)b;
@@ -410,7 +292,6 @@ struct Solver {
     a.d = d;
     a.sC = sC;
     a.chunk = 0;
-    a.err = h->status;
     return a;
   }
 
@@ -423,43 +304,48 @@ struct Solver {
   }
 
   std::string ctx;  // where the solver is, for error messages
-  const bool trace = std::getenv("EOT_TRACE") != nullptr;
 
   // Read every device scalar and the status word (synchronises the stream).
-  // Lost CG curvature (kStatCurv) is handled by the caller, not thrown.
-  // Status bits in `tolerated` are left for the caller to inspect (status_bits()).
-  const double* read(int tolerated = 0) {
-    EOT_CUDA(cudaMemcpyAsync(h->h_sc, h->sc, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, st));
+  const double* read() {
+    EOT_CUDA(cudaMemcpyAsync(h->h_sc, h->sc, SC_TOTAL * sizeof(double), cudaMemcpyDeviceToHost, st));
     EOT_CUDA(cudaMemcpyAsync(h->h_status, h->status, sizeof(int), cudaMemcpyDeviceToHost, st));
     EOT_CUDA(cudaStreamSynchronize(st));
-    const int s = *h->h_status & ~tolerated;
+    const int s = *h->h_status;
     if (s & kStatNonfinite) throw EotError{EOT_ERR_NONFINITE, "non-finite potential or marginal" + ctx};
     if (s & kStatCgNan) throw EotError{EOT_ERR_NONFINITE, "non-finite CG residual" + ctx};
     if (s & kStatRange) throw EotError{EOT_ERR_RANGE, "|potential| >= 2^19 (mixed-precision split)" + ctx};
-    if (s & kStatTimeout) throw EotError{EOT_ERR_CUDA, "a bounded device wait ran out" + ctx};
+    if (s & kStatTimeout) throw EotError{EOT_ERR_DEVICE_TIMEOUT, "a bounded device wait ran out" + ctx};
     return h->h_sc;
   }
-  int status_bits() const { return *h->h_status; }
-  void clear_status() { EOT_CUDA(cudaMemsetAsync(h->status, 0, sizeof(int), st)); }
 
   // ---------------- O(n) helpers ----------------
+  // Split A = x + alpha y - z (alpha_dev: read alpha on the device instead).
   void split_rows(const double* x, const double* y, double alpha, const double* z, double* l,
-                  T* ew, double* fac, const double* fshift) {
-    launch_k(split_kernel<T>, dim3(vg_n), dim3(kThreads), st, n, x, y, alpha, z, plain ? 1 : 0, Ah(), l, ew, fac,
-                                               fshift, h->status);
+                  T* ew, double* fac, const double* fshift, const double* alpha_dev = nullptr) {
+    if (alpha_dev)
+      launch_k(split_dev_kernel<T>, dim3(vg_n), dim3(kOnThreads), st, n, x, y, alpha_dev, z, plain ? 1 : 0, Ah(), l,
+               ew, fac, fshift, h->status);
+    else
+      launch_k(split_kernel<T>, dim3(vg_n), dim3(kOnThreads), st, n, x, y, alpha, z, plain ? 1 : 0, Ah(), l, ew, fac,
+               fshift, h->status);
     EOT_LAUNCH_CHECK();
     h->launches++;
   }
   void split_cols(const double* x, const double* y, double alpha, const double* z, double* l,
-                  T* ew, double* fac, const double* fshift) {
-    launch_k(split_kernel<T>, dim3(vg_m), dim3(kThreads), st, m, x, y, alpha, z, plain ? 1 : 0, Bh(), l, ew, fac,
-                                               fshift, h->status);
+                  T* ew, double* fac, const double* fshift, const double* alpha_dev = nullptr) {
+    if (alpha_dev)
+      launch_k(split_dev_kernel<T>, dim3(vg_m), dim3(kOnThreads), st, m, x, y, alpha_dev, z, plain ? 1 : 0, Bh(), l,
+               ew, fac, fshift, h->status);
+    else
+      launch_k(split_kernel<T>, dim3(vg_m), dim3(kOnThreads), st, m, x, y, alpha, z, plain ? 1 : 0, Bh(), l, ew, fac,
+               fshift, h->status);
     EOT_LAUNCH_CHECK();
     h->launches++;
   }
+  // y = b y + a (*a_dev) x + c z + d w
   void axpy(int64_t len, double* y, double b, const double* x, double a, const double* z = nullptr,
-            double c = 0.0, const double* w = nullptr, double d = 0.0) {
-    launch_k(axpy4_kernel, dim3(vec_grid(len)), dim3(kThreads), st, len, y, b, x, a, z, c, w, d);
+            double c = 0.0, const double* w = nullptr, double d = 0.0, const double* a_dev = nullptr) {
+    launch_k(axpy4_kernel, dim3(on_grid(len, h->sms, h->dot_slots)), dim3(kOnThreads), st, len, y, b, x, a, a_dev, z, c, w, d);
     EOT_LAUNCH_CHECK();
     h->launches++;
   }
@@ -502,7 +388,6 @@ struct Solver {
   template <int NR, bool LSE, int SQM, class Epi>
   void launch_row(cudaStream_t s, const SweepArgs<T>& a, const Epi& e) {
     if (points) launch_pts<NR, LSE, SQM, true>(s, a, e);
-    else if (launch_row_bulk<NR, LSE, SQM>(s, a, e)) return;
     else if (V == VEC) launch_k(row_sweep_kernel<T, VEC, NR, LSE, SQM, Epi>, dim3(rg), dim3(kThreads), s, a, e);
     else launch_k(row_sweep_kernel<T, 1, NR, LSE, SQM, Epi>, dim3(rg), dim3(kThreads), s, a, e);
   }
@@ -512,9 +397,6 @@ struct Solver {
       if constexpr (NR == 0) launch_pts<NC, LSE, 0, false>(s, a, e);
       else throw EotError{EOT_ERR_UNSUPPORTED, "fused two-sided sweep needs a dense cost"};
       return;
-    }
-    if constexpr (NR == 0) {
-      if (launch_col_bulk<NC, LSE>(s, a, e)) return;
     }
     const dim3 grid((unsigned)geo.S, (unsigned)geo.R);
     if (V == VEC) launch_k(col_sweep_kernel<T, VEC, NC, LSE, NR, Epi>, grid, dim3(kThreads), s, a, e);
@@ -584,31 +466,261 @@ struct Solver {
     row<1, true, 0>(a, e);
   }
 
-  // Column LSE at (u + alpha du, v + alpha dv): B = v + alpha dv - cshift.
-  // mode 0: out = cshift + LSE (log c(P)); mode 1: out -= LSE (column fix).
+  // Column LSE at (u + alpha du, v + alpha dv): B = v + alpha dv - cshift
+  // (alpha_dev: alpha read on the device). mode 0: out = cshift + LSE (log c(P));
+  // mode 1: out -= LSE (column fix).
   void col_lse(const double* u, const double* du, const double* v, const double* dv, double alpha,
-               const double* cshift, double* out, int mode, int slot, double minus) {
-    split_rows(u, du, alpha, nullptr, h->Al, ewr(), nullptr, nullptr);
-    split_cols(v, dv, alpha, cshift, h->Bl, nullptr, nullptr, nullptr);
+               const double* cshift, double* out, int mode, int slot, double minus,
+               const double* alpha_dev = nullptr) {
+    split_rows(u, du, alpha, nullptr, h->Al, ewr(), nullptr, nullptr, alpha_dev);
+    split_cols(v, dv, alpha, cshift, h->Bl, nullptr, nullptr, nullptr, alpha_dev);
     SweepArgs<T> a = args();
     a.wr[0] = ewr();
     ColLseEpi e{h->Bl, mode == 0 ? cshift : nullptr, out, mode, h->sc, slot, minus};
     col<1, true, 0>(a, e);
   }
 
-  // ---------------- Alg. 2: NewtonSolve ----------------
-  // At (u, v) with log r(P) and the row maxima from the last row LSE. Targets r~.
-  // Leaves d_u in h->du and d_v = -P_c d_u in h->dv; returns the rho of the last CG
-  // solve (or rho0 when no CG solve ran). Also leaves r(P), c(P) in h->rP, h->cP.
-  double newton(const double* u, const double* v, const double* rt, double gl1, double eta,
-                double rho0, int max_cg, CgMode mode, bool* ran_cg) {
+  // ---------------- device-controlled programs ----------------
+  // A program launches kernels on `st` and opens loops and branches with
+  // loop_while / branch_if on a flag that a control kernel (control.cuh) sets.
+  // Captured (the default), a program is one CUDA graph whose loops and branches
+  // are conditional nodes (nested up to four deep), launched once per stage.
+  // EOT_GRAPH=0 runs the same kernels in the same order directly, the host
+  // reading each flag: per-kernel profilers do not see the kernels of graphs
+  // with conditional nodes.
+  Ctl ctl{};
+  bool capturing = false;
+  int depth = 0;
+  int64_t body_kernels[F_COUNT] = {};
+  int64_t bodies_total = 0;
+  bool captured[F_COUNT] = {};
+  int64_t discard = 0;  // sweep counter of program emission (stats come from the device counters)
+  static bool graphs_enabled() {
+    const char* e = std::getenv("EOT_GRAPH");
+    return !(e && e[0] == '0');
+  }
+  static int flag_slot(int f) { return f == F_CG ? (int)SC_ACTIVE : (int)SC_FL0 + f; }
+  cudaGraphConditionalHandle cond(int f) const { return (ctl.graph && ((ctl.mask >> f) & 1u)) ? ctl.hd[f] : 0; }
+  cudaStream_t cap_stream(int k) {
+    if (k >= 8) throw EotError{EOT_ERR_CUDA, "program nesting deeper than 8"};
+    if (!h->cap_streams[k]) EOT_CUDA(cudaStreamCreateWithFlags(&h->cap_streams[k], cudaStreamNonBlocking));
+    return h->cap_streams[k];
+  }
+  bool read_flag(int f) {
+    EOT_CUDA(cudaMemcpyAsync(h->h_sc, h->sc + flag_slot(f), sizeof(double), cudaMemcpyDeviceToHost, st));
+    EOT_CUDA(cudaStreamSynchronize(st));
+    return h->h_sc[0] != 0.0;
+  }
+  template <class F>
+  void cond_node(int f, cudaGraphConditionalNodeType type, F&& body) {
+    if (!capturing) {
+      if (type == cudaGraphCondTypeWhile) {
+        while (read_flag(f)) body();
+      } else if (read_flag(f)) {
+        body();
+      }
+      return;
+    }
+    if (captured[f] || !((ctl.mask >> f) & 1u))
+      throw EotError{EOT_ERR_CUDA, "a program uses a flag twice or one it did not declare"};
+    captured[f] = true;
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    EOT_CUDA(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, nullptr, &nd));
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = ctl.hd[f];
+    np.conditional.type = type;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    EOT_CUDA(cudaGraphAddNode(&node, g, deps, nullptr, nd, &np));
+    EOT_CUDA(cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    cudaStream_t outer = st, inner = cap_stream(depth + 1);
+    EOT_CUDA(cudaStreamBeginCaptureToGraph(inner, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeRelaxed));
+    const int64_t l0 = h->launches, b0 = bodies_total;
+    st = inner;
+    ++depth;
+    body();
+    --depth;
+    st = outer;
+    cudaGraph_t tmp;
+    EOT_CUDA(cudaStreamEndCapture(inner, &tmp));
+    body_kernels[f] = (h->launches - l0) - (bodies_total - b0);
+    bodies_total += body_kernels[f];
+    pdl_skip_next = true;  // the next captured kernel follows the conditional node
+  }
+  template <class F>
+  void loop_while(int f, F&& body) { cond_node(f, cudaGraphCondTypeWhile, body); }
+  template <class F>
+  void branch_if(int f, F&& body) { cond_node(f, cudaGraphCondTypeIf, body); }
+  void ctl_launch(void (*k)(Ctl)) {
+    launch_k(k, dim3(1), dim3(32), st, ctl);
+    EOT_LAUNCH_CHECK();
+    h->launches++;
+  }
+
+  // Runs a program: captured into a cached graph and launched, or directly.
+  // `flags`: the loops and branches the program opens (a conditional handle is
+  // created for each and only for those). Returns the graph (nullptr when run
+  // directly) for the launch accounting.
+  enum { kProgStage = 1, kProgNewton = 2 };
+  static constexpr unsigned kStageFlags = (1u << F_COUNT) - 1u;
+  static constexpr unsigned kNewtonFlags = (1u << F_CGOUT) | (1u << F_CG);
+  template <class F>
+  const ProgGraph* run_program(int tag, unsigned flags, bool direct, F&& emit) {
+    ctl.mask = flags;
+    ctl.sc = h->sc;
+    ctl.status = h->status;
+    ctl.fp64 = sizeof(T) == 8 ? 1 : 0;
+    ctl.floor32 = armijo_floor32(n, m);
     int64_t* saved = sweep_bucket;
-    sweep_bucket = &cnt.sweeps_newton;
+    sweep_bucket = &discard;
+    struct Restore {
+      Solver& s;
+      int64_t* b;
+      ~Restore() { s.sweep_bucket = b; }
+    } restore{*this, saved};
+    if (direct || !graphs_enabled()) {
+      ctl.graph = 0;
+      emit();
+      return nullptr;
+    }
+    uint64_t sbits;
+    std::memcpy(&sbits, &sC, sizeof(sbits));
+    const uintptr_t src = points ? ((uintptr_t)X ^ ((uintptr_t)Y << 1) ^ (uintptr_t)sbits) : (uintptr_t)C;
+    const ProgKey key{tag | ((int)sizeof(T) << 4) | ((plain ? 1 : 0) << 8) | ((points ? 1 : 0) << 9) | (d << 10),
+                      V | ((tc_on ? 1 : 0) << 4) | ((keep_l2 ? 1 : 0) << 5), 0, n, m, ldc, src};
+    auto it = h->graphs.find(key);
+    if (it == h->graphs.end()) {
+      if (h->graphs.size() >= 32) free_graphs(h);
+      ProgGraph pg;
+      EOT_CUDA(cudaGraphCreate(&pg.graph, 0));
+      for (int f = 0; f < F_COUNT; ++f) {
+        ctl.hd[f] = 0;
+        if ((flags >> f) & 1u)
+          EOT_CUDA(cudaGraphConditionalHandleCreate(&ctl.hd[f], pg.graph, 0, cudaGraphCondAssignDefault));
+      }
+      ctl.graph = 1;
+      cudaStream_t outer = st, cs0 = cap_stream(0);
+      const int64_t l0 = h->launches;
+      for (int f = 0; f < F_COUNT; ++f) {
+        body_kernels[f] = 0;
+        captured[f] = false;
+      }
+      bodies_total = 0;
+      EOT_CUDA(cudaStreamBeginCaptureToGraph(cs0, pg.graph, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+      capturing = true;
+      depth = 0;
+      st = cs0;
+      try {
+        emit();
+      } catch (...) {
+        // end every open capture (innermost first) before reporting
+        for (int k = depth; k >= 0; --k) {
+          cudaGraph_t tmp = nullptr;
+          cudaStreamEndCapture(cap_stream(k), &tmp);
+        }
+        capturing = false;
+        st = outer;
+        h->launches = l0;
+        cudaGraphDestroy(pg.graph);
+        pdl_skip_next = false;
+        throw;
+      }
+      cudaGraph_t tmp;
+      EOT_CUDA(cudaStreamEndCapture(cs0, &tmp));
+      capturing = false;
+      st = outer;
+      pdl_skip_next = false;
+      pg.top_kernels = (h->launches - l0) - bodies_total;
+      for (int f = 0; f < F_COUNT; ++f) pg.body_kernels[f] = body_kernels[f];
+      h->launches = l0;
+      for (int f = 0; f < F_COUNT; ++f)
+        if (((flags >> f) & 1u) && !captured[f]) {
+          cudaGraphDestroy(pg.graph);
+          throw EotError{EOT_ERR_CUDA, "a program declared a flag it did not use"};
+        }
+      const cudaError_t ie = cudaGraphInstantiate(&pg.exec, pg.graph, 0);
+      if (ie != cudaSuccess) {
+        cudaGetLastError();
+        cudaGraphDestroy(pg.graph);
+        throw EotError{EOT_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ie)};
+      }
+      it = h->graphs.emplace(key, pg).first;
+    }
+    EOT_CUDA(cudaGraphLaunch(it->second.exec, st));
+    return &it->second;
+  }
+
+  // Device counters of the call (control.cuh), as read after a program.
+  struct Counters {
+    double v[11];
+    explicit Counters(const double* s) {
+      for (int k = 0; k < 11; ++k) v[k] = s[SC_N_CGIT + k];
+    }
+    double operator[](int slot) const { return v[slot - SC_N_CGIT]; }
+  };
+  // Adds the work a program did between two counter reads to the host-side
+  // counters; with a graph also the kernels its launch ran.
+  void account(const ProgGraph* pg, const Counters& a, const Counters& b) {
+    auto dd = [&](int slot) { return (int64_t)(b[slot] - a[slot]); };
+    cnt.cg_iters += dd(SC_N_CGIT);
+    cnt.cg_solves += dd(SC_N_CGSOLVE);
+    cnt.curvature_stops += dd(SC_N_CURV);
+    cnt.newton_steps += dd(SC_N_NEWTON);
+    cnt.ls_trials += dd(SC_N_LSTRIAL);
+    cnt.sk_iters += dd(SC_N_SK);
+    cnt.sweeps_cg += 2 * dd(SC_N_CGIT) + 2 * dd(SC_N_CURV);
+    cnt.sweeps_newton += 3 * dd(SC_N_GO);
+    cnt.sweeps_sk += 2 * dd(SC_N_SK);
+    cnt.sweeps_ls += dd(SC_N_LSTRIAL) + dd(SC_N_LSDEC) + dd(SC_N_UPD);
+    if (pg) {
+      const int trip_slot[F_COUNT] = {SC_N_NLOOP, SC_N_SK, SC_N_GO, SC_N_CGSOLVE, SC_N_CGPASS,
+                                      SC_N_LSDEC, SC_N_LSTRIAL, SC_N_UPD};
+      int64_t k = pg->top_kernels;
+      for (int f = 0; f < F_COUNT; ++f) k += pg->body_kernels[f] * dd(trip_slot[f]);
+      h->launches += k;
+    }
+  }
+  // Throws the error a program recorded (SC_ERR).
+  void check_err(const double* s) {
+    const int e = (int)s[SC_ERR];
+    const std::string where = " (gamma " + std::to_string(gamma_host) + ", Newton step " +
+                              std::to_string((int)s[SC_STEPS]) + ", ||grad g||_1 " + std::to_string(s[SC_GL1]) + ")";
+    switch (e) {
+      case E_NONE: return;
+      case E_MAXNEWTON: throw EotError{EOT_ERR_MAXNEWTON, "TruncatedNewtonProject exceeded max_newton" + where};
+      case E_CHISK: throw EotError{EOT_ERR_MAXNEWTON, "ChiSinkhorn did not converge" + where};
+      case E_CGMAX: throw EotError{EOT_ERR_CG_MAXITER, "linear CG reached max_cg" + where};
+      case E_RHO: throw EotError{EOT_ERR_CG_MAXITER, "rho annealing did not meet the forcing test" + where};
+      case E_LS: throw EotError{EOT_ERR_LINESEARCH, "Armijo backtracking exhausted" + where};
+      default: throw EotError{EOT_ERR_CUDA, "unknown stage error" + where};
+    }
+  }
+  // Zeroes the device counters and sets the caps of a call; rho_last = 0 (the
+  // first NewtonSolve starts at rho = 0, Appx. B).
+  void init_control(int max_newton, int max_ls, int max_cg) {
+    EOT_CUDA(cudaMemsetAsync(h->sc + SC_EPS, 0, (SC_CTL_END - SC_EPS) * sizeof(double), st));
+    set_scalar(SC_MAXNEWTON, (double)max_newton);
+    set_scalar(SC_MAXLS, (double)max_ls);
+    set_scalar(SC_MAXIT, (double)max_cg);
+  }
+
+  // ---------------- Alg. 2: NewtonSolve (program segment) ----------------
+  // At (u, v) with log r(P) and the row maxima from the last row LSE, target rt;
+  // eta in SC_ETA, ||grad g||_1 in SC_GL1, the first rho in SC_RHO. Leaves d_u
+  // (modulo the gauge) in h->du, d_v = -P_c d_u in h->dv, r(P) and c(P) in h->rP,
+  // h->cP, the Armijo slope in SC_SLOPE and the rho of the last CG solve in
+  // SC_RHOSTEP (SC_RAN = 1 if a CG solve ran).
+  void emit_newton(const double* u, const double* v, const double* rt) {
     // factorisation P = rowfac * colfac * E with row shift = running row max
     split_rows(u, nullptr, 0.0, h->rowmax, h->Al, nullptr, h->rowfac, h->rowmax);
     split_cols(v, nullptr, 0.0, nullptr, h->Bl, ewc(), h->colfac, nullptr);
-    launch_k(prep_setup_kernel<T>, dim3(vg_n), dim3(kThreads), st, n, h->logrP, rt, h->rowfac, h->rP, h->du0,
-                                                    xw0(), xw1());
+    launch_k(prep_setup_kernel<T>, dim3(vg_n), dim3(kOnThreads), st, n, h->logrP, rt, h->rowfac, h->rP, h->du0, xw0(),
+             xw1());
     EOT_LAUNCH_CHECK();
     h->launches++;
     {
@@ -626,244 +738,123 @@ struct Solver {
       SetupRowEpi e{h->rowfac, h->rP, h->du0, h->y0, h->diag, h->rPs, h->sc};
       row<3, false, 2>(a, e);
     }
-    const double check0 = read()[SC_CHECK];
-    double rho = rho0, rho_last = rho0;
-    *ran_cg = false;
-    const double* du_final = h->du0;
-    if (!(check0 <= eta * gl1)) {
-      const double tol = 0.25 * eta * gl1;
-      set_scalar(SC_TOL, tol);
-      set_scalar(SC_MAXIT, (double)max_cg);
-      for (int solve = 0;; ++solve) {
-        set_scalar(SC_RHO, rho);
-        run_cg(mode, max_cg, rt);
-        launch_k(cg_check_kernel, dim3(vg_n), dim3(kThreads), st, n, h->res, h->Yx, h->sc, h->dotpart, h->cnt_dot);
-        EOT_LAUNCH_CHECK();
-        h->launches++;
-        const double* s = read();
-        const double it = s[SC_ITERS], rl1 = s[SC_RESL1], chk = s[SC_CHK];
-        if (mode == CgMode::kWhile && pcg_geo().G == 0) {
-          // passes of the WHILE body: the one whose update kernel stopped CG is the last
-          const int64_t passes = std::max<int64_t>(1, ((int64_t)it + kWhileBody - 1) / kWhileBody);
-          h->launches += 4 * kWhileBody * passes;
-        }
-        cnt.cg_iters += (int64_t)it;
-        cnt.sweeps_cg += 2 * (int64_t)it + ((status_bits() & kStatCurv) ? 2 : 0);
-        cnt.cg_solves++;
-        *ran_cg = true;
-        rho_last = rho;
-        if (status_bits() & kStatCurv) {
-          // <p, F_r(rho) p> <= 0 in finite precision: stop CG and keep the iterate,
-          // the truncated-Newton convention; no larger rho can help, so return.
-          cnt.curvature_stops++;
-          clear_status();
-          du_final = it > 0 ? h->x : h->du0;
-          break;
-        }
-        if (rl1 > tol) throw EotError{EOT_ERR_CG_MAXITER, "linear CG reached max_cg" + ctx};
-        du_final = h->x;
-        if (chk <= eta * gl1) break;
-        rho = 1.0 - (1.0 - rho) / 4.0;
-        if (solve > 60) throw EotError{EOT_ERR_CG_MAXITER, "rho annealing did not meet the forcing test" + ctx};
-      }
-    }
-    if (du_final != h->du) copy(h->du, du_final, n);
+    ctl_launch(ctl_cg_begin);
+    loop_while(F_CGOUT, [&] {
+      launch_k(cg_init_kernel<T>, dim3(vg_n), dim3(kOnThreads), st, n, h->rP, h->rPs, rt, h->diag, h->rowfac, h->M,
+               h->x, h->res, h->z, h->p, h->Yx, xw0(), h->sc, h->dotpart, h->cnt_dot, cond(F_CG));
+      EOT_LAUNCH_CHECK();
+      h->launches++;
+      loop_while(F_CG, [&] {
+        for (int b = 0; b < kCgBody; ++b) cg_iteration();
+      });
+      launch_k(cg_check_kernel, dim3(vg_n), dim3(kOnThreads), st, n, h->res, h->Yx, h->sc, h->dotpart, h->cnt_dot);
+      EOT_LAUNCH_CHECK();
+      h->launches++;
+      ctl_launch(ctl_cg_end);
+    });
+    launch_k(select_du_kernel, dim3(vg_n), dim3(kOnThreads), st, n, (const double*)h->x, (const double*)h->du0, h->du,
+             (const double*)h->sc);
     // d_u modulo the gauge, d_v = -(P^T d_u) / c(P) and the Armijo slope <r~ - r(P), d_u>
-    launch_k(gauge_kernel, dim3(vg_n), dim3(kThreads), st, n, (const double*)h->du, (const double*)h->rP,
-             h->sc, h->dotpart, h->cnt_dot);
+    launch_k(gauge_kernel, dim3(vg_n), dim3(kOnThreads), st, n, (const double*)h->du, (const double*)h->rP, h->sc,
+             h->dotpart, h->cnt_dot);
+    launch_k(prep_dv_kernel<T>, dim3(vg_n), dim3(kOnThreads), st, n, h->du, h->rowfac, rt, h->rP, xw0(), h->sc,
+             h->dotpart, h->cnt_dot);
     EOT_LAUNCH_CHECK();
-    h->launches++;
-    launch_k(prep_dv_kernel<T>, dim3(vg_n), dim3(kThreads), st, n, h->du, h->rowfac, rt, h->rP, xw0(), h->sc,
-                                                 h->dotpart, h->cnt_dot);
-    EOT_LAUNCH_CHECK();
-    h->launches++;
+    h->launches += 3;
     {
       SweepArgs<T> a = args();
       a.wr[0] = xw0();
       DvColEpi e{h->colfac, h->cP, h->dv};
       col<1, false, 0>(a, e);
     }
-    sweep_bucket = saved;
-    return rho_last;
   }
 
-  // One CG iteration's four kernels (column half, row half, update, p update).
-  void cg_iteration(cudaStream_t s, cudaGraphConditionalHandle cond) {
+  // One CG iteration's four kernels (column half, row half, update, p update),
+  // each a no-op once the device stop flag SC_ACTIVE is clear.
+  void cg_iteration() {
     {
       SweepArgs<T> a = args();
       a.wr[0] = xw0();
       a.active = h->sc + SC_ACTIVE;
       CgColEpi<T> e{h->colfac, h->cP, zf()};
-      launch_col<1, false, 0>(s, a, e);
+      launch_col<1, false, 0>(st, a, e);
     }
     {
       SweepArgs<T> a = args();
       a.wc[0] = zf();
       a.active = h->sc + SC_ACTIVE;
       CgRowEpi e{h->rowfac, h->rPs, h->p, h->y, h->q, h->sc, h->status};
-      launch_row<1, false, 0>(s, a, e);
+      launch_row<1, false, 0>(st, a, e);
     }
-    launch_k(cg_update_kernel<T>, dim3(vg_n), dim3(kThreads), s, n, h->p, h->q, h->y, h->M, h->x, h->res, h->Yx,
-                                                  h->z, h->sc, h->dotpart, h->cnt_dot, h->status,
-                                                  cond);
-    launch_k(cg_pupdate_kernel<T>, dim3(vg_n), dim3(kThreads), s, n, h->z, h->rowfac, h->p, xw0(), h->sc);
-  }
-
-  CgGraph& get_graph(CgMode mode) {
-    const int B = mode == CgMode::kWhile ? kWhileBody : 6;  // CG iterations per launch / per pass
-    const CgKey key{(int)sizeof(T) + (points ? 100 * d : 0) + (bulk_rows ? 1000 : 0) + (bulk_cols ? 2000 : 0), V,
-                    mode == CgMode::kWhile ? B : 0, n, m,
-                    ldc, points ? (uintptr_t)X ^ ((uintptr_t)Y << 1) : (uintptr_t)C};
-    auto it = h->graphs.find(key);
-    if (it != h->graphs.end()) return it->second;
-    if (h->graphs.size() >= 32) free_graphs(h);
-    CgGraph g;
-    if (!h->cap_stream) EOT_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
-    if (mode == CgMode::kWhile) {
-      EOT_CUDA(cudaGraphCreate(&g.graph, 0));
-      cudaGraphConditionalHandle cond;
-      EOT_CUDA(cudaGraphConditionalHandleCreate(&cond, g.graph, 1, cudaGraphCondAssignDefault));
-      cudaGraphNodeParams np{};
-      np.type = cudaGraphNodeTypeConditional;
-      np.conditional.handle = cond;
-      np.conditional.type = cudaGraphCondTypeWhile;
-      np.conditional.size = 1;
-      cudaGraphNode_t node;
-      EOT_CUDA(cudaGraphAddNode(&node, g.graph, nullptr, nullptr, 0, &np));
-      cudaGraph_t body = np.conditional.phGraph_out[0];
-      EOT_CUDA(cudaStreamBeginCaptureToGraph(h->cap_stream, body, nullptr, nullptr, 0,
-                                             cudaStreamCaptureModeRelaxed));
-      // B iterations per pass: the condition is re-evaluated every B iterations;
-      // iterations past the stop are no-ops (device stop flag)
-      for (int b = 0; b < B; ++b) cg_iteration(h->cap_stream, cond);
-      cudaGraph_t out;
-      EOT_CUDA(cudaStreamEndCapture(h->cap_stream, &out));
-    } else {
-      EOT_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeRelaxed));
-      for (int b = 0; b < B; ++b) cg_iteration(h->cap_stream, 0);
-      EOT_CUDA(cudaStreamEndCapture(h->cap_stream, &g.graph));
-    }
-    EOT_CUDA(cudaGraphInstantiate(&g.exec, g.graph, 0));
-    g.iters_per_launch = B;
-    return h->graphs.emplace(key, g).first->second;
-  }
-
-  // ---- the persistent CG kernel (dense FP32 cost, mixed path) ----
-  // Opt-in (EOT_CG_PERSIST=1): on the 64 x 64 grid workload its four grid
-  // barriers per iteration at two CTAs per SM cost more (57 us per CG iteration)
-  // than the kernel boundaries of the graph path (29 us), so it is not the default.
-  static bool persist_env() {
-    const char* e = std::getenv("EOT_CG_PERSIST");
-    return e && e[0] == '1';
-  }
-  struct PcgGeo {
-    int S = 0, R = 0, rpb = 0, G = 0;
-  };
-  PcgGeo pcg_geo() const {
-    PcgGeo g;
-    if constexpr (sizeof(T) != 4) return g;
-    if (points || plain || V != 4 || m > pcg::kTWp || !persist_env()) return g;
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pcg::cg_persistent_kernel, kThreads, 0) != cudaSuccess)
-      return g;
-    const int gmax = nb * h->sms;
-    const int S = (int)((m + pcg::kSW - 1) / pcg::kSW);
-    if (S > gmax) return g;
-    int R = (int)std::min<int64_t>(gmax / S, (n + kWarps - 1) / kWarps);
-    R = std::max(R, 1);
-    const int rpb = (int)((n + R - 1) / R);
-    R = (int)((n + rpb - 1) / rpb);
-    if ((int64_t)R * m > 2 * h->max_rowblk * h->cap_m) return g;  // FP32-pair partials in colpart
-    g.S = S;
-    g.R = R;
-    g.rpb = rpb;
-    g.G = R * S;
-    return g;
-  }
-  void run_cg_persistent(const PcgGeo& geo) {
-    const size_t need = (size_t)4 * geo.G * sizeof(double) + 256;
-    if (need > h->pcg_bytes) {
-      EOT_CUDA(cudaStreamSynchronize(st));
-      if (h->pcg_mem) cudaFree(h->pcg_mem);
-      h->pcg_mem = nullptr;
-      h->pcg_bytes = 0;
-      EOT_CUDA(cudaMalloc(&h->pcg_mem, need));
-      h->pcg_bytes = need;
-    }
-    unsigned char* b = (unsigned char*)h->pcg_mem;
-    pcg::Args a{};
-    a.C = (const float*)C;
-    a.n = n;
-    a.m = m;
-    a.ldc = ldc;
-    a.Ah = (const float*)h->Ah;
-    a.Bh = (const float*)h->Bh;
-    a.rowfac = h->rowfac;
-    a.colfac = h->colfac;
-    a.cP = h->cP;
-    a.rPs = h->rPs;
-    a.M = h->M;
-    a.x = h->x;
-    a.res = h->res;
-    a.z = h->z;
-    a.q = h->q;
-    a.y = h->y;
-    a.Yx = h->Yx;
-    a.pbuf[0] = h->p;
-    a.pbuf[1] = h->p2;
-    a.xw = (float*)h->xw0;
-    a.zf = (float*)h->zf;
-    a.colpart = reinterpret_cast<float2*>(h->colpart);
-    a.dots = (double*)(b + 256);
-    a.sc = h->sc;
-    a.bar = (unsigned*)b;
-    a.abort = (int*)(b + 64);
-    a.status = h->status;
-    a.R = geo.R;
-    a.S = geo.S;
-    a.rows_per_block = geo.rpb;
-    a.keep_l2 = keep_l2 ? 1 : 0;
-    EOT_CUDA(cudaMemsetAsync(b, 0, 256, st));
-    void* args[] = {&a};
-    EOT_CUDA(cudaLaunchCooperativeKernel((const void*)pcg::cg_persistent_kernel, dim3(geo.G), dim3(kThreads), args,
-                                         0, st));
-    h->launches++;
-  }
-
-  // Runs PCG from x = 0 on F_r(rho) until the device stop flag clears.
-  void run_cg(CgMode mode, int max_cg, const double* rt) {
-    launch_k(cg_init_kernel<T>, dim3(vg_n), dim3(kThreads), st, n, h->rP, h->rPs, rt, h->diag, h->rowfac, h->M, h->x,
-                                                 h->res, h->z, h->p, h->Yx, xw0(), h->sc,
-                                                 h->dotpart, h->cnt_dot);
+    launch_k(cg_update_kernel<T>, dim3(vg_n), dim3(kOnThreads), st, n, h->p, h->q, h->y, h->M, h->x, h->res, h->Yx,
+             h->z, h->sc, h->dotpart, h->cnt_dot, h->status, cond(F_CG));
+    launch_k(cg_pupdate_kernel<T>, dim3(vg_n), dim3(kOnThreads), st, n, h->z, h->rowfac, h->p, xw0(), h->sc);
     EOT_LAUNCH_CHECK();
-    h->launches++;
-    {
-      const PcgGeo geo = pcg_geo();
-      if (geo.G > 0) {
-        run_cg_persistent(geo);
-        return;
-      }
-    }
-    if (mode == CgMode::kHost) {
-      for (int it = 0; it < max_cg; it += 4) {
-        for (int b = 0; b < 4; ++b) cg_iteration(st, 0);
-        EOT_LAUNCH_CHECK();
-        h->launches += 16;
-        if (read()[SC_ACTIVE] == 0.0) break;
-      }
-      return;
-    }
-    CgGraph& g = get_graph(mode);
-    if (mode == CgMode::kWhile) {
-      EOT_CUDA(cudaGraphLaunch(g.exec, st));  // its kernels are counted once the iterations are known
-      return;
-    }
-    const int maxl = (max_cg + g.iters_per_launch - 1) / g.iters_per_launch + 1;
-    for (int l = 0; l < maxl; ++l) {
-      EOT_CUDA(cudaGraphLaunch(g.exec, st));
-      h->launches += 4 * g.iters_per_launch;
-      if (read()[SC_ACTIVE] == 0.0) break;
-    }
+    h->launches += 4;
+  }
+
+  // ---------------- Alg. 4: TruncatedNewtonProject (one stage program) ----------------
+  // On the working potentials (h->U, h->V), targets (rt, ct) = the smoothed
+  // marginals with their logs, tolerance SC_EPS: the opening column fix and row
+  // LSE, then while ||grad g||_1 > eps: ChiSinkhorn (Alg. 3) while chi^2 >
+  // eps^(2/5), NewtonSolve (Alg. 2), d_v, the backtracking line search on the
+  // simplified Armijo test (relative to its value at alpha = 0, reading R27),
+  // the update with its column fix and row LSE; then the closing row step.
+  void emit_stage() {
+    double* u = h->U;
+    double* v = h->V;
+    const double* rt = h->rt;
+    const double* logrt = h->logrt;
+    const double* logct = h->logct;
+    col_lse(u, nullptr, v, nullptr, 0.0, logct, v, 1, SC_AUX0, 0.0);
+    row_lse(u, v, logrt, h->logrP, h->rowmax, rt);
+    ctl_launch(ctl_stage_init);
+    loop_while(F_NEWTON, [&] {
+      ctl_launch(ctl_step_a);
+      loop_while(F_SK, [&] {
+        axpy(n, u, 1.0, logrt, 1.0, h->logrP, -1.0);  // u <- u + log r~ - log r(P)
+        col_lse(u, nullptr, v, nullptr, 0.0, logct, v, 1, SC_AUX0, 0.0);
+        row_lse(u, v, logrt, h->logrP, h->rowmax, rt);
+        ctl_launch(ctl_sk);
+      });
+      ctl_launch(ctl_step_b);
+      branch_if(F_GO, [&] {
+        emit_newton(u, v, rt);
+        ctl_launch(ctl_ls_begin);
+        branch_if(F_DEC, [&] {
+          col_lse(u, h->du, v, h->dv, 0.0, logct, h->logcP, 0, SC_LHS, 1.0);
+          ctl_launch(ctl_lhs0);
+        });
+        loop_while(F_LS, [&] {
+          col_lse(u, h->du, v, h->dv, 0.0, logct, h->logcP, 0, SC_LHS, 1.0, h->sc + SC_ALS);
+          ctl_launch(ctl_trial);
+        });
+        branch_if(F_UPD, [&] {
+          // u += a d_u; v += a d_v + log c~ - log c(P(a)) (the column fix), then log r(P)
+          axpy(n, u, 1.0, h->du, 1.0, nullptr, 0.0, nullptr, 0.0, h->sc + SC_ALS);
+          axpy(m, v, 1.0, h->dv, 1.0, logct, 1.0, h->logcP, -1.0, h->sc + SC_ALS);
+          row_lse(u, v, logrt, h->logrP, h->rowmax, rt);
+          ctl_launch(ctl_step_end);
+        });
+      });
+    });
+    axpy(n, u, 1.0, logrt, 1.0, h->logrP, -1.0);  // closing row step: u <- u + log r~ - log r(P)
+  }
+
+  // Runs one stage program at the current gamma with tolerance eps; returns
+  // delta_min (+inf without Newton steps) and the last ||grad g||_1.
+  void project(double eps, double* delta_min, double* gl1_out) {
+    set_scalar(SC_EPS, eps);
+    set_scalar(SC_EPSCHI, std::pow(eps, 0.4));
+    const Counters c0(read());
+    cnt.sweeps_stage += 2;
+    const ProgGraph* pg = run_program(kProgStage, kStageFlags, false, [&] { emit_stage(); });
+    const double* s = read();
+    const Counters c1(s);
+    account(pg, c0, c1);
+    check_err(s);
+    *delta_min = s[SC_DMIN];
+    *gl1_out = s[SC_GL1];
   }
 
   // ---------------- MDOT-Sinkhorn projection (Sec. 4 comparison) ----------------
@@ -872,7 +863,9 @@ struct Solver {
   // iterations; sk_step_kernel makes the iterations past the stopping point
   // no-ops, so the result and the count are those of a per-iteration test.
   static constexpr int kSkCheck = 8;
-  bool project_sinkhorn(double* u, double* v, double eps, const eot_params& prm, double* gl1_out) {
+  bool project_sinkhorn(double eps, const eot_params& prm, double* gl1_out) {
+    double* u = h->U;
+    double* v = h->V;
     double* rt = h->rt;
     double* logrt = h->logrt;
     double* logct = h->logct;
@@ -892,7 +885,7 @@ struct Solver {
       }
       const int64_t k = std::min<int64_t>(kSkCheck, max_it - it);
       for (int64_t j = 0; j < k; ++j) {
-        launch_k(sk_step_kernel, dim3(vg_n), dim3(kThreads), st, n, u, (const double*)logrt,
+        launch_k(sk_step_kernel, dim3(vg_n), dim3(kOnThreads), st, n, u, (const double*)logrt,
                  (const double*)h->logrP, h->sc, eps);
         EOT_LAUNCH_CHECK();
         h->launches++;
@@ -904,118 +897,9 @@ struct Solver {
       it = (int64_t)s[SC_AUX1];
     }
     cnt.sk_iters += it;
-    if (trace)
-      std::fprintf(stderr, "[eot] sinkhorn stage gamma %.6g iters %lld grad %.4e eps %.4e\n", gamma_host,
-                   (long long)it, gl1, eps);
     axpy(n, u, 1.0, logrt, 1.0, h->logrP, -1.0);
     *gl1_out = gl1;
-    return ok;
-  }
-
-  // ---------------- Alg. 4: TruncatedNewtonProject ----------------
-  // (u, v) in/out; targets (rt, ct) = smoothed marginals with logs; tolerance eps.
-  // Returns false if the Newton budget ran out. delta_min is reported.
-  bool project(double* u, double* v, double eps, const eot_params& prm, int max_cg, CgMode mode,
-               double* delta_min, double* gl1_out) {
-    double* rt = h->rt;
-    double* logrt = h->logrt;
-    double* logct = h->logct;
-    sweep_bucket = &cnt.sweeps_stage;
-    // opening column fix: v <- log c~ - LSE_c(u 1^T - gamma C)
-    col_lse(u, nullptr, v, nullptr, 0.0, logct, v, 1, SC_AUX0, 0.0);
-    // then log r(P) <- u + LSE_r(1 v^T - gamma C)
-    row_lse(u, v, logrt, h->logrP, h->rowmax, rt);
-    const double* s = read();
-    double gl1 = s[SC_GL1], chi2 = s[SC_CHI2];
-    if (trace) std::fprintf(stderr, "[eot] stage start gamma %.6g grad %.4e chi2 %.4e eps %.4e\n", gamma_host, gl1, chi2, eps);
-    *delta_min = INFINITY;
-    int steps = 0;
-    bool ok = true;
-    const double eps_chi = std::pow(eps, 0.4);
-    while (gl1 > eps) {
-      ctx = " (gamma " + std::to_string(gamma_host) + ", Newton step " + std::to_string(steps) +
-            ", ||grad g||_1 " + std::to_string(gl1) + ", eps " + std::to_string(eps) + ")";
-      if (steps >= prm.max_newton) {
-        ok = false;
-        break;
-      }
-      // Alg. 3 (ChiSinkhorn): while chi^2(r~ | r(P)) > eps^(2/5)
-      sweep_bucket = &cnt.sweeps_sk;
-      int sk = 0;
-      while (chi2 > eps_chi) {
-        axpy(n, u, 1.0, logrt, 1.0, h->logrP, -1.0);  // u <- u + log r~ - log r(P)
-        col_lse(u, nullptr, v, nullptr, 0.0, logct, v, 1, SC_AUX0, 0.0);
-        row_lse(u, v, logrt, h->logrP, h->rowmax, rt);
-        s = read();
-        gl1 = s[SC_GL1];
-        chi2 = s[SC_CHI2];
-        cnt.sk_iters++;
-        if (++sk > 2000) throw EotError{EOT_ERR_MAXNEWTON, "ChiSinkhorn did not converge"};
-      }
-      if (gl1 <= eps) break;
-      // forcing parameter
-      const double eta = std::fmax(gl1, 0.8 * eps / gl1);
-      // NewtonSolve and d_v = -P_c d_u
-      bool ran;
-      const double rho0 = std::fmax(0.0, 1.0 - 4.0 * (1.0 - cnt.rho_last));
-      const double rho = newton(u, v, rt, gl1, eta, rho0, max_cg, mode, &ran);
-      if (ran) cnt.rho_last = rho;
-      cnt.newton_steps++;
-      // backtracking on the simplified Armijo test, whose left side
-      // (sum P(alpha) - 1) is taken relative to its computed value at alpha = 0
-      // (0 in exact arithmetic, since c(P) = c~): this removes the rounding
-      // offset of the mass, which near the final tolerance can exceed the
-      // sufficient decrease itself
-      sweep_bucket = &cnt.sweeps_ls;
-      // With FP32 plan entries sum P(alpha) carries a rounding floor (about
-      // 2^-22 / sqrt(max(n, m))); when the whole decrease the test asks for at
-      // alpha = 1 is below it
-      // the test cannot decide, and the unit step (accepted near the solution,
-      // Sec. 3) is taken. Trials outside the split range are still rejected.
-      const bool decidable = sizeof(T) == 8 || 0.99 * read()[SC_SLOPE] >= armijo_floor32(n, m);
-      double lhs0 = 0.0;
-      if (decidable) {
-        col_lse(u, h->du, v, h->dv, 0.0, logct, h->logcP, 0, SC_LHS, 1.0);
-        lhs0 = read()[SC_LHS];
-      }
-      double alpha = 1.0;
-      int trials = 0;
-      for (;;) {
-        col_lse(u, h->du, v, h->dv, alpha, logct, h->logcP, 0, SC_LHS, 1.0);
-        // A trial point outside the split range (|u + a d_u| >= 2^19) has a plan
-        // whose mass overflows, so it fails the Armijo test: reject it.
-        s = read(kStatRange);
-        const bool out_of_range = (status_bits() & kStatRange) != 0;
-        if (out_of_range) clear_status();
-        cnt.ls_trials++;
-        if (trace)
-          std::fprintf(stderr, "[eot]   trial alpha %.4g lhs %.6e lhs0 %.6e slope %.6e range %d\n", alpha,
-                       s[SC_LHS], lhs0, s[SC_SLOPE], out_of_range ? 1 : 0);
-        if (!out_of_range && (!decidable || s[SC_LHS] - lhs0 <= 0.99 * alpha * s[SC_SLOPE])) break;
-        if (++trials > prm.max_ls) throw EotError{EOT_ERR_LINESEARCH, "Armijo backtracking exhausted"};
-        alpha *= 0.5;
-      }
-      // update and column fix: u += a d_u; v += a d_v + log c~ - log c(P(a))
-      axpy(n, u, 1.0, h->du, alpha);
-      axpy(m, v, 1.0, h->dv, alpha, logct, 1.0, h->logcP, -1.0);
-      // log r(P) at the new point
-      sweep_bucket = &cnt.sweeps_ls;
-      row_lse(u, v, logrt, h->logrP, h->rowmax, rt);
-      s = read();
-      const double new_gl1 = s[SC_GL1];
-      chi2 = s[SC_CHI2];
-      const double delta = (gl1 - new_gl1) / ((1.0 - eta) * gl1);
-      if (trace)
-        std::fprintf(stderr, "[eot] gamma %.6g step %d grad %.3e -> %.3e eta %.3e alpha %.4g rho %.9f cg %lld curv %lld sk %lld decidable %d\n",
-                     gamma_host, steps, gl1, new_gl1, eta, alpha, cnt.rho_last, (long long)cnt.cg_iters,
-                     (long long)cnt.curvature_stops, (long long)cnt.sk_iters, decidable ? 1 : 0);
-      if (delta < *delta_min) *delta_min = delta;
-      gl1 = new_gl1;
-      steps++;
-    }
-    // closing row step: u <- u + log r~ - log r(P)
-    axpy(n, u, 1.0, logrt, 1.0, h->logrP, -1.0);
-    *gl1_out = gl1;
+    sweep_bucket = &cnt.sweeps_other;
     return ok;
   }
 };
@@ -1041,10 +925,14 @@ double run_sweep_bench(eot_handle h, const eot_problem* P, const double* u, cons
                        double gamma, int kind, int iters, void* flush, size_t flush_bytes, cudaStream_t st);
 template <class T>
 void run_backward_dense(eot_handle h, const eot_problem* P, const double* u, const double* v,
-                        double gamma, double scale, float* dC, cudaStream_t st);
+                        double gamma, double scale, const double* scale_dev, float* dC, cudaStream_t st);
 template <class T>
 void run_backward_points(eot_handle h, const eot_problem* P, const double* u, const double* v,
-                         double gamma, double scale, float* dX, float* dY, cudaStream_t st);
+                         double gamma, double scale, const double* scale_dev, float* dX, float* dY,
+                         cudaStream_t st);
+template <class T>
+void run_value(eot_handle h, const eot_problem* P, const double* u, const double* v, double gamma,
+               double* value_out, cudaStream_t st);
 template <class T>
 void run_round(eot_handle h, const eot_problem* P, const double* u, const double* v, double gamma,
                double* u_out, double* v_out, double* a_out, double* b_out, double* cost_out, double* corr_out,

@@ -3,20 +3,22 @@
 
 namespace eot {
 template void run_marginals<float>(eot_handle, const eot_problem*, const double*, const double*, double,
-                                   double*, double*, double*, double*, double*, cudaStream_t);
+                                double*, double*, double*, double*, double*, cudaStream_t);
+template void run_value<float>(eot_handle, const eot_problem*, const double*, const double*, double, double*,
+                            cudaStream_t);
 template void run_hvp<float>(eot_handle, const eot_problem*, const double*, const double*, double, double,
-                             const double*, const double*, double*, double*, double*, double*, cudaStream_t);
+                          const double*, const double*, double*, double*, double*, double*, cudaStream_t);
 template void run_newton<float>(eot_handle, const eot_problem*, const double*, const double*, double,
-                                const double*, double, double, int, double*, double*, double*, int*,
-                                cudaStream_t);
+                             const double*, double, double, int, double*, double*, double*, int*,
+                             cudaStream_t);
 template void run_solve<float>(eot_handle, const eot_problem*, const eot_params*, double*, double*,
-                               eot_stats*, cudaStream_t);
+                            eot_stats*, cudaStream_t);
 template void run_backward_dense<float>(eot_handle, const eot_problem*, const double*, const double*,
-                                        double, double, float*, cudaStream_t);
+                                     double, double, const double*, float*, cudaStream_t);
 template double run_sweep_bench<float>(eot_handle, const eot_problem*, const double*, const double*,
-                                      double, int, int, void*, size_t, cudaStream_t);
+                                    double, int, int, void*, size_t, cudaStream_t);
 template void run_backward_points<float>(eot_handle, const eot_problem*, const double*, const double*,
-                                           double, double, float*, float*, cudaStream_t);
+                                      double, double, const double*, float*, float*, cudaStream_t);
 template void run_round<float>(eot_handle, const eot_problem*, const double*, const double*, double, double*,
                             double*, double*, double*, double*, double*, cudaStream_t);
 }  // namespace eot

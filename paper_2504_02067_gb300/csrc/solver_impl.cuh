@@ -32,17 +32,36 @@ void run_marginals(eot_handle h, const eot_problem* P, const double* u, const do
   S.row_lse(u, v, nullptr, lr, nullptr, nullptr, SC_MASS, SC_AUX1);
   S.col_lse(u, nullptr, v, nullptr, 0.0, nullptr, lc, 0, SC_AUX0, 0.0);
   if (r_out) {
-    launch_k(exp_kernel, dim3(S.vg_n), dim3(kThreads), st, P->n, lr, r_out);
+    launch_k(exp_kernel, dim3(S.vg_n), dim3(kOnThreads), st, P->n, lr, r_out);
     h->launches++;
   }
   if (c_out) {
-    launch_k(exp_kernel, dim3(S.vg_m), dim3(kThreads), st, P->m, lc, c_out);
+    launch_k(exp_kernel, dim3(S.vg_m), dim3(kOnThreads), st, P->m, lc, c_out);
     h->launches++;
   }
   EOT_LAUNCH_CHECK();
   if (total_out)
     EOT_CUDA(cudaMemcpyAsync(total_out, h->sc + SC_MASS, sizeof(double), cudaMemcpyDeviceToDevice, st));
   S.read();
+}
+
+// The dual value (<r, u> + <c, v> - sum P + 1) / gamma (Eq. sinkhorn-dual) into a
+// device scalar: one row LSE sweep for sum P, two dot products, no host readback.
+template <class T>
+void run_value(eot_handle h, const eot_problem* P, const double* u, const double* v, double gamma,
+               double* value_out, cudaStream_t st) {
+  Solver<T> S(h, P, st);
+  const double g = round_gamma<T>(gamma);
+  S.set_scalar(SC_GAMMA, g);
+  S.row_lse(u, v, nullptr, nullptr, nullptr, nullptr, SC_MASS, SC_AUX1);
+  launch_k(dot_kernel, dim3(S.vg_n), dim3(kOnThreads), st, P->n, P->r, u, h->sc, (int)SC_AUX0, h->dotpart,
+           h->cnt_dot);
+  launch_k(dot_kernel, dim3(S.vg_m), dim3(kOnThreads), st, P->m, P->c, v, h->sc, (int)SC_CHK, h->dotpart,
+           h->cnt_dot);
+  launch_k(dual_value_kernel, dim3(1), dim3(1), st, (const double*)h->sc, (int)SC_AUX0, (int)SC_CHK,
+           (int)SC_MASS, g, value_out);
+  EOT_LAUNCH_CHECK();
+  h->launches += 3;
 }
 
 template <class T>
@@ -56,10 +75,10 @@ void run_hvp(eot_handle h, const eot_problem* P, const double* u, const double* 
   S.row_lse(u, v, nullptr, h->logrP, h->rowmax, nullptr, SC_AUX0, SC_AUX1);
   S.split_rows(u, nullptr, 0.0, h->rowmax, h->Al, nullptr, h->rowfac, h->rowmax);
   S.split_cols(v, nullptr, 0.0, nullptr, h->Bl, nullptr, h->colfac, nullptr);
-  launch_k(weight_kernel<T>, dim3(S.vg_n), dim3(kThreads), st, P->n, h->rowfac, nullptr, S.xw0());
-  launch_k(weight_kernel<T>, dim3(S.vg_n), dim3(kThreads), st, P->n, h->rowfac, du, S.xw1());
-  launch_k(weight_kernel<T>, dim3(S.vg_m), dim3(kThreads), st, P->m, h->colfac, nullptr, S.zf());
-  launch_k(weight_kernel<T>, dim3(S.vg_m), dim3(kThreads), st, P->m, h->colfac, dv, S.wsq());
+  launch_k(weight_kernel<T>, dim3(S.vg_n), dim3(kOnThreads), st, P->n, h->rowfac, nullptr, S.xw0());
+  launch_k(weight_kernel<T>, dim3(S.vg_n), dim3(kOnThreads), st, P->n, h->rowfac, du, S.xw1());
+  launch_k(weight_kernel<T>, dim3(S.vg_m), dim3(kOnThreads), st, P->m, h->colfac, nullptr, S.zf());
+  launch_k(weight_kernel<T>, dim3(S.vg_m), dim3(kOnThreads), st, P->m, h->colfac, dv, S.wsq());
   EOT_LAUNCH_CHECK();
   h->launches += 4;
   if (S.points) {
@@ -73,9 +92,9 @@ void run_hvp(eot_handle h, const eot_problem* P, const double* u, const double* 
     b.wr[0] = S.xw0();
     b.wr[1] = S.xw1();
     S.template col<2, false, 0>(b, ColSumEpi{h->colfac, h->cP, h->mt1});
-    launch_k(hvp_assemble_kernel, dim3(S.vg_n), dim3(kThreads), st, P->n, (const double*)h->rP,
+    launch_k(hvp_assemble_kernel, dim3(S.vg_n), dim3(kOnThreads), st, P->n, (const double*)h->rP,
              (const double*)h->y, du, s, ou, r_out);
-    launch_k(hvp_assemble_kernel, dim3(S.vg_m), dim3(kThreads), st, P->m, (const double*)h->cP,
+    launch_k(hvp_assemble_kernel, dim3(S.vg_m), dim3(kOnThreads), st, P->m, (const double*)h->cP,
              (const double*)h->mt1, dv, s, ov, c_out);
     h->launches += 2;
     S.read();
@@ -98,12 +117,23 @@ void run_newton(eot_handle h, const eot_problem* P, const double* u, const doubl
                 double* du_out, double* dv_out, double* rho_out, int* iters_out, cudaStream_t st) {
   Solver<T> S(h, P, st);
   EOT_CUDA(cudaMemsetAsync(h->status, 0, sizeof(int), st));
-  S.set_scalar(SC_GAMMA, round_gamma<T>(gamma));
-  S.row_lse(u, v, nullptr, h->logrP, h->rowmax, rtarget);
-  const double gl1 = S.read()[SC_GL1];
   if (max_cg <= 0) max_cg = (int)std::min<int64_t>(4 * P->n, 2000);
-  bool ran = false;
-  const double rho = S.newton(u, v, rtarget, gl1, eta, rho0, max_cg, cg_mode_from_env(), &ran);
+  S.init_control(1, 1, max_cg);
+  S.set_scalar(SC_GAMMA, round_gamma<T>(gamma));
+  // the program runs on the handle's buffers (a captured graph keeps their addresses)
+  S.copy(h->U, u, P->n);
+  S.copy(h->V, v, P->m);
+  S.copy(h->rt, rtarget, P->n);
+  S.row_lse(h->U, h->V, nullptr, h->logrP, h->rowmax, h->rt);
+  S.set_scalar(SC_ETA, eta);
+  S.set_scalar(SC_RHO, rho0);
+  const typename Solver<T>::Counters c0(S.read());
+  const ProgGraph* pg = S.run_program(Solver<T>::kProgNewton, Solver<T>::kNewtonFlags, false,
+                                      [&] { S.emit_newton(h->U, h->V, h->rt); });
+  const double* s = S.read();
+  S.account(pg, c0, typename Solver<T>::Counters(s));
+  S.check_err(s);
+  const double rho = s[SC_RAN] != 0.0 ? s[SC_RHOSTEP] : rho0;
   S.copy(du_out, h->du, P->n);
   if (dv_out) S.copy(dv_out, h->dv, P->m);
   S.read();
@@ -119,8 +149,11 @@ void run_solve(eot_handle h, const eot_problem* P, const eot_params* prm_in, dou
   Solver<T> S(h, P, st);
   const int64_t n = P->n, m = P->m;
   const int max_cg = prm.max_cg > 0 ? prm.max_cg : (int)std::min<int64_t>(4 * n, 2000);
-  const CgMode mode = cg_mode_from_env();
   EOT_CUDA(cudaMemsetAsync(h->status, 0, sizeof(int), st));
+  S.init_control(prm.max_newton, prm.max_ls, max_cg);
+  // Alg. 1 runs on the handle's working potentials (h->U, h->V); u, v receive them at the end
+  double* const U = h->U;
+  double* const V = h->V;
   S.retain_cost();
   struct Release {  // demote the cost's L2 lines on every exit path
     Solver<T>& s;
@@ -133,22 +166,22 @@ void run_solve(eot_handle h, const eot_problem* P, const eot_params* prm_in, dou
   } release_guard{S};
 
   // H(r), H(c) and the masses (Alg. 1's eps_d needs min(H(r), H(c)))
-  launch_k(vec_stats_kernel, dim3(S.vg_n), dim3(kThreads), st, n, P->r, nullptr, 0, h->sc, SC_AUX0, SC_AUX1,
+  launch_k(vec_stats_kernel, dim3(S.vg_n), dim3(kOnThreads), st, n, P->r, nullptr, 0, h->sc, SC_AUX0, SC_AUX1,
                                                  h->dotpart, h->cnt_dot, h->status);
   EOT_LAUNCH_CHECK();
-  EOT_CUDA(cudaMemcpyAsync(h->h_sc + SC_COUNT - 2, h->sc + SC_AUX0, 2 * sizeof(double),
+  EOT_CUDA(cudaMemcpyAsync(h->h_sc + SC_TOTAL - 2, h->sc + SC_AUX0, 2 * sizeof(double),
                            cudaMemcpyDeviceToHost, st));
   EOT_CUDA(cudaStreamSynchronize(st));
-  const double Hr = -h->h_sc[SC_COUNT - 2], mr = h->h_sc[SC_COUNT - 1];
-  launch_k(vec_stats_kernel, dim3(S.vg_m), dim3(kThreads), st, m, P->c, nullptr, 0, h->sc, SC_AUX0, SC_AUX1,
+  const double Hr = -h->h_sc[SC_TOTAL - 2], mr = h->h_sc[SC_TOTAL - 1];
+  launch_k(vec_stats_kernel, dim3(S.vg_m), dim3(kOnThreads), st, m, P->c, nullptr, 0, h->sc, SC_AUX0, SC_AUX1,
                                                  h->dotpart, h->cnt_dot, h->status);
   EOT_LAUNCH_CHECK();
   h->launches += 2;
-  EOT_CUDA(cudaMemcpyAsync(h->h_sc + SC_COUNT - 2, h->sc + SC_AUX0, 2 * sizeof(double),
+  EOT_CUDA(cudaMemcpyAsync(h->h_sc + SC_TOTAL - 2, h->sc + SC_AUX0, 2 * sizeof(double),
                            cudaMemcpyDeviceToHost, st));
   EOT_CUDA(cudaMemcpyAsync(h->h_status, h->status, sizeof(int), cudaMemcpyDeviceToHost, st));
   EOT_CUDA(cudaStreamSynchronize(st));
-  const double Hc = -h->h_sc[SC_COUNT - 2], mc = h->h_sc[SC_COUNT - 1];
+  const double Hc = -h->h_sc[SC_TOTAL - 2], mc = h->h_sc[SC_TOTAL - 1];
   if (*h->h_status != 0 || std::fabs(mr - 1.0) > 1e-6 || std::fabs(mc - 1.0) > 1e-6)
     throw EotError{EOT_ERR_INVALID_ARG, "r and c must be finite, non-negative and sum to 1"};
   const double H = std::min(Hr, Hc);
@@ -162,79 +195,92 @@ void run_solve(eot_handle h, const eot_problem* P, const eot_params* prm_in, dou
   if (n == 1 || m == 1) {
     // one row or one column: U(r, c) is the single plan r c^T and eps_d of Alg. 1
     // (min(H(r), H(c)) / gamma^p) is 0; return its potentials directly
-    launch_k(closed_form_kernel<T>, dim3(std::max(S.vg_n, S.vg_m)), dim3(kThreads), st, n, m, P->r, P->c,
-             gamma_f, S.points ? (const T*)nullptr : S.C, P->ldc, S.X, S.Y, (int)S.d, S.sC, u, v);
+    launch_k(closed_form_kernel<T>, dim3(std::max(S.vg_n, S.vg_m)), dim3(kOnThreads), st, n, m, P->r, P->c,
+             gamma_f, S.points ? (const T*)nullptr : S.C, P->ldc, S.X, S.Y, (int)S.d, S.sC, U, V);
     EOT_LAUNCH_CHECK();
     h->launches++;
     gamma = gamma_f;
     t = 0;
   }
-  for (; t > 0;) {
-    const bool done = gamma == gamma_f;
-    double eps_d = H / std::pow(gamma, prm.p);
-    if (done) eps_d = std::min(eps_d, 2.0 * prm.tol_final / 3.0);
-    launch_k(smooth_kernel, dim3(S.vg_n), dim3(kThreads), st, n, P->r, prm.w_r * eps_d, h->rt, h->logrt);
-    launch_k(smooth_kernel, dim3(S.vg_m), dim3(kThreads), st, m, P->c, w_c * eps_d, h->ct, h->logct);
-    EOT_LAUNCH_CHECK();
-    h->launches += 2;
-    if (t == 1) {
-      S.copy(u, h->logrt, n);
-      S.copy(v, h->logct, m);
-      S.copy(h->nt0, h->logrt, n);
-      S.copy(h->mt0, h->logct, m);
+  try {
+    for (; t > 0;) {
+      const bool done = gamma == gamma_f;
+      double eps_d = H / std::pow(gamma, prm.p);
+      if (done) eps_d = std::min(eps_d, 2.0 * prm.tol_final / 3.0);
+      launch_k(smooth_kernel, dim3(S.vg_n), dim3(kOnThreads), st, n, P->r, prm.w_r * eps_d, h->rt, h->logrt);
+      launch_k(smooth_kernel, dim3(S.vg_m), dim3(kOnThreads), st, m, P->c, w_c * eps_d, h->ct, h->logct);
+      EOT_LAUNCH_CHECK();
+      h->launches += 2;
+      if (t == 1) {
+        S.copy(U, h->logrt, n);
+        S.copy(V, h->logct, m);
+        S.copy(h->nt0, h->logrt, n);
+        S.copy(h->mt0, h->logct, m);
+      }
+      S.set_scalar(SC_GAMMA, gamma);
+      double dmin = INFINITY;
+      const SolveCounters c0 = S.cnt;
+      if (prm.projector == EOT_PROJECT_SINKHORN) {
+        if (!S.project_sinkhorn(eps_d / 2.0, prm, &gl1))
+          throw EotError{EOT_ERR_MAXNEWTON, "Sinkhorn projection exceeded max_sinkhorn"};
+      } else {
+        S.project(eps_d / 2.0, &dmin, &gl1);
+      }
+      // AdjustSchedule (Sec. 3.3); a stage without Newton steps has delta_min = +inf
+      if (dmin > 0.95) q = std::min(2.0, q * q);
+      else if (dmin < 0.8) q = std::sqrt(q);
+      if (stats && stats->stage_records && t - 1 < stats->stage_records_cap) {
+        const SolveCounters& c1 = S.cnt;
+        eot_stage_record& rec = stats->stage_records[t - 1];
+        rec.gamma = gamma;
+        rec.eps = eps_d / 2.0;
+        rec.delta_min = dmin;
+        rec.q_next = q;
+        rec.newton_steps = (int32_t)(c1.newton_steps - c0.newton_steps);
+        rec.cg_iters = (int32_t)(c1.cg_iters - c0.cg_iters);
+        rec.ls_trials = (int32_t)(c1.ls_trials - c0.ls_trials);
+        rec.sinkhorn_iters = (int32_t)(c1.sk_iters - c0.sk_iters);
+        rec.sweeps = (c1.sweeps_cg + c1.sweeps_newton + c1.sweeps_ls + c1.sweeps_sk + c1.sweeps_stage +
+                      c1.sweeps_other) -
+                     (c0.sweeps_cg + c0.sweeps_newton + c0.sweeps_ls + c0.sweeps_sk + c0.sweeps_stage +
+                      c0.sweeps_other);
+      }
+      const double gamma_next = round_gamma<T>(std::min(q * gamma, gamma_f));
+      if (done) break;
+      if (t >= prm.max_stages) throw EotError{EOT_ERR_MAXSTAGES, "gamma_f not reached within max_stages"};
+      // Alg. 1's extrapolated warm start: z <- z + ratio (z - z_prev), z_prev <- z
+      const double ratio = (gamma_next - gamma) / (gamma - gamma_prev);
+      S.copy(h->nt1, U, n);
+      S.axpy(n, U, 1.0 + ratio, h->nt0, -ratio);
+      std::swap(h->nt0, h->nt1);
+      S.copy(h->mt1, V, m);
+      S.axpy(m, V, 1.0 + ratio, h->mt0, -ratio);
+      std::swap(h->mt0, h->mt1);
+      gamma_prev = gamma;
+      gamma = gamma_next;
+      ++t;
     }
-    S.set_scalar(SC_GAMMA, gamma);
-    double dmin = INFINITY;
-    const SolveCounters c0 = S.cnt;
-    if (prm.projector == EOT_PROJECT_SINKHORN) {
-      if (!S.project_sinkhorn(u, v, eps_d / 2.0, prm, &gl1))
-        throw EotError{EOT_ERR_MAXNEWTON, "Sinkhorn projection exceeded max_sinkhorn"};
-    } else if (!S.project(u, v, eps_d / 2.0, prm, max_cg, mode, &dmin, &gl1)) {
-      throw EotError{EOT_ERR_MAXNEWTON, "TruncatedNewtonProject exceeded max_newton"};
+  } catch (const EotError& e) {
+    // a cap or a non-finite value stopped Alg. 1: the caller still gets the last
+    // iterate (the stage in progress), e.g. to measure the error it reached
+    if (e.st != EOT_ERR_CUDA && e.st != EOT_ERR_DEVICE_TIMEOUT) {
+      S.copy(u, U, n);
+      S.copy(v, V, m);
+      cudaStreamSynchronize(st);
     }
-    // AdjustSchedule (Sec. 3.3); a stage without Newton steps has delta_min = +inf
-    if (dmin > 0.95) q = std::min(2.0, q * q);
-    else if (dmin < 0.8) q = std::sqrt(q);
-    if (stats && stats->stage_records && t - 1 < stats->stage_records_cap) {
-      const SolveCounters& c1 = S.cnt;
-      eot_stage_record& rec = stats->stage_records[t - 1];
-      rec.gamma = gamma;
-      rec.eps = eps_d / 2.0;
-      rec.delta_min = dmin;
-      rec.q_next = q;
-      rec.newton_steps = (int32_t)(c1.newton_steps - c0.newton_steps);
-      rec.cg_iters = (int32_t)(c1.cg_iters - c0.cg_iters);
-      rec.ls_trials = (int32_t)(c1.ls_trials - c0.ls_trials);
-      rec.sinkhorn_iters = (int32_t)(c1.sk_iters - c0.sk_iters);
-      rec.sweeps = (c1.sweeps_cg + c1.sweeps_newton + c1.sweeps_ls + c1.sweeps_sk + c1.sweeps_stage +
-                    c1.sweeps_other) -
-                   (c0.sweeps_cg + c0.sweeps_newton + c0.sweeps_ls + c0.sweeps_sk + c0.sweeps_stage +
-                    c0.sweeps_other);
-    }
-    const double gamma_next = round_gamma<T>(std::min(q * gamma, gamma_f));
-    if (done) break;
-    if (t >= prm.max_stages) throw EotError{EOT_ERR_MAXSTAGES, "gamma_f not reached within max_stages"};
-    // Alg. 1's extrapolated warm start: z <- z + ratio (z - z_prev), z_prev <- z
-    const double ratio = (gamma_next - gamma) / (gamma - gamma_prev);
-    S.copy(h->nt1, u, n);
-    S.axpy(n, u, 1.0 + ratio, h->nt0, -ratio);
-    std::swap(h->nt0, h->nt1);
-    S.copy(h->mt1, v, m);
-    S.axpy(m, v, 1.0 + ratio, h->mt0, -ratio);
-    std::swap(h->mt0, h->mt1);
-    gamma_prev = gamma;
-    gamma = gamma_next;
-    ++t;
+    throw;
   }
 
   // marginal L1 error of the output against the unsmoothed r, c, at gamma_f (set
   // here too: the one-row / one-column closed form runs no stage that sets it)
   S.set_scalar(SC_GAMMA, gamma);
   S.sweep_bucket = &S.cnt.sweeps_other;
+  S.copy(u, U, n);
+  S.copy(v, V, m);
   S.row_lse(u, v, nullptr, h->logrP, nullptr, P->r, SC_GL1, SC_CHI2);
   S.col_lse(u, nullptr, v, nullptr, 0.0, nullptr, h->logcP, 0, SC_AUX0, 0.0);
-  launch_k(exp_kernel, dim3(S.vg_m), dim3(kThreads), st, m, h->logcP, h->mt1);
-  launch_k(vec_stats_kernel, dim3(S.vg_m), dim3(kThreads), st, m, h->mt1, P->c, 1, h->sc, SC_AUX1, -1,
+  launch_k(exp_kernel, dim3(S.vg_m), dim3(kOnThreads), st, m, h->logcP, h->mt1);
+  launch_k(vec_stats_kernel, dim3(S.vg_m), dim3(kOnThreads), st, m, h->mt1, P->c, 1, h->sc, SC_AUX1, -1,
                                                  h->dotpart, h->cnt_dot, h->status);
   EOT_LAUNCH_CHECK();
   h->launches += 2;
@@ -257,7 +303,7 @@ void run_solve(eot_handle h, const eot_problem* P, const eot_params* prm_in, dou
     stats->sinkhorn_iters = (int32_t)c.sk_iters;
     stats->curvature_stops = (int32_t)c.curvature_stops;
     stats->final_gamma = gamma;
-    stats->final_rho = c.rho_last;
+    stats->final_rho = s[SC_RHOLAST];
     stats->grad_l1 = gl1;
     stats->marg_err_l1 = s[SC_GL1] + s[SC_AUX1];
     stats->seconds = wall_now() - t0;
@@ -273,22 +319,28 @@ double run_sweep_bench(eot_handle h, const eot_problem* P, const double* u, cons
   S.set_scalar(SC_GAMMA, round_gamma<T>(gamma));
   // untimed set-up: the Newton-step factorisation and a CG start at rho = 1/2
   S.row_lse(u, v, nullptr, h->logrP, h->rowmax, nullptr, SC_AUX0, SC_AUX1);
-  launch_k(exp_kernel, dim3(S.vg_n), dim3(kThreads), st, P->n, h->logrP, h->rt);  // r~ := r(P) (any finite target)
+  launch_k(exp_kernel, dim3(S.vg_n), dim3(kOnThreads), st, P->n, h->logrP, h->rt);  // r~ := r(P) (any finite target)
   EOT_LAUNCH_CHECK();
-  bool ran = false;
-  S.newton(u, v, h->rt, 1.0, 1e300, 0.0, 1, CgMode::kHost, &ran);
+  // Newton-step set-up without CG (eta huge: Alg. 2's first test passes), run directly
+  S.init_control(1, 1, 1);
+  S.copy(h->U, u, P->n);
+  S.copy(h->V, v, P->m);
+  S.set_scalar(SC_GL1, 1.0);
+  S.set_scalar(SC_ETA, 1e300);
+  S.set_scalar(SC_RHO, 0.0);
+  S.run_program(Solver<T>::kProgNewton, Solver<T>::kNewtonFlags, true, [&] { S.emit_newton(h->U, h->V, h->rt); });
   S.set_scalar(SC_RHO, 0.5);
   S.set_scalar(SC_TOL, -1.0);
   S.set_scalar(SC_MAXIT, 1e6);
   // a positive direction p = rowfac (so <p, F_r p> > 0) and its column-sweep weights
-  launch_k(weight_kernel<double>, dim3(S.vg_n), dim3(kThreads), st, P->n, h->rowfac, nullptr, h->p);
-  launch_k(weight_kernel<T>, dim3(S.vg_n), dim3(kThreads), st, P->n, h->rowfac, h->p, S.xw0());
+  launch_k(weight_kernel<double>, dim3(S.vg_n), dim3(kOnThreads), st, P->n, h->rowfac, nullptr, h->p);
+  launch_k(weight_kernel<T>, dim3(S.vg_n), dim3(kOnThreads), st, P->n, h->rowfac, h->p, S.xw0());
   S.set_scalar(SC_RZ, 1.0);
   EOT_LAUNCH_CHECK();
   if (kind == 2 && S.points) throw EotError{EOT_ERR_UNSUPPORTED, "kind 2 (fused HVP sweep) needs a dense cost"};
   if (kind == 2) {
-    launch_k(weight_kernel<T>, dim3(S.vg_n), dim3(kThreads), st, P->n, h->rowfac, nullptr, S.xw1());
-    launch_k(weight_kernel<T>, dim3(S.vg_m), dim3(kThreads), st, P->m, h->colfac, nullptr, S.wsq());
+    launch_k(weight_kernel<T>, dim3(S.vg_n), dim3(kOnThreads), st, P->n, h->rowfac, nullptr, S.xw1());
+    launch_k(weight_kernel<T>, dim3(S.vg_m), dim3(kOnThreads), st, P->m, h->colfac, nullptr, S.wsq());
     ensure_rowpart(h, P->n, S.geo.S);
   }
   cudaEvent_t e0, e1;
@@ -342,13 +394,17 @@ double run_sweep_bench(eot_handle h, const eot_problem* P, const double* u, cons
 
 template <class T>
 void run_backward_dense(eot_handle h, const eot_problem* P, const double* u, const double* v,
-                        double gamma, double scale, float* dC, cudaStream_t st) {
+                        double gamma, double scale, const double* scale_dev, float* dC, cudaStream_t st) {
   Solver<T> S(h, P, st);
   EOT_CUDA(cudaMemsetAsync(h->status, 0, sizeof(int), st));
   S.set_scalar(SC_GAMMA, round_gamma<T>(gamma));
   S.row_lse(u, v, nullptr, h->logrP, h->rowmax, nullptr, SC_AUX0, SC_AUX1);
   S.split_rows(u, nullptr, 0.0, h->rowmax, h->Al, nullptr, h->rowfac, h->rowmax);
   S.split_cols(v, nullptr, 0.0, nullptr, h->Bl, nullptr, h->colfac, nullptr);
+  if (scale_dev) {
+    launch_k(scale_by_dev_kernel, dim3(S.vg_n), dim3(kOnThreads), st, P->n, h->rowfac, scale_dev);
+    h->launches++;
+  }
   int64_t blocks = (P->n * P->m + kThreads - 1) / kThreads;
   if (blocks > 16 * (int64_t)h->sms * 8) blocks = 16 * (int64_t)h->sms * 8;
   launch_k(plan_dense_kernel<T>, dim3((unsigned)blocks), dim3(kThreads), st, P->n, P->m, S.C, P->ldc, S.Ah(), S.Bh(),
@@ -365,7 +421,8 @@ void run_backward_dense(eot_handle h, const eot_problem* P, const double* u, con
 // exponents are <= 0 whatever the gauge of (u, v).
 template <class T>
 void run_backward_points(eot_handle h, const eot_problem* P, const double* u, const double* v,
-                         double gamma, double scale, float* dX, float* dY, cudaStream_t st) {
+                         double gamma, double scale, const double* scale_dev, float* dX, float* dY,
+                         cudaStream_t st) {
   Solver<T> S(h, P, st);
   EOT_CUDA(cudaMemsetAsync(h->status, 0, sizeof(int), st));
   S.set_scalar(SC_GAMMA, round_gamma<T>(gamma));
@@ -374,12 +431,20 @@ void run_backward_points(eot_handle h, const eot_problem* P, const double* u, co
     S.row_lse(u, v, nullptr, h->logrP, h->rowmax, nullptr, SC_AUX0, SC_AUX1);
     S.split_rows(u, nullptr, 0.0, h->logrP, h->Al, nullptr, h->rowfac, h->logrP);
     S.split_cols(v, nullptr, 0.0, nullptr, h->Bl, S.ewc(), nullptr, nullptr);
+    if (scale_dev) {
+      launch_k(scale_by_dev_kernel, dim3(S.vg_n), dim3(kOnThreads), st, P->n, h->rowfac, scale_dev);
+      h->launches++;
+    }
     S.template grad_pts<true>(f, h->rowfac, dX);
   }
   if (dY) {
     S.col_lse(u, nullptr, v, nullptr, 0.0, nullptr, h->logcP, 0, SC_AUX0, 0.0);
     S.split_rows(u, nullptr, 0.0, nullptr, h->Al, S.ewr(), nullptr, nullptr);
     S.split_cols(v, nullptr, 0.0, h->logcP, h->Bl, nullptr, h->colfac, h->logcP);
+    if (scale_dev) {
+      launch_k(scale_by_dev_kernel, dim3(S.vg_m), dim3(kOnThreads), st, P->m, h->colfac, scale_dev);
+      h->launches++;
+    }
     S.template grad_pts<false>(f, h->colfac, dY);
   }
   S.read();
@@ -439,10 +504,10 @@ void run_round(eot_handle h, const eot_problem* P, const double* u, const double
   if (S.points) go(rnd::PointCost{S.X, S.Y, S.d, S.sC});
   else if (P->kind == EOT_COST_DENSE_F64) go(rnd::DenseCost<double>{(const double*)P->C, P->ldc});
   else go(rnd::DenseCost<float>{(const float*)P->C, P->ldc});
-  EOT_CUDA(cudaMemcpyAsync(h->h_sc + SC_COUNT - 2, tot, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  EOT_CUDA(cudaMemcpyAsync(h->h_sc + SC_TOTAL - 2, tot, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
   EOT_CUDA(cudaStreamSynchronize(st));
-  if (cost_out) *cost_out = h->h_sc[SC_COUNT - 2];
-  if (corr_out) *corr_out = h->h_sc[SC_COUNT - 1];
+  if (cost_out) *cost_out = h->h_sc[SC_TOTAL - 2];
+  if (corr_out) *corr_out = h->h_sc[SC_TOTAL - 1];
 }
 
 }  // namespace eot

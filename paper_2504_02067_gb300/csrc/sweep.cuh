@@ -46,9 +46,7 @@ struct SweepArgs {
   const float* Y;           // [m][d]
   int d;
   double sC;
-  int64_t chunk;            // other-side elements per chunk (grid.y); strip width of a bulk column sweep
-  int* err;                 // status word of bounded waits (bulk-copy sweeps)
-  int stages;               // ring stages of a bulk-copy sweep
+  int64_t chunk;            // other-side elements per chunk (grid.y)
 };
 
 template <int N>

@@ -28,7 +28,8 @@ def libpath():
 def test_header_declares_the_boundary():
     names = declared_functions()
     for f in ("eot_create", "eot_destroy", "eot_marginals", "eot_hvp", "eot_newton_solve",
-              "eot_solve", "eot_backward", "eot_params_default", "eot_status_string"):
+              "eot_solve", "eot_backward", "eot_params_default", "eot_status_string", "eot_value",
+              "eot_plan_argmax", "eot_plan_support", "eot_solve_batched", "eot_round"):
         assert f in names
 
 
@@ -51,6 +52,8 @@ def test_library_loads_and_binding_matches(libpath):
     p = L.eot_params_default()
     assert p.gamma_i == 16.0 and p.gamma_f == 4096.0 and p.p == 1.5 and p.w_r == 0.45
     assert L.eot_status_string(3) == b"EOT_ERR_CG_MAXITER"
+    for code, name in binding.STATUS_NAMES.items():
+        assert L.eot_status_string(code) == name.encode()
     assert ctypes.sizeof(binding.EotProblem) == 88
     assert ctypes.sizeof(binding.EotParams) == 72
     assert ctypes.sizeof(binding.EotStats) == 136
@@ -84,3 +87,23 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(cls), cname
         for f, _ in cls._fields_:
             assert got[(cname, f)] == getattr(cls, f).offset, (cname, f)
+
+
+def test_status_codes_match_the_header(tmp_path):
+    """The binding's status names carry the header's enum values, including the
+    bounded-device-wait status EOT_ERR_DEVICE_TIMEOUT."""
+    if not shutil.which("gcc"):
+        pytest.skip("gcc not available")
+    from paper_2504_02067_gb300 import binding
+    src = tmp_path / "codes.c"
+    src.write_text('#include <stdio.h>\n#include "eot.h"\nint main(void) {\n'
+                   + "\n".join('  printf("%s %%d\\n", (int)%s);' % (nm, nm)
+                               for nm in binding.STATUS_NAMES.values())
+                   + "\n  return 0;\n}\n")
+    exe = tmp_path / "codes"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
+    got = {out[k]: int(out[k + 1]) for k in range(0, len(out), 2)}
+    for code, name in binding.STATUS_NAMES.items():
+        assert got[name] == code
+    assert got["EOT_ERR_DEVICE_TIMEOUT"] == 10

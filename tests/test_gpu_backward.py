@@ -229,3 +229,54 @@ def test_eot_function_fd_d64_mixed(H):
     rX, rY = O.eot_grads_points(u.cpu().numpy(), v.cpu().numpy(), 1024.0, X, Y, sC)
     assert rel(gX, rX) <= 1e-5 and rel(gY, rY) <= 1e-5
     assert abs(fd - pred) <= 1e-4 * abs(pred), (fd, pred)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_eot_value_is_the_dual_value_and_the_primal_at_the_optimum(H, prec):
+    """eot_value returns (<r, u> + <c, v> - sum P + 1) / gamma on the device (Eq.
+    sinkhorn-dual) at any (u, v): against the oracle's formula at the same point
+    (relative 1e-12 in FP64, 1e-7 mixed: sum P carries the FP32 sweep's relative
+    error, about 1e-7); and at a tight optimum it equals the primal value
+    <P, C> - H(P) / gamma (strong duality, Sec. 2.1) to the same tolerances."""
+    from paper_2504_02067_gb300 import Problem
+    X, Y, r, c = cloud(91, 400, 350, 3)
+    sC = O.sqeuclid_scale(X, Y)
+    C64 = sC * O.sqeuclid(X, Y)
+    g = 256.0 if prec == "fp64" else float(np.float32(256.0))
+    prob = Problem(X=t(X, torch.float32), Y=t(Y, torch.float32), r=t(r), c=t(c), precision=prec, cost_scale=sC)
+    rng = np.random.default_rng(5)
+    u0 = np.log(r) + rng.normal(0, 0.2, 400) + 3.0
+    v0 = np.log(c) - O.lse_c(u0[:, None] - g * C64)
+    tol = 1e-12 if prec == "fp64" else 1e-7
+    us, vs = O.sinkhorn_log(C64, r, c, g, tol=1e-14, max_iter=200000)
+    for (u, v) in ((u0, v0), (us, vs)):
+        val = torch.empty((), dtype=torch.float64, device=DEV)
+        H.eot_value(prob, t(u), t(v), g, val)
+        ref = (r @ u + c @ v - O.plan(u, v, g, C64).sum() + 1.0) / g
+        assert abs(val.item() - ref) <= tol * abs(ref), (val.item(), ref)
+    primal = O.primal_value(O.plan(us, vs, g, C64), C64, g)
+    assert abs(val.item() - primal) <= max(tol, 1e-11) * abs(primal)
+
+
+def test_backward_reads_the_gradient_scale_on_the_device(H):
+    """grad_scale_dev (a device scalar, e.g. the incoming autograd gradient)
+    multiplies every output as the host grad_scale does (a power of two, so both
+    orders of the products are exact and the outputs bit-identical)."""
+    from paper_2504_02067_gb300 import Problem
+    X, Y, r, c = cloud(92, 300, 257, 3)
+    sC = O.sqeuclid_scale(X, Y)
+    C64 = sC * O.sqeuclid(X, Y)
+    g = 512.0
+    u = np.log(r) + 2.0
+    v = np.log(c) - O.lse_c(u[:, None] - g * C64)
+    prob = Problem(X=t(X, torch.float32), Y=t(Y, torch.float32), precision="fp64", cost_scale=sC)
+    outs = []
+    for host, dev in ((-0.5, None), (1.0, t(np.array(-0.5)))):
+        dX = torch.empty(300, 3, dtype=torch.float32, device=DEV)
+        dY = torch.empty(257, 3, dtype=torch.float32, device=DEV)
+        dr = torch.empty(300, dtype=torch.float64, device=DEV)
+        dc = torch.empty(257, dtype=torch.float64, device=DEV)
+        H.eot_backward(prob, t(u), t(v), g, host, dX=dX, dY=dY, dr=dr, dc=dc, grad_scale_dev=dev)
+        outs.append([x.cpu().numpy() for x in (dX, dY, dr, dc)])
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)

@@ -587,3 +587,87 @@ def test_mdot_sinkhorn_reaches_the_same_optimum():
     assert O.marginal_l1_error(b.u, b.v, 512.0, C, r, c) <= 1e-8
     Pa, Pb = O.plan(a.u, a.v, 512.0, C), O.plan(b.u, b.v, 512.0, C)
     assert np.abs(Pa - Pb).sum() <= 1e-6
+
+
+# ---------------- integer outputs of the plan (row argmax, support) ----------------
+
+def test_sqeuclid_ordered_exact_on_integer_points():
+    """Integer coordinates make every difference, square and partial sum exact in
+    FP64, so the ordered distance must equal the exact integer distance; on
+    general points it agrees with the vectorised distance to rounding."""
+    rng = np.random.default_rng(70)
+    Xi = rng.integers(-1000, 1000, size=(9, 5))
+    Yi = rng.integers(-1000, 1000, size=(7, 5))
+    exact = np.array([[sum(int(a - b) ** 2 for a, b in zip(x, y)) for y in Yi] for x in Xi])
+    D = O.sqeuclid_ordered(Xi.astype(np.float32), Yi.astype(np.float32))
+    assert np.array_equal(D, exact.astype(np.float64))
+    X = rng.normal(size=(11, 33)).astype(np.float32)
+    Y = rng.normal(size=(13, 33)).astype(np.float32)
+    np.testing.assert_allclose(O.sqeuclid_ordered(X, Y), O.sqeuclid(X, Y), rtol=1e-14)
+
+
+def test_row_argmax_is_argmax_of_the_plan_and_breaks_ties_low():
+    """The argmax of v_j - gamma C_ij equals the argmax of the formed plan P_ij
+    (exp is increasing and u_i is constant along a row) where the maximum is not
+    within rounding of a tie; duplicated columns give exact ties, which go to
+    the lower index."""
+    C, u, v, g = rand_problem(71, 40, 57, gamma=64.0)
+    C[:, 20] = C[:, 9]
+    v[20] = v[9]
+    idx = O.plan_row_argmax(v, g, C)
+    P = O.plan(u, v, g, C)
+    t = v[None, :] - g * C
+    srt = np.sort(t, axis=1)
+    clear = srt[:, -1] - srt[:, -2] > 1e-9
+    assert np.array_equal(idx[clear], np.argmax(P, axis=1)[clear])
+    # rows whose maximum is the duplicated pair report the lower index 9, never 20
+    assert not np.any(idx == 20)
+    tied = np.argmax(t[:, [9, 20]].max(axis=1)[:, None] >= t, axis=1)
+    assert np.sum(idx == 9) >= 0 and np.all((idx != 9) | (tied >= 0))
+    # a brute-force scan in Python: first index of the maximum
+    for i in range(C.shape[0]):
+        best, bj = -math.inf, -1
+        for j in range(C.shape[1]):
+            if t[i, j] > best:
+                best, bj = t[i, j], j
+        assert idx[i] == bj
+
+
+def test_row_argmax_recovers_the_optimal_assignment():
+    """Uniform marginals at a large gamma: the EOT plan concentrates on the LP
+    optimum, a permutation (Birkhoff; Sec. 2.2's error bound), so the row argmax
+    is that permutation when it is unique (checked by brute force)."""
+    n = 6
+    rng = np.random.default_rng(72)
+    C = rng.uniform(0, 1, size=(n, n))
+    C /= C.max()
+    r = c = np.full(n, 1.0 / n)
+    ri, ci = scipy.optimize.linear_sum_assignment(C)
+    costs = sorted(C[np.arange(n), list(p)].sum() for p in __import__("itertools").permutations(range(n)))
+    assert costs[1] - costs[0] > 1e-3  # a unique optimum with a margin
+    res = O.mdot(C, r, c, gamma_i=4.0, gamma_f=2.0 ** 12, tol_final=1e-9)
+    idx = O.plan_row_argmax(res.v, res.gamma, C)
+    assert np.array_equal(idx[ri], ci)
+
+
+def test_support_counts_match_thresholded_plan():
+    """Counts of the exponent test equal counts of the formed plan above tau away
+    from rounding ties, are monotone in tau, give m per row at log tau = -inf and
+    0 above the largest entry, and exclude an entry lying exactly on the threshold."""
+    C, u, v, g = rand_problem(73, 50, 61, gamma=32.0)
+    P = O.plan(u, v, g, C)
+    t = (u[:, None] + v[None, :]) - g * C
+    for q in (0.1, 0.5, 0.9):
+        lt = float(np.quantile(t, q))
+        near = np.abs(t - lt) < 1e-9
+        cnt = O.plan_support_counts(u, v, g, C, lt)
+        ref = (P > math.exp(lt)).sum(axis=1)
+        ok_rows = ~near.any(axis=1)
+        assert np.array_equal(cnt[ok_rows], ref[ok_rows])
+    assert np.all(O.plan_support_counts(u, v, g, C, -math.inf) == C.shape[1])
+    assert np.all(O.plan_support_counts(u, v, g, C, float(t.max())) == 0)
+    c1 = O.plan_support_counts(u, v, g, C, float(np.quantile(t, 0.3)))
+    c2 = O.plan_support_counts(u, v, g, C, float(np.quantile(t, 0.6)))
+    assert np.all(c1 >= c2)
+    on = float(t[3, 7])
+    assert O.plan_support_counts(u, v, g, C, on)[3] == int((t[3] > on).sum())

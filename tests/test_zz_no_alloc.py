@@ -74,3 +74,46 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     v = torch.zeros(4, dtype=torch.float64, device=DEV)
     with pytest.raises(EotError):
         eot_marginals_noalloc(prob, u, v, 1.0, torch.empty_like(u), torch.empty_like(v))
+
+
+def test_noalloc_at_its_size_limit_with_unaligned_rows():
+    """n = m = 16384, the largest size the fixed scratch array serves, with a
+    leading dimension m + 1 (16-byte loads impossible: the scalar path with the
+    most column strips and tickets), compared with eot_marginals on the same
+    seeded inputs; then m = 16385 is rejected."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2504_02067_gb300 as E
+    from paper_2504_02067_gb300.binding import EotError, eot_marginals_noalloc
+    E.build()
+    n = m = 16384
+    gen = torch.Generator(device=DEV).manual_seed(7)
+    Cfull = torch.rand(n, m + 1, generator=gen, device=DEV, dtype=torch.float32)
+    C = Cfull[:, :m]
+    assert C.stride(0) == m + 1
+    gamma = 8.0
+    u = (torch.randn(n, generator=gen, device=DEV, dtype=torch.float64) * 0.3 - np.log(n))
+    v = (torch.randn(m, generator=gen, device=DEV, dtype=torch.float64) * 0.3 - np.log(m))
+    prob = E.Problem(C, precision="mixed")
+    h = E.Handle(0, 64, 64)
+    try:
+        r_ref, c_ref, _, _, _ = h.marginals(prob, u, v, gamma)
+    finally:
+        h.close()
+    for call in range(2):
+        r = torch.full((n,), float("nan"), dtype=torch.float64, device=DEV)
+        c = torch.full((m,), float("nan"), dtype=torch.float64, device=DEV)
+        status = torch.full((1,), -1, dtype=torch.int32, device=DEV)
+        eot_marginals_noalloc(prob, u, v, gamma, r, c, status)
+        torch.cuda.synchronize()
+        assert status.item() == 0
+        mass = r_ref.sum().item()
+        assert (r - r_ref).abs().sum().item() <= 1e-6 * mass
+        assert (c - c_ref).abs().sum().item() <= 1e-6 * mass
+    del Cfull, C
+    Cw = torch.zeros(4, 16385, dtype=torch.float32, device=DEV)
+    probw = E.Problem(Cw, precision="mixed")
+    uw = torch.zeros(4, dtype=torch.float64, device=DEV)
+    vw = torch.zeros(16385, dtype=torch.float64, device=DEV)
+    with pytest.raises(EotError):
+        eot_marginals_noalloc(probw, uw, vw, 1.0, torch.empty_like(uw), torch.empty_like(vw))
