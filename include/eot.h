@@ -299,8 +299,10 @@ eot_status eot_plan_support(eot_handle h, const eot_problem* prob, const double*
 
 /* Measurement aid: times `iters` launches of one sweep kernel at (u, v) with CUDA
  * events recorded on `stream` (after an untimed set-up at the same point):
- *   kind 0: the CG column half  w = P^T p            (Alg. 2 inner CG, F_r(rho) p)
- *   kind 1: the CG row half     y = P (w / c(P)), q = r(P) p - rho y, <p, q>
+ *   kind 0: the CG column half  w = P^T p            (Alg. 2 inner CG, F_r(rho) p; dense
+ *           costs: P^T (rowfac z) + beta w_prev, with the stop test in its prologue)
+ *   kind 1: the CG row half     y = P (w / c(P)), q = r(P) p - rho y, <p, q> (dense
+ *           costs: also p = z + beta p_prev per row)
  *   kind 2: the fused two-sided HVP sweep of eot_hvp
  *   kind 3: the row log-sum-exp sweep (Alg. 3 / Alg. 4 row updates)
  * flush == NULL: the launches run back to back between two events (the cost stays

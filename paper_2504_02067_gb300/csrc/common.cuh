@@ -164,6 +164,42 @@ __device__ __forceinline__ typename VecOf<T>::type pack(const T (&x)[16 / sizeof
   else return make_double2(x[0], x[1]);
 }
 
+// In-order combine of a strided sequence base[k * stride], k < cnt, written by
+// earlier CTAs: the loads go out in batches of 8 (independent L2 round trips
+// overlap) and f(value) consumes them in index order, so the result is the same
+// as a plain sequential loop.
+template <class V, class F>
+__device__ __forceinline__ void ordered_loads(const V* base, int64_t stride, int64_t cnt, F&& f) {
+  constexpr int B = 8;
+  for (int64_t k0 = 0; k0 < cnt; k0 += B) {
+    V q[B];
+#pragma unroll
+    for (int u = 0; u < B; ++u)
+      if (k0 + u < cnt) q[u] = __ldcg(base + (k0 + u) * stride);
+#pragma unroll
+    for (int u = 0; u < B; ++u)
+      if (k0 + u < cnt) f(q[u]);
+  }
+}
+// The same for two sequences read in step: f(a_k, b_k).
+template <class V, class W, class F>
+__device__ __forceinline__ void ordered_loads2(const V* a, const W* b, int64_t stride, int64_t cnt, F&& f) {
+  constexpr int B = 8;
+  for (int64_t k0 = 0; k0 < cnt; k0 += B) {
+    V qa[B];
+    W qb[B];
+#pragma unroll
+    for (int u = 0; u < B; ++u)
+      if (k0 + u < cnt) {
+        qa[u] = __ldcg(a + (k0 + u) * stride);
+        qb[u] = __ldcg(b + (k0 + u) * stride);
+      }
+#pragma unroll
+    for (int u = 0; u < B; ++u)
+      if (k0 + u < cnt) f(qa[u], qb[u]);
+  }
+}
+
 __device__ __forceinline__ double warp_sum(double x) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);

@@ -21,7 +21,7 @@ enum Flag : int { F_NEWTON = 0, F_SK, F_GO, F_CGOUT, F_CG, F_DEC, F_LS, F_UPD, F
 
 // device scalars of the stage control (continuing the Sc enum of kernels.cuh)
 enum ScCtl : int {
-  SC_EPS = 22,      // tolerance eps of the projection (Alg. 4)
+  SC_EPS = 23,      // tolerance eps of the projection (Alg. 4)
   SC_EPSCHI,        // eps^(2/5), ChiSinkhorn's tolerance (Alg. 3)
   SC_ETA,           // forcing parameter of the Newton step
   SC_GL1K,          // ||grad g||_1 at the start of the Newton step
@@ -62,6 +62,7 @@ struct Ctl {
   int graph;        // 1: set the conditional handles too
   unsigned mask;    // flags whose handle belongs to a node of this program
   int fp64;         // FP64 path: the Armijo test is always decided
+  int fused_cg;     // dense-cost CG: the column half of iteration k + 1 decides the stop
   double floor32;   // FP32 paths: rounding floor of sum P(alpha) - 1 (reading R28)
 };
 
@@ -145,7 +146,8 @@ EOT_CTL_KERNEL(ctl_cg_end) {
   EOT_CTL_BEGIN
   const double it = sc[SC_ITERS];
   const bool curv = (atomicAnd(c.status, ~kStatCurv) & kStatCurv) != 0;
-  const double tried = it + (curv ? 1.0 : 0.0);
+  // iterations whose kernels ran: the loop body repeats kCgBody of them
+  const double tried = c.fused_cg ? it + 1.0 : it + (curv ? 1.0 : 0.0);
   sc[SC_N_CGIT] += it;
   sc[SC_N_CGPASS] += ceil(tried / (double)kCgBody);
   sc[SC_N_CGSOLVE] += 1.0;

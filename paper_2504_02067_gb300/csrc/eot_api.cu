@@ -55,11 +55,12 @@ void ensure_capacity(eot_handle h, int64_t n, int64_t m) {
   EOT_CUDA(cudaMemset(h->cnt_dot, 0, sizeof(int)));
   h->colpart = (double*)dev_alloc(h, 2 * h->max_rowblk * Mm * sizeof(double));
   h->dotpart = (double*)dev_alloc(h, 2 * h->dot_slots * sizeof(double));
+  h->cgpart = (double*)dev_alloc(h, 2 * (4 * (int64_t)h->sms + 8) * sizeof(double));
   double** nv[] = {&h->Al, &h->rowfac, &h->rP, &h->logrP, &h->rowmax, &h->rt, &h->logrt,
                    &h->du, &h->x, &h->res, &h->z, &h->p, &h->q, &h->y, &h->Yx, &h->M,
                    &h->diag, &h->y0, &h->du0, &h->nt0, &h->nt1, &h->rPs, &h->U};
   for (double** p : nv) *p = (double*)dev_alloc(h, N * sizeof(double));
-  double** mv[] = {&h->Bl, &h->colfac, &h->cP, &h->logcP, &h->ct, &h->logct, &h->dv, &h->mt0, &h->mt1, &h->V};
+  double** mv[] = {&h->Bl, &h->colfac, &h->cP, &h->logcP, &h->ct, &h->logct, &h->dv, &h->mt0, &h->mt1, &h->V, &h->wprev};
   for (double** p : mv) *p = (double*)dev_alloc(h, Mm * sizeof(double));
   void** ev[] = {&h->Ah, &h->Bh, &h->xw0, &h->xw1, &h->zf, &h->wsq, &h->ewr, &h->ewc};
   for (void** p : ev) *p = dev_alloc(h, L * sizeof(double));

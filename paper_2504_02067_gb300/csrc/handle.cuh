@@ -77,6 +77,8 @@ struct eot_handle_s {
   double *Bl = nullptr, *colfac = nullptr, *cP = nullptr, *logcP = nullptr, *ct = nullptr;
   double *logct = nullptr, *dv = nullptr, *mt0 = nullptr, *mt1 = nullptr;
   double* V = nullptr;
+  double* wprev = nullptr;  // dense CG: P^T (rowfac p) of the previous iteration
+  double* cgpart = nullptr; // dense CG: per-CTA (<res, z>, ||res||_1) partials of the update kernel
   // element-type vectors (8 bytes per entry, used as float or double)
   void *Ah = nullptr, *Bh = nullptr, *xw0 = nullptr, *xw1 = nullptr, *zf = nullptr;
   void *wsq = nullptr, *ewr = nullptr, *ewc = nullptr;

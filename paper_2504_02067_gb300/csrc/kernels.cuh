@@ -15,6 +15,7 @@ enum Sc : int {
   SC_RZ = 0, SC_PQ, SC_ALPHA, SC_BETA, SC_RESL1, SC_TOL, SC_RHO, SC_ITERS, SC_ACTIVE, SC_MAXIT,
   SC_CHECK, SC_GL1, SC_CHI2, SC_LHS, SC_SLOPE, SC_MASS, SC_CHK, SC_GAMMA, SC_AUX0, SC_AUX1,
   SC_GRD, SC_GMASS,  // <r(P), d_u> and sum r(P): the gauge component of d_u
+  SC_RZPREV,         // <res, z> of the previous CG iteration (dense CG: beta's denominator)
   SC_COUNT = 32,     // the slots the sweeps and O(n) kernels use (eot_marginals_noalloc keeps these)
   SC_TOTAL = 64      // with the stage control's slots (control.cuh): the handle's array
 };
@@ -128,6 +129,153 @@ struct CgColEpi {
   __device__ void col(int64_t j, const double* s, double* d) {
     const double f = colfac[j];
     zf[j] = (T)(f * f * s[0] / cP[j]);
+  }
+  __device__ void finish(const double*) {}
+};
+
+// ---- the CG iteration of dense costs: three kernels, one grid-wide ticket ----
+// PCG on F_r(rho) (Alg. 2) with the search-direction update folded into the
+// sweeps. By linearity, w = P^T (rowfac p) for p = z + beta p_prev is
+// P^T (rowfac z) + beta w_prev, so the column half sweeps the row weights
+// rowfac z that the update kernel wrote and adds beta w_prev per column; the
+// row half forms p = z + beta p_prev per row. beta and the stop test come from
+// the update kernel's per-CTA partials of <res, z> and ||res||_1, which every
+// CTA of the column half sums itself in fixed order (no grid-wide ticket);
+// likewise the update kernel sums the row half's partials of <p, q> for alpha.
+
+// (<res, z>, ||res||_1) from `nparts` per-CTA partials, in fixed order; one warp.
+__device__ __forceinline__ void sum_cg_partials(const double* part, int nparts, double& rz, double& r1) {
+  const int lane = threadIdx.x & 31;
+  double a = 0.0, b = 0.0;
+  for (int k = lane; k < nparts; k += 32) {
+    a += part[2 * k];
+    b += part[2 * k + 1];
+  }
+  rz = warp_sum(a);
+  r1 = warp_sum(b);
+}
+
+constexpr int kCgMaxParts = 1024;  // update-kernel partials a column half can stage
+constexpr int kCgMaxStrip = 128;   // columns of one strip of the column sweep (32 V)
+struct CgStage {
+  double part[2 * kCgMaxParts];   // (<res, z>, ||res||_1) partials
+  double wprev[kCgMaxStrip];      // w_prev of the CTA's strip
+  double iters, rzprev;           // SC_ITERS, SC_RZPREV
+};
+__device__ __forceinline__ CgStage& cg_stage_smem() {
+  __shared__ __align__(16) CgStage st;
+  return st;
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+
+// Column half: w_j = (P^T (rowfac z))_j + beta w_prev_j; zf_j = colfac_j^2 w_j / c(P)_j,
+// with beta = <res, z> / <res, z>_prev (0 on the first iteration). begin(): warp 0
+// starts asynchronous copies of what the strip's epilogue needs (the update
+// kernel's partials, w_prev of the strip's columns, two scalars) into shared
+// memory, where they land while the CTA sweeps; drain(): warp 0 waits for them;
+// prepare() (the CTAs that finish a strip): beta and the stop test ||res||_1 <=
+// tol or the iteration cap, published by the finisher of strip 0. When the test
+// stops CG this sweep's results are not used: the row half and the update see
+// the cleared flag and return.
+template <class T>
+struct CgColFusedEpi {
+  static constexpr int kDot = 0;
+  static constexpr bool kPrefetch = true;
+  const double *colfac, *cP;
+  T* zf;
+  double* wprev;       // [m] w of the previous iteration
+  const double* part;  // [nparts][2] partials of the update kernel (or of cg_init)
+  int nparts;          // <= kCgMaxParts
+  double* sc;
+  int* status;
+  cudaGraphConditionalHandle cond;
+  double beta;
+  bool first;
+  int64_t j0;          // first column of the strip
+  __device__ void begin(int64_t strip0, int sw, int64_t m) {
+    j0 = strip0;
+    if (threadIdx.x < 32) {
+      CgStage& s = cg_stage_smem();
+      for (int k = threadIdx.x; k < nparts; k += 32) cp_async16(s.part + 2 * k, part + 2 * k);
+      // w_prev of the strip (pairs of columns: the strip start is a multiple of 32 V >= 32)
+      const int w = (int)min((int64_t)sw, m - strip0);
+      for (int k = 2 * threadIdx.x; k < w; k += 64) {
+        if (k + 1 < w) cp_async16(s.wprev + k, wprev + strip0 + k);
+        else cp_async8(s.wprev + k, wprev + strip0 + k);
+      }
+      if (threadIdx.x == 0) {
+        cp_async8(&s.iters, sc + SC_ITERS);
+        cp_async8(&s.rzprev, sc + SC_RZPREV);
+      }
+      asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+  }
+  __device__ void drain() {
+    if (threadIdx.x < 32) asm volatile("cp.async.wait_all;" ::: "memory");
+  }
+  __device__ void prepare(bool publish) {
+    __shared__ double sbeta;
+    __shared__ int sfirst;
+    CgStage& st = cg_stage_smem();
+    __syncthreads();  // the copies warp 0 waited for are visible to every thread
+    if (threadIdx.x < 32) {
+      double rz, r1;
+      sum_cg_partials(st.part, nparts, rz, r1);
+      if (threadIdx.x == 0) {
+        const double it = st.iters;
+        const bool f = it == 0.0;
+        const double b = f ? 0.0 : rz / st.rzprev;
+        sbeta = b;
+        sfirst = f ? 1 : 0;
+        if (publish) {
+          const bool fin = isfinite(rz) && isfinite(r1) && isfinite(b);
+          const bool go = fin && r1 > sc[SC_TOL] && it < sc[SC_MAXIT] && it < 1.0e6;
+          sc[SC_RZ] = rz;
+          sc[SC_RESL1] = r1;
+          sc[SC_BETA] = b;
+          if (!fin) atomicOr(status, kStatCgNan);
+          if (!go) {
+            sc[SC_ACTIVE] = 0.0;
+            if (cond) cudaGraphSetConditional(cond, 0);
+          }
+        }
+      }
+    }
+    __syncthreads();
+    beta = sbeta;
+    first = sfirst != 0;
+  }
+  __device__ void col(int64_t j, const double* s, double* d) {
+    const double w = first ? s[0] : s[0] + beta * cg_stage_smem().wprev[j - j0];
+    wprev[j] = w;
+    const double f = colfac[j];
+    zf[j] = (T)(f * f * w / cP[j]);
+  }
+  __device__ void finish(const double*) {}
+};
+
+// Row half: p = z + beta p_prev (in place), y = P (w / c(P)), q = r(P) p - rho y;
+// one partial of <p, q> per CTA.
+struct CgRowFusedEpi {
+  static constexpr int kDot = 1;
+  static constexpr bool kNoTicket = true;
+  const double *rowfac, *rP, *z;
+  double *p, *y, *q, *sc;
+  __device__ void row(int64_t i, const double* s, double* d) {
+    const double pi = z[i] + sc[SC_BETA] * p[i];
+    p[i] = pi;
+    const double yi = rowfac[i] * s[0];
+    const double qi = rP[i] * pi - sc[SC_RHO] * yi;
+    y[i] = yi;
+    q[i] = qi;
+    d[0] = pi * qi;
   }
   __device__ void finish(const double*) {}
 };
@@ -441,6 +589,103 @@ __global__ void cg_pupdate_kernel(int64_t n, const double* z, const double* rowf
     const double pi = z[i] + beta * p[i];
     p[i] = pi;
     xw[i] = (T)(rowfac[i] * pi);
+  }
+}
+
+// Dense-cost PCG start (x = 0): Minv = 1 / diag(F_r(rho)) (clamped as in
+// cg_init_kernel) into M, res = r~ - r(P), z = Minv res, p_prev = 0, the column half's row weights
+// rowfac z, and one (<res, z>, ||res||_1) partial per CTA; the CG loop starts
+// (the first column half decides whether it runs).
+template <class T>
+__global__ void cg_init_fused_kernel(int64_t n, const double* rP, const double* rPs, const double* rt,
+                                     const double* diag, const double* rowfac, double* M, double* x, double* res,
+                                     double* z, double* p, double* Yx, T* xw, double* sc, double* part,
+                                     cudaGraphConditionalHandle cond) {
+  pdl_wait();
+  const double rho = sc[SC_RHO];
+  double a = 0.0, b1 = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double Mi = fmax(rPs[i] - rho * diag[i], (1.0 - rho) * rPs[i]);
+    const double b = rt[i] - rP[i];
+    const double mi = 1.0 / Mi;
+    const double zi = b * mi;
+    M[i] = mi;
+    x[i] = 0.0;
+    res[i] = b;
+    z[i] = zi;
+    p[i] = 0.0;
+    Yx[i] = 0.0;
+    xw[i] = (T)(rowfac[i] * zi);
+    a += b * zi;
+    b1 += fabs(b);
+  }
+  a = warp_sum(a);
+  b1 = warp_sum(b1);
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = a;
+    part[2 * blockIdx.x + 1] = b1;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    sc[SC_ITERS] = 0.0;
+    sc[SC_BETA] = 0.0;
+    sc[SC_ACTIVE] = 1.0;
+    if (cond) cudaGraphSetConditional(cond, 1);
+  }
+}
+
+// Dense-cost PCG step: alpha = <res, z> / <p, q> from the row half's partials
+// (summed by every CTA in fixed order; <p, F_r p> <= 0 stops CG, reading R21),
+// x += alpha p, res -= alpha q, Yx += alpha y, z = Minv res, the next column
+// half's row weights rowfac z, and one (<res, z>, ||res||_1) partial per CTA.
+template <class T>
+__global__ void cg_update_fused_kernel(int64_t n, const double* p, const double* q, const double* y,
+                                       const double* Minv, const double* rowfac, double* x, double* res,
+                                       double* Yx, double* z, T* xw, double* sc, const double* rowpart,
+                                       int nrow, double* part, int* status, cudaGraphConditionalHandle cond) {
+  pdl_wait();
+  if (sc[SC_ACTIVE] == 0.0) {
+    if (cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, 0);
+    return;
+  }
+  double pq = 0.0;
+  for (int k = threadIdx.x; k < nrow; k += 32) pq += __ldcg(rowpart + 2 * k);
+  pq = warp_sum(pq);
+  if (!(pq > 0.0) || !isfinite(pq)) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      atomicOr(status, kStatCurv);
+      sc[SC_PQ] = pq;
+      sc[SC_ALPHA] = 0.0;
+      sc[SC_ACTIVE] = 0.0;
+      if (cond) cudaGraphSetConditional(cond, 0);
+    }
+    return;
+  }
+  const double alpha = sc[SC_RZ] / pq;
+  double a = 0.0, b1 = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] += alpha * p[i];
+    const double r = res[i] - alpha * q[i];
+    res[i] = r;
+    Yx[i] += alpha * y[i];
+    const double zi = r * Minv[i];
+    z[i] = zi;
+    xw[i] = (T)(rowfac[i] * zi);
+    a += r * zi;
+    b1 += fabs(r);
+  }
+  a = warp_sum(a);
+  b1 = warp_sum(b1);
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = a;
+    part[2 * blockIdx.x + 1] = b1;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    sc[SC_ITERS] += 1.0;
+    sc[SC_PQ] = pq;
+    sc[SC_ALPHA] = alpha;
+    sc[SC_RZPREV] = sc[SC_RZ];
   }
 }
 

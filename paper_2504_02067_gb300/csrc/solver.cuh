@@ -143,6 +143,7 @@ struct Solver {
     }
     vg_n = on_grid(n, h->sms, h->dot_slots);
     vg_m = on_grid(m, h->sms, h->dot_slots);
+    if (vg_n > kCgMaxParts) throw EotError{EOT_ERR_UNSUPPORTED, "more update partials than the CG sweep stages"};
     rg = row_grid(n);
     geo = col_geo(h, n, m, V);
     sweep_bucket = &cnt.sweeps_other;
@@ -402,6 +403,18 @@ struct Solver {
     if (V == VEC) launch_k(col_sweep_kernel<T, VEC, NC, LSE, NR, Epi>, grid, dim3(kThreads), s, a, e);
     else launch_k(col_sweep_kernel<T, 1, NC, LSE, NR, Epi>, grid, dim3(kThreads), s, a, e);
   }
+  // dense-cost sweeps only (epilogues that exist for the dense path alone)
+  template <int NR, bool LSE, int SQM, class Epi>
+  void launch_row_dense(cudaStream_t s, const SweepArgs<T>& a, const Epi& e) {
+    if (V == VEC) launch_k(row_sweep_kernel<T, VEC, NR, LSE, SQM, Epi>, dim3(rg), dim3(kThreads), s, a, e);
+    else launch_k(row_sweep_kernel<T, 1, NR, LSE, SQM, Epi>, dim3(rg), dim3(kThreads), s, a, e);
+  }
+  template <int NC, bool LSE, class Epi>
+  void launch_col_dense(cudaStream_t s, const SweepArgs<T>& a, const Epi& e) {
+    const dim3 grid((unsigned)geo.S, (unsigned)geo.R);
+    if (V == VEC) launch_k(col_sweep_kernel<T, VEC, NC, LSE, 0, Epi>, grid, dim3(kThreads), s, a, e);
+    else launch_k(col_sweep_kernel<T, 1, NC, LSE, 0, Epi>, grid, dim3(kThreads), s, a, e);
+  }
   template <int NR, bool LSE, int SQM, class Epi>
   void row(const SweepArgs<T>& a, const Epi& e) {
     launch_row<NR, LSE, SQM>(st, a, e);
@@ -575,6 +588,7 @@ struct Solver {
     ctl.sc = h->sc;
     ctl.status = h->status;
     ctl.fp64 = sizeof(T) == 8 ? 1 : 0;
+    ctl.fused_cg = points ? 0 : 1;
     ctl.floor32 = armijo_floor32(n, m);
     int64_t* saved = sweep_bucket;
     sweep_bucket = &discard;
@@ -740,8 +754,12 @@ struct Solver {
     }
     ctl_launch(ctl_cg_begin);
     loop_while(F_CGOUT, [&] {
-      launch_k(cg_init_kernel<T>, dim3(vg_n), dim3(kOnThreads), st, n, h->rP, h->rPs, rt, h->diag, h->rowfac, h->M,
-               h->x, h->res, h->z, h->p, h->Yx, xw0(), h->sc, h->dotpart, h->cnt_dot, cond(F_CG));
+      if (points)
+        launch_k(cg_init_kernel<T>, dim3(vg_n), dim3(kOnThreads), st, n, h->rP, h->rPs, rt, h->diag, h->rowfac,
+                 h->M, h->x, h->res, h->z, h->p, h->Yx, xw0(), h->sc, h->dotpart, h->cnt_dot, cond(F_CG));
+      else
+        launch_k(cg_init_fused_kernel<T>, dim3(vg_n), dim3(kOnThreads), st, n, h->rP, h->rPs, rt, h->diag,
+                 h->rowfac, h->M, h->x, h->res, h->z, h->p, h->Yx, xw0(), h->sc, h->cgpart, cond(F_CG));
       EOT_LAUNCH_CHECK();
       h->launches++;
       loop_while(F_CG, [&] {
@@ -769,9 +787,35 @@ struct Solver {
     }
   }
 
-  // One CG iteration's four kernels (column half, row half, update, p update),
-  // each a no-op once the device stop flag SC_ACTIVE is clear.
+  // One CG iteration, each kernel a no-op once the device stop flag SC_ACTIVE
+  // is clear. Dense costs: the column half (which also takes beta and the stop
+  // test), the row half (which forms p) and the update (CgColFusedEpi,
+  // CgRowFusedEpi, cg_update_fused_kernel). Point costs: column half, row half,
+  // update, p update.
   void cg_iteration() {
+    if (!points) {
+      {
+        SweepArgs<T> a = args();
+        a.wr[0] = xw0();
+        a.active = h->sc + SC_ACTIVE;
+        CgColFusedEpi<T> e{h->colfac, h->cP, zf(), h->wprev, h->cgpart, vg_n, h->sc, h->status, cond(F_CG), 0.0,
+                           false, 0};
+        launch_col_dense<1, false>(st, a, e);
+      }
+      {
+        SweepArgs<T> a = args();
+        a.wc[0] = zf();
+        a.active = h->sc + SC_ACTIVE;
+        CgRowFusedEpi e{h->rowfac, h->rPs, h->z, h->p, h->y, h->q, h->sc};
+        launch_row_dense<1, false, 0>(st, a, e);
+      }
+      launch_k(cg_update_fused_kernel<T>, dim3(vg_n), dim3(kOnThreads), st, n, (const double*)h->p,
+               (const double*)h->q, (const double*)h->y, (const double*)h->M, (const double*)h->rowfac, h->x, h->res,
+               h->Yx, h->z, xw0(), h->sc, (const double*)h->dotpart, rg, h->cgpart, h->status, cond(F_CG));
+      EOT_LAUNCH_CHECK();
+      h->launches += 3;
+      return;
+    }
     {
       SweepArgs<T> a = args();
       a.wr[0] = xw0();

@@ -336,6 +336,13 @@ double run_sweep_bench(eot_handle h, const eot_problem* P, const double* u, cons
   launch_k(weight_kernel<double>, dim3(S.vg_n), dim3(kOnThreads), st, P->n, h->rowfac, nullptr, h->p);
   launch_k(weight_kernel<T>, dim3(S.vg_n), dim3(kOnThreads), st, P->n, h->rowfac, h->p, S.xw0());
   S.set_scalar(SC_RZ, 1.0);
+  if (!S.points) {
+    // the dense CG kernels read the update kernel's partials: start them as cg_init does
+    launch_k(cg_init_fused_kernel<T>, dim3(S.vg_n), dim3(kOnThreads), st, P->n, (const double*)h->rP,
+             (const double*)h->rPs, (const double*)h->rt, (const double*)h->diag, (const double*)h->rowfac, h->M,
+             h->x, h->res, h->z, h->p, h->Yx, S.xw0(), h->sc, h->cgpart, (cudaGraphConditionalHandle)0);
+    EOT_LAUNCH_CHECK();
+  }
   EOT_LAUNCH_CHECK();
   if (kind == 2 && S.points) throw EotError{EOT_ERR_UNSUPPORTED, "kind 2 (fused HVP sweep) needs a dense cost"};
   if (kind == 2) {
@@ -358,10 +365,18 @@ double run_sweep_bench(eot_handle h, const eot_problem* P, const double* u, cons
     }
     if (kind == 0) {
       a.wr[0] = S.xw0();
-      S.template col<1, false, 0>(a, CgColEpi<T>{h->colfac, h->cP, S.zf()});
+      if (S.points)
+        S.template col<1, false, 0>(a, CgColEpi<T>{h->colfac, h->cP, S.zf()});
+      else
+        S.template launch_col_dense<1, false>(st, a, CgColFusedEpi<T>{h->colfac, h->cP, S.zf(), h->wprev, h->cgpart,
+                                                                       S.vg_n, h->sc, h->status,
+                                                                       (cudaGraphConditionalHandle)0, 0.0, false, 0});
     } else if (kind == 1) {
       a.wc[0] = S.zf();
-      S.template row<1, false, 0>(a, CgRowEpi{h->rowfac, h->rPs, h->p, h->y, h->q, h->sc, h->status});
+      if (S.points)
+        S.template row<1, false, 0>(a, CgRowEpi{h->rowfac, h->rPs, h->p, h->y, h->q, h->sc, h->status});
+      else
+        S.template launch_row_dense<1, false, 0>(st, a, CgRowFusedEpi{h->rowfac, h->rPs, h->z, h->p, h->y, h->q, h->sc});
     } else if (kind == 2) {
       a.wr[0] = S.xw0();
       a.wr[1] = S.xw1();

@@ -17,6 +17,8 @@
 // plain sum; the running max lives on the 1/8 grid so that (Ah - max) stays
 // exact and t - max is rounded once, relative to its own (small) magnitude.
 #pragma once
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace eot {
@@ -54,6 +56,22 @@ struct DotArr {
   double v[N > 0 ? N : 1];
 };
 
+// Epilogue traits. kNoTicket: the sweep only writes one partial per CTA of its
+// epilogue sums (the next kernel reduces them itself, in fixed order, so no CTA
+// waits on a grid-wide ticket). kPrefetch (column sweeps): every CTA calls
+// epi.begin(first column, strip width, m) after the dependency wait and
+// epi.drain() before its ticket, and a
+// CTA that finishes a strip calls epi.prepare(publish) before its epilogue
+// (publish: strip 0).
+template <class E, class = void>
+struct NoTicket : std::false_type {};
+template <class E>
+struct NoTicket<E, std::void_t<decltype(E::kNoTicket)>> : std::bool_constant<E::kNoTicket> {};
+template <class E, class = void>
+struct HasPrefetch : std::false_type {};
+template <class E>
+struct HasPrefetch<E, std::void_t<decltype(E::kPrefetch)>> : std::bool_constant<E::kPrefetch> {};
+
 // ----------------------------------------------------------------------------
 // CTA-level deterministic sum of per-warp epilogue contributions, then a ticket
 // so that the last CTA calls epi.finish with the totals over all CTAs.
@@ -78,9 +96,12 @@ __device__ __forceinline__ void cta_dot_finish(double (&wd)[ND > 0 ? ND : 1], in
         for (int w = 0; w < NW; ++w) t += sd[w][k];
         dotpart[part_idx * 2 + k] = t;
       }
-      __threadfence();
-      last = (atomicAdd(cnt, 1) == (int)nparts - 1);
+      if constexpr (!NoTicket<Epi>::value) {
+        __threadfence();
+        last = (atomicAdd(cnt, 1) == (int)nparts - 1);
+      }
     }
+    if constexpr (NoTicket<Epi>::value) return;
     __syncthreads();
     if (last) {
       // all threads of the last CTA add the partials: fixed assignment and a
@@ -163,28 +184,28 @@ __device__ __forceinline__ void col_combine_f32(const float2* cp2, int R, int64_
 #pragma unroll
     for (int k = 0; k < NC; ++k) {
       float s0 = 0.f, c0 = 0.f;
-      for (int r = 0; r < R; ++r) {
-        const float2 q = __ldcg(cp2 + ((int64_t)k * R + r) * m + jj);
+      ordered_loads(cp2 + (int64_t)k * R * m + jj, m, R, [&](float2 q) {
         kadd(s0, c0, q.x);
         c0 += q.y;
-      }
+      });
       s[k] = (double)s0 + (double)c0;
     }
     epi.col(jj, s, dv);
   } else {
+    // slot 0 holds the (max, 0) pairs, slot 1 the compensated sums
+    const float2* mx = cp2 + jj;
+    const float2* sm = cp2 + (int64_t)R * m + jj;
     float M = -INFINITY;
-    for (int r = 0; r < R; ++r) {
-      const float2 qs = __ldcg(cp2 + ((int64_t)R + r) * m + jj);
-      if (qs.x != 0.f || qs.y != 0.f) M = fmaxf(M, __ldcg(cp2 + (int64_t)r * m + jj).x);
-    }
+    ordered_loads2(mx, sm, m, R, [&](float2 qm, float2 qs) {
+      if (qs.x != 0.f || qs.y != 0.f) M = fmaxf(M, qm.x);
+    });
     float s0 = 0.f, c0 = 0.f;
-    for (int r = 0; r < R; ++r) {
-      const float2 qs = __ldcg(cp2 + ((int64_t)R + r) * m + jj);
-      if (qs.x == 0.f && qs.y == 0.f) continue;
-      const float f = expT(__ldcg(cp2 + (int64_t)r * m + jj).x - M);
+    ordered_loads2(mx, sm, m, R, [&](float2 qm, float2 qs) {
+      if (qs.x == 0.f && qs.y == 0.f) return;
+      const float f = expT(qm.x - M);
       kadd(s0, c0, qs.x * f);
       c0 += qs.y * f;
-    }
+    });
     epi.col_lse(jj, (double)M, (double)s0 + (double)c0, dv);
   }
 }
@@ -424,6 +445,7 @@ __global__ void __launch_bounds__(kThreads, kColCtasPerSm) col_sweep_kernel(Swee
   }
   pdl_wait();
   if (a.active && *a.active == 0.0) return;
+  if constexpr (HasPrefetch<Epi>::value) epi.begin(strip * SW, SW, a.m);
   const T g = a.gamma_dev ? (T)*a.gamma_dev : a.gamma;
 
   T b[V], wcv[2][V];
@@ -645,6 +667,7 @@ __global__ void __launch_bounds__(kThreads, kColCtasPerSm) col_sweep_kernel(Swee
 
   // ---- tickets: the last CTA of the strip combines the R partials ----
   __shared__ int last_strip, last_rows;
+  if constexpr (HasPrefetch<Epi>::value) epi.drain();
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
@@ -654,6 +677,7 @@ __global__ void __launch_bounds__(kThreads, kColCtasPerSm) col_sweep_kernel(Swee
   __syncthreads();
   if (last_strip) {
     __threadfence();
+    if constexpr (HasPrefetch<Epi>::value) epi.prepare(strip == 0);
     double wd[ND > 0 ? ND : 1];
 #pragma unroll
     for (int k = 0; k < (ND > 0 ? ND : 1); ++k) wd[k] = 0.0;
@@ -668,15 +692,14 @@ __global__ void __launch_bounds__(kThreads, kColCtasPerSm) col_sweep_kernel(Swee
 #pragma unroll
         for (int k = 0; k < NC; ++k) {
           double t = 0.0;
-          for (int r = 0; r < R; ++r) t += __ldcg(a.colpart + ((int64_t)k * R + r) * a.m + jj);
+          ordered_loads(a.colpart + (int64_t)k * R * a.m + jj, a.m, R, [&](double q) { t += q; });
           s[k] = t;
         }
         epi.col(jj, s, d.v);
       } else {
         LsePair p{0.0, 0.0};
-        for (int r = 0; r < R; ++r)
-          p = lse_combine<T>(p, LsePair{__ldcg(a.colpart + (int64_t)r * a.m + jj),
-                                        __ldcg(a.colpart + ((int64_t)R + r) * a.m + jj)});
+        ordered_loads2(a.colpart + jj, a.colpart + (int64_t)R * a.m + jj, a.m, R,
+                       [&](double qm, double qs) { p = lse_combine<T>(p, LsePair{qm, qs}); });
         epi.col_lse(jj, p.m, p.s, d.v);
       }
 #pragma unroll
@@ -698,7 +721,7 @@ __global__ void __launch_bounds__(kThreads, kColCtasPerSm) col_sweep_kernel(Swee
 #pragma unroll
         for (int k = 0; k < NR; ++k) {
           double t = 0.0;
-          for (int64_t q = 0; q < S; ++q) t += __ldcg(a.rowpart + ((int64_t)k * S + q) * a.n + i);
+          ordered_loads(a.rowpart + (int64_t)k * S * a.n + i, a.n, S, [&](double q) { t += q; });
           s[k] = t;
         }
         epi.row_part(i, s);

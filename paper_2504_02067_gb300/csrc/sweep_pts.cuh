@@ -235,16 +235,15 @@ __global__ void __launch_bounds__(kThreads, 2) pts_sweep_kernel(SweepArgs<T> a, 
 #pragma unroll
       for (int k = 0; k < NR; ++k) {
         double v = 0.0;
-        for (int64_t q = 0; q < S; ++q) v += __ldcg(a.rowpart + ((int64_t)k * S + q) * n_own + e[r]);
+        ordered_loads(a.rowpart + (int64_t)k * S * n_own + e[r], n_own, S, [&](double q) { v += q; });
         tot[k] = v;
       }
       if constexpr (ROWS) epi.row(e[r], tot, dd.v);
       else epi.col(e[r], tot, dd.v);
     } else {
       LsePair p{0.0, 0.0};
-      for (int64_t q = 0; q < S; ++q)
-        p = lse_combine<T>(p, LsePair{__ldcg(a.rowpart + q * n_own + e[r]),
-                                      __ldcg(a.rowpart + (S + q) * n_own + e[r])});
+      ordered_loads2(a.rowpart + e[r], a.rowpart + S * n_own + e[r], n_own, S,
+                     [&](double qm, double qs) { p = lse_combine<T>(p, LsePair{qm, qs}); });
       if constexpr (ROWS) epi.row_lse(e[r], p.m, p.s, dd.v);
       else epi.col_lse(e[r], p.m, p.s, dd.v);
     }
@@ -349,7 +348,7 @@ __global__ void __launch_bounds__(kThreads, DMAX > 16 ? 1 : 2)
     for (int k = 0; k < DG; ++k) {
       if (k0 + k >= d) break;
       double v = 0.0;
-      for (int64_t q = 0; q < S; ++q) v += __ldcg(a.rowpart + ((int64_t)k * S + q) * n_own + e);
+      ordered_loads(a.rowpart + (int64_t)k * S * n_own + e, n_own, S, [&](double q) { v += q; });
       out[e * d + k0 + k] = (float)(f * v);
     }
   }

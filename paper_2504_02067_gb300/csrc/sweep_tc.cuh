@@ -408,16 +408,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_sweep_kernel(SweepArgs<float
 #pragma unroll
         for (int k = 0; k < NR; ++k) {
           double v = 0.0;
-          for (int64_t qq = 0; qq < S; ++qq) v += __ldcg(a.rowpart + ((int64_t)k * S + qq) * n_own + ee);
+          ordered_loads(a.rowpart + (int64_t)k * S * n_own + ee, n_own, S, [&](double q) { v += q; });
           tot[k] = v;
         }
         if constexpr (ROWS) epi.row(ee, tot, dd.v);
         else epi.col(ee, tot, dd.v);
       } else {
         LsePair p{0.0, 0.0};
-        for (int64_t qq = 0; qq < S; ++qq)
-          p = lse_combine<float>(p, LsePair{__ldcg(a.rowpart + qq * n_own + ee),
-                                            __ldcg(a.rowpart + (S + qq) * n_own + ee)});
+        ordered_loads2(a.rowpart + ee, a.rowpart + S * n_own + ee, n_own, S,
+                       [&](double qm, double qs) { p = lse_combine<float>(p, LsePair{qm, qs}); });
         if constexpr (ROWS) epi.row_lse(ee, p.m, p.s, dd.v);
         else epi.col_lse(ee, p.m, p.s, dd.v);
       }
