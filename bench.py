@@ -40,6 +40,13 @@ WORKLOAD = "grid64x64_sqeuclid_f32_n4096_gamma2^14"
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 
 
+def bench_config(args, world):
+    """The workload both arms report on (identical keys in both lines)."""
+    return {"workload": WORKLOAD, "n": N, "m": N, "gamma_i": GAMMA_I, "gamma_f": GAMMA_F, "tol": TOL,
+            "cost": args.cost, "parallelism": "replicas" if world > 1 else "single",
+            "l2": "flushed between steps (512 MiB write)"}
+
+
 def env_rank():
     return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
             int(os.environ.get("LOCAL_RANK", 0)))
@@ -49,11 +56,28 @@ def env_rank():
 # CPU baseline: the FP64 oracle as it stands, timed on a bounded sample
 # ---------------------------------------------------------------------------
 
-def cpu_sample(seconds=12.0):
-    """Times the oracle's two primitive costs on the full-size workload with one
-    thread: one O(n^2) log-sum-exp sweep (plan formation + reduction, as in every
-    oracle LSE update) and one CG step on a stored plan (two matrix-vector products,
-    as in the oracle's NewtonSolve). Returns seconds per op."""
+def oracle_ops_of_workload():
+    """The oracle's own operation counts on this workload, from its recorded run
+    (tests/golden/grid4096_oracle_trace.json, written by calling oracle/ only). In
+    the oracle every stage makes a column and a row LSE update, every Newton step
+    forms the plan once and makes a row LSE update, every line-search trial a
+    column LSE, every ChiSinkhorn iteration two LSE updates; the outer tests of
+    NewtonSolve and d_v are matrix-vector products on the stored plan, as are the
+    CG steps."""
+    tr = json.load(open(os.path.join(ROOT, "tests", "golden", "grid4096_oracle_trace.json")))
+    t = tr["sqeuclid"]
+    lse_like = 2 * t["stages"] + 2 * t["newton_steps"] + t["ls_trials"] + 2 * t["sinkhorn_iters"]
+    cg_like = t["cg_iters"] + 2 * t["newton_steps"]
+    return {"lse_like": lse_like, "cg_like": cg_like, "recorded_seconds": t.get("oracle_seconds"),
+            "source": "tests/golden/grid4096_oracle_trace.json"}
+
+
+def oracle_sample(seconds):
+    """Times the oracle's two primitive operations on the full-size workload with
+    numpy's default threading (BLAS on every host core; numpy's elementwise exp
+    is single-threaded): one O(n^2) log-sum-exp update (plan formation and a
+    reduction, as in each of the oracle's LSE updates) and one CG step on a stored
+    plan (F_r(rho) applied: two matrix-vector products). Returns seconds per op."""
     import numpy as np
 
     import workloads as W
@@ -78,27 +102,39 @@ def cpu_sample(seconds=12.0):
         O.F_r_apply(P, 0.9, x)
         k_cg += 1
     t_cg = (time.perf_counter() - t1) / k_cg
-    return {"t_lse": t_lse, "t_cg": t_cg, "k_lse": k_lse, "k_cg": k_cg}
+    return {"t_lse": t_lse, "t_cg": t_cg, "k_lse": k_lse, "k_cg": k_cg,
+            "wall": time.perf_counter() - t0}
 
 
-def run_cpu_sample_subprocess(seconds=12.0):
-    """Runs cpu_sample in a child process pinned to one BLAS/OpenMP thread."""
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    code = ("import json, sys; sys.path.insert(0, %r); import bench; "
-            "print(json.dumps(bench.cpu_sample(%r)))" % (ROOT, seconds))
-    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
-                         timeout=600)
-    if out.returncode != 0:
-        raise RuntimeError(out.stderr[-2000:])
-    return json.loads(out.stdout.strip().splitlines()[-1])
+def oracle_estimate(sample, ops):
+    """The oracle's time for one solve of the workload: its recorded operation
+    counts priced at the sampled per-operation times."""
+    return ops["lse_like"] * sample["t_lse"] + ops["cg_like"] * sample["t_cg"]
 
 
-def oracle_solve_seconds(sample, ops):
-    """Oracle time for a solve with the given op counts: every sweep outside CG is
-    a plan formation + reduction in the oracle; every CG iteration is two
-    matrix-vector products on the stored plan."""
-    other = ops["sweeps_total"] - ops["sweeps_cg"]
-    return other * sample["t_lse"] + ops["cg_iters"] * sample["t_cg"]
+def cpu_cores():
+    return os.cpu_count() or 1
+
+
+def cpu_sample_text(sample, ops):
+    return ("oracle log_row_sum x%d (%.4f s each) and F_r_apply x%d (%.5f s each) at n = 4096, "
+            "BLAS on %d host threads; one solve = the oracle's recorded %d LSE updates and %d "
+            "CG-step products (%s) at those times"
+            % (sample["k_lse"], sample["t_lse"], sample["k_cg"], sample["t_cg"], cpu_cores(),
+               ops["lse_like"], ops["cg_like"], ops["source"]))
+
+
+def oracle_full_solve_seconds():
+    """One complete oracle solve of the workload (measured, not estimated)."""
+    import numpy as np
+
+    import workloads as W
+    from oracle import eot_oracle as O
+    p = W.grid_problem_4096(0, "sqeuclid")
+    C = p["C"].astype(np.float64)
+    t0 = time.perf_counter()
+    res = O.mdot(C, p["r"], p["c"], gamma_i=GAMMA_I, gamma_f=GAMMA_F, tol_final=TOL)
+    return time.perf_counter() - t0, res
 
 
 # ---------------------------------------------------------------------------
@@ -225,6 +261,186 @@ def roofline_at_scale(h, E, dev, flush, peak, side=128):
     return out
 
 
+# ---------------------------------------------------------------------------
+# sub-records of the other workloads (driver-visible: they ride on the default
+# run's JSON line; each takes seconds)
+# ---------------------------------------------------------------------------
+
+MUFU_PER_CLK_SM = 16     # ex2 results per clock per SM (4 per SM sub-partition)
+FP32_LANES_SM = 128      # FP32 lanes per SM
+SM_MAX_GHZ = 2.07
+
+
+def _event_time(fn, stream=None):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    out = fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / 1e3, out
+
+
+def _solve_record(h, E, prob, prm, n, m, warm=1, reps=1):
+    import torch
+    u = torch.empty(n, dtype=torch.float64, device="cuda")
+    v = torch.empty(m, dtype=torch.float64, device="cuda")
+    for _ in range(warm):
+        h.eot_solve(prob, prm, u, v)
+    ts = []
+    for _ in range(reps):
+        t, st = _event_time(lambda: h.eot_solve(prob, prm, u, v).as_dict())
+        ts.append(t)
+    sec = statistics.mean(ts)
+    return {"seconds": round(sec, 5), "marg_err_l1": st["marg_err_l1"], "reached_tol": st["marg_err_l1"] <= TOL,
+            "stages": st["stages"], "newton_steps": st["newton_steps"], "cg_iters": st["cg_iters"],
+            "sweeps_total": st["sweeps_total"],
+            "p_entries_per_s": round(st["sweeps_total"] * n * m / sec, 1)}, u, v
+
+
+def record_cfg1_fp64(E, dev):
+    """28 x 28 grid (n = m = 784), 3-Gaussian histograms, squared-Euclidean cost,
+    FP64 throughout (the paper's precision), gamma 2^4 -> 2^12, tol 1e-6."""
+    import torch
+    import workloads as W
+    p = W.grid_problem_784(0)
+    h = E.Handle(0, 784, 784)
+    try:
+        prob = E.Problem(torch.from_numpy(p["C"]).to(dev), torch.from_numpy(p["r"]).to(dev),
+                         torch.from_numpy(p["c"]).to(dev), precision="fp64")
+        prm = E.default_params(gamma_i=16.0, gamma_f=4096.0, tol_final=TOL)
+        rec, _, _ = _solve_record(h, E, prob, prm, 784, 784, warm=1, reps=3)
+    finally:
+        h.close()
+    rec["workload"] = "grid28x28_sqeuclid_f64_n784_gamma2^12"
+    return rec
+
+
+def record_cfg2_breadth(E, dev):
+    """The 64 x 64 grid workload with both costs (squared Euclidean and L1) and
+    seeds 0, 1, 2, mixed precision, gamma 2^4 -> 2^14, tol 1e-6."""
+    import torch
+    import workloads as W
+    h = E.Handle(0, N, N)
+    out = []
+    try:
+        prm = E.default_params(gamma_i=GAMMA_I, gamma_f=GAMMA_F, tol_final=TOL)
+        for kind in ("sqeuclid", "l1"):
+            for seed in (0, 1, 2):
+                p = W.grid_problem_4096(seed, kind)
+                prob = E.Problem(torch.from_numpy(p["C"]).to(dev), torch.from_numpy(p["r"]).to(dev),
+                                 torch.from_numpy(p["c"]).to(dev), precision="mixed")
+                rec, _, _ = _solve_record(h, E, prob, prm, N, N, warm=1, reps=1)
+                rec.update({"cost": kind, "seed": seed})
+                out.append(rec)
+    finally:
+        h.close()
+    return {"workload": "grid64x64_f32_n4096_gamma2^14 (3 seeds x 2 costs)", "solves": out,
+            "all_reached": all(r["reached_tol"] for r in out)}
+
+
+def record_d64(E, dev, peaks):
+    """n = m = 16384 points in d = 64 (8-component mixtures), gamma 2^4 -> 2^10,
+    tol 1e-6: the mixed path (tensor-core sweeps) against the plain FP32 comparator
+    on the same points. The comparator runs with max_newton = 10 per stage (a
+    bound on the benchmark's wall time); when a cap stops it, its floor is the
+    marginal L1 error of the last iterate, evaluated by eot_marginals on the mixed
+    path (accurate to about 1e-7)."""
+    import numpy as np
+    import torch
+    import workloads as W
+    p = W.gmm_problem_d64(0)
+    n = p["X"].shape[0]
+    X, Y = torch.from_numpy(p["X"]).to(dev), torch.from_numpy(p["Y"]).to(dev)
+    r, c = torch.from_numpy(p["r"]).to(dev), torch.from_numpy(p["c"]).to(dev)
+    gf = 1024.0
+    h = E.Handle(0, n, n, 64)
+    out = {"workload": "gmm8_d64_n16384_gamma2^10", "n": n, "d": 64, "gamma_f": gf, "tol": TOL}
+    try:
+        prob = E.Problem(X=X, Y=Y, r=r, c=c, precision="mixed", cost_scale=0.0)
+        prm = E.default_params(gamma_i=16.0, gamma_f=gf, tol_final=TOL)
+        mixed, u, v = _solve_record(h, E, prob, prm, n, n, warm=1, reps=2)
+        out["mixed"] = mixed
+        # sweep rates of the tensor-core kernels at the solution
+        rates = {}
+        for kind, name in ((0, "cg_col_sweep"), (1, "cg_row_sweep"), (3, "row_lse_sweep")):
+            ms = h.eot_sweep_bench(prob, u, v, gf, kind, 5)
+            rates[name] = {"ms": round(ms, 4), "p_entries_per_s": round(n * n / (ms * 1e-3), 1)}
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        bf16 = (peaks or {}).get("bf16_tflops", 1900.0) * 1e12
+        flop_per_entry = 15 * 2 * 64           # 15 digit-slice BF16 MMAs of K = 64 per entry
+        fp32_issue = sms * FP32_LANES_SM * SM_MAX_GHZ * 1e9
+        ex2 = sms * MUFU_PER_CLK_SM * SM_MAX_GHZ * 1e9
+        best = max(rates["cg_col_sweep"]["p_entries_per_s"], rates["cg_row_sweep"]["p_entries_per_s"])
+        out["tc_sweeps"] = rates
+        out["tc_roofline"] = {
+            "bound": "alu", "kernel": "tc_sweep_kernel (CG halves)", "achieved_entries_per_s": best,
+            "peak_tensor_entries_per_s": round(bf16 / flop_per_entry, 1),
+            "peak_ex2_entries_per_s": round(ex2, 1),
+            "fp32_issue_per_s": round(fp32_issue, 1),
+            "frac_of_tensor": round(best / (bf16 / flop_per_entry), 4),
+            "frac_of_ex2": round(best / ex2, 4),
+            "peak_source": "tensor: measured bf16 burst (MEASURED_PEAKS.json) / %d flop per entry; ex2 and "
+                           "FP32 issue: %d SMs x %d ex2 / %d lanes per clock x %.2f GHz" %
+                           (flop_per_entry, sms, MUFU_PER_CLK_SM, FP32_LANES_SM, SM_MAX_GHZ)}
+        # the plain FP32 comparator on the same points
+        probp = E.Problem(X=X, Y=Y, r=r, c=c, precision="plain_fp32", cost_scale=0.0)
+        prmp = E.default_params(gamma_i=16.0, gamma_f=gf, tol_final=TOL, max_newton=10)
+        up = torch.empty(n, dtype=torch.float64, device=dev)
+        vp = torch.empty(n, dtype=torch.float64, device=dev)
+        t0 = time.perf_counter()
+        try:
+            stp = h.eot_solve(probp, prmp, up, vp).as_dict()
+            status = "EOT_OK"
+        except E.EotError as ex:
+            stp, status = getattr(ex, "stats", None), str(ex).split(":")[0]
+        torch.cuda.synchronize()
+        tp = time.perf_counter() - t0
+        g_last = stp["final_gamma"] if stp else float(np.float32(gf))
+        rr, cc, _, _, _ = h.marginals(prob, up, vp, g_last)
+        floor = float((rr - r).abs().sum() + (cc - c).abs().sum())
+        out["plain_fp32"] = {"status": status, "seconds": round(tp, 3), "stopped_at_gamma": g_last,
+                             "marg_err_l1_last_iterate": floor,
+                             "reached_tol": status == "EOT_OK" and floor <= TOL, "max_newton": 10,
+                             "stats": ({k: stp[k] for k in ("stages", "newton_steps", "cg_iters", "grad_l1")}
+                                       if stp else None)}
+        out["mixed_faster_to_1e-6"] = bool(mixed["reached_tol"] and not out["plain_fp32"]["reached_tol"])
+    finally:
+        h.close()
+    return out
+
+
+def record_batch256(E, dev):
+    """256 point problems (n = m uniform in [256, 4096], uniform points in the unit
+    square, Dirichlet(1) weights), gamma 2^4 -> 2^12, mixed, tol 1e-6, one
+    eot_solve_batched launch (autotuned on the first call)."""
+    import numpy as np
+    import torch
+    import workloads as W
+    sizes = W.batch_sizes(0)
+    ps = [W.uniform_points_problem(1000 + k, int(nk)) for k, nk in enumerate(sizes)]
+    devs = [{k: torch.from_numpy(p[k]).to(dev) for k in ("X", "Y", "r", "c")} for p in ps]
+    probs = [E.Problem(X=d["X"], Y=d["Y"], r=d["r"], c=d["c"], precision="mixed", cost_scale=0.0) for d in devs]
+    us = [torch.empty(int(nk), dtype=torch.float64, device=dev) for nk in sizes]
+    vs = [torch.empty(int(nk), dtype=torch.float64, device=dev) for nk in sizes]
+    h = E.Handle(0, 64, 64)
+    try:
+        prm = E.default_params(gamma_i=16.0, gamma_f=4096.0, tol_final=TOL)
+        t_first = time.perf_counter()
+        h.eot_solve_batched(probs, prm, us, vs)
+        t_first = time.perf_counter() - t_first
+        sec, (st, stats) = _event_time(lambda: h.eot_solve_batched(probs, prm, us, vs))
+        G, ro, groups = h.batch_last_config()
+    finally:
+        h.close()
+    entries = sum(sm["sweeps_total"] * int(nk) * int(nk) for sm, nk in zip(stats, sizes))
+    return {"workload": "batch256_uniform2d_n256-4096_gamma2^12", "seconds": round(sec, 4),
+            "all_ok": all(x == 0 for x in st), "max_marg_err_l1": max(sm["marg_err_l1"] for sm in stats),
+            "p_entries_per_s": round(entries / sec, 1), "first_call_incl_autotune_s": round(t_first, 3),
+            "sum_n2": int(np.sum(sizes.astype(np.int64) ** 2)),
+            "batch_config": {"ctas_per_group": G, "elements_per_thread": ro, "groups": groups}}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -329,6 +545,8 @@ def run_ours(args):
                 "at_scale": roofline_at_scale(h, E, dev, flush, peak)}
 
     # ---- plain FP32 comparator (same workload, same tolerance) ----
+    # When a cap stops it, eot_solve leaves its last iterate in (u, v): its marginal
+    # L1 error, evaluated on the mixed path (about 1e-7 accurate), is the floor.
     plain = None
     if not args.no_plain:
         prob_p = E.Problem(C, r, c, precision="plain_fp32")
@@ -336,12 +554,17 @@ def run_ours(args):
         t0 = time.perf_counter()
         try:
             stp = h.eot_solve(prob_p, prm, u, v).as_dict()
-            torch.cuda.synchronize()
-            plain = {"seconds": time.perf_counter() - t0, "marg_err_l1": stp["marg_err_l1"],
-                     "reached": stp["marg_err_l1"] <= TOL}
+            status = "EOT_OK"
         except E.EotError as ex:
-            torch.cuda.synchronize()
-            plain = {"seconds": time.perf_counter() - t0, "reached": False, "error": str(ex)[:160]}
+            stp, status = getattr(ex, "stats", None), str(ex)[:160]
+        torch.cuda.synchronize()
+        secs = time.perf_counter() - t0
+        g_last = stp["final_gamma"] if stp else GAMMA_F
+        rr, cc, _, _, _ = h.marginals(prob, u, v, g_last)
+        floor = float((rr - r).abs().sum() + (cc - c).abs().sum())
+        plain = {"seconds": round(secs, 3), "status": status, "stopped_at_gamma": g_last,
+                 "marg_err_l1_last_iterate": floor, "reached": status == "EOT_OK" and floor <= TOL,
+                 "note": "marginal L1 error of the last iterate at the temperature of the stage it stopped in"}
 
     # ---- Round (Alg. 1's closing step) of the last solve's plan ----
     h.eot_solve(prob, prm, u, v)
@@ -393,6 +616,18 @@ def run_ours(args):
                 "seconds": round(e0.elapsed_time(e1) / 1e3, 4), "reached_tol": False,
                 "error": str(ex)[:120]}
 
+    extra = {}
+    if not args.no_extra and world == 1:
+        for key, fn in (("cfg1_fp64", lambda: record_cfg1_fp64(E, dev)),
+                        ("cfg2_breadth", lambda: record_cfg2_breadth(E, dev)),
+                        ("d64", lambda: record_d64(E, dev, measured_peaks())),
+                        ("batch256", lambda: record_batch256(E, dev))):
+            try:
+                extra[key] = fn()
+            except Exception as ex:  # a sub-record never hides the headline line
+                extra[key] = {"error": str(ex)[:200]}
+            torch.cuda.empty_cache()
+
     result = None
     if rank == 0:
         # Table 1's shape (operations per subroutine) and Fig. 1's (delta_min and q per
@@ -415,23 +650,17 @@ def run_ours(args):
                                 for rc in last.get("stage_records", [])]}
         cpu = None
         if not args.no_cpu_baseline and world == 1:
-            s = run_cpu_sample_subprocess(args.cpu_seconds)
-            est = oracle_solve_seconds(s, last)
-            cpu = {"value": round(est, 3), "unit": "s", "cores": 1, "kind": "oracle",
-                   "sample": ("oracle log_row_sum x%d (%.3f s each) and F_r_apply x%d (%.4f s "
-                              "each) at n = 4096, one thread; solve time = %d non-CG sweeps x "
-                              "LSE + %d CG iterations x CG step, counts from this solve"
-                              % (s["k_lse"], s["t_lse"], s["k_cg"], s["t_cg"],
-                                 last["sweeps_total"] - last["sweeps_cg"], last["cg_iters"]))}
+            ops = oracle_ops_of_workload()
+            smp = oracle_sample(args.cpu_seconds)
+            cpu = {"value": round(oracle_estimate(smp, ops), 3), "unit": "s", "cores": cpu_cores(),
+                   "kind": "oracle", "sample": cpu_sample_text(smp, ops),
+                   "sample_wall_s": round(smp["wall"], 2)}
         result = {
             "metric": METRIC, "value": round(sec, 5), "unit": "s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(sec * 1e3, 3),
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 exp/sums on f64 potentials (mixed)", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": N, "m": N, "gamma_i": GAMMA_I,
-                       "gamma_f": GAMMA_F, "tol": TOL, "cost": args.cost,
-                       "parallelism": "replicas" if world > 1 else "single",
-                       "l2": "flushed between steps (512 MiB write)"},
+            "config": bench_config(args, world),
             "marg_err_l1": last["marg_err_l1"], "reached_tol": last["marg_err_l1"] <= TOL,
             "p_entries_per_s": round(p_entries_per_s, 1), "sweeps_per_solve": sweeps,
             "solve_stats": {k: last[k] for k in ("stages", "newton_steps", "cg_iters", "cg_solves",
@@ -443,6 +672,7 @@ def run_ours(args):
             "op_breakdown": op_breakdown, "stage_trace": stage_trace,
             "gpu_launches": int(launches), "roofline": roofline, "cpu_baseline": cpu,
             "plain_fp32": plain, "rounded": rounded, "mdot_sinkhorn": mdot_sk, "clocks": clocks,
+            **extra,
         }
         print(json.dumps(result), flush=True)
     h.close()
@@ -455,43 +685,43 @@ def run_ours(args):
 # reference arm: the oracle on the host cores
 # ---------------------------------------------------------------------------
 
-def oracle_ops_of_workload():
-    """The oracle's own operation counts on this workload, from its recorded run
-    (tests/golden/grid4096_oracle_trace.json). In the oracle every stage makes a
-    column and a row LSE update, every Newton step forms the plan once and makes a
-    row LSE update, every line-search trial a column LSE, every ChiSinkhorn
-    iteration two LSE updates; the outer tests of NewtonSolve and d_v are
-    matrix-vector products on the stored plan, as are the CG steps."""
-    tr = json.load(open(os.path.join(ROOT, "tests", "golden", "grid4096_oracle_trace.json")))
-    t = tr["sqeuclid"]
-    lse_like = 2 * t["stages"] + 2 * t["newton_steps"] + t["ls_trials"] + 2 * t["sinkhorn_iters"]
-    cg_like = t["cg_iters"] + 2 * t["newton_steps"]
-    return {"sweeps_total": lse_like + cg_like, "sweeps_cg": cg_like, "cg_iters": cg_like,
-            "source": "tests/golden/grid4096_oracle_trace.json"}
-
-
 def run_reference(args):
+    """The reference arm: the oracle (the paper ships no code), as it stands, on the
+    host cores. Each step is one bounded sample of the workload (the oracle's LSE
+    update and CG step timed for --cpu-seconds / 2 s each, as in the GPU arm's
+    cpu_baseline); value = the oracle's time for one whole solve, its recorded
+    operation counts priced at the step's per-operation times, averaged over the
+    timed steps. ms_per_step is the wall time of one sample step. With --cpu-full
+    each step is instead one complete oracle solve (about two minutes)."""
     rank, world, _ = env_rank()
     if rank != 0:
         return None
     ops = oracle_ops_of_workload()
     per = max(2.0, args.cpu_seconds / 2)
-    vals = []
+    vals, walls, last = [], [], None
     for k in range(args.warmup + args.steps):
-        s = run_cpu_sample_subprocess(per)
+        t0 = time.perf_counter()
+        if args.cpu_full:
+            sec, _ = oracle_full_solve_seconds()
+            est = sec
+        else:
+            last = oracle_sample(per)
+            est = oracle_estimate(last, ops)
         if k >= args.warmup:
-            vals.append(oracle_solve_seconds(s, ops))
+            vals.append(est)
+            walls.append(time.perf_counter() - t0)
     v = statistics.mean(vals)
+    sample = ("per step: one complete oracle solve" if args.cpu_full else cpu_sample_text(last, ops))
     out = {"impl": "reference", "metric": METRIC, "value": round(v, 3), "unit": "s",
            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-           "ms_per_step": round(v * 1e3, 1), "higher_is_better": False, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "n": N, "m": N, "gamma_i": GAMMA_I,
-                      "gamma_f": GAMMA_F, "tol": TOL, "cost": args.cost},
-           "cpu_baseline": {"value": round(v, 3), "unit": "s", "cores": 1, "kind": "oracle",
-                            "sample": "per step: oracle LSE sweep and CG step timed for %.0f s at "
-                                      "n = 4096, scaled by the oracle's own op counts of this "
-                                      "workload (%s)" % (per, ops.get("source", ""))},
+           "ms_per_step": round(1e3 * statistics.mean(walls), 1), "higher_is_better": False,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": bench_config(args, world),
+           "value_is": ("mean measured oracle solve time" if args.cpu_full else
+                        "oracle solve time estimated per step from a bounded sample; ms_per_step is "
+                        "the sample's wall time"),
+           "cpu_baseline": {"value": round(v, 3), "unit": "s", "cores": cpu_cores(), "kind": "oracle",
+                            "sample": sample},
            "e2e": {"value": round(v, 3), "unit": "s", "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -501,9 +731,6 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # further workloads (parity-test configurations; each prints its own JSON line)
 # ---------------------------------------------------------------------------
-
-MUFU_PER_CLK_SM = 16     # ex2 results per clock per SM (4 per SM sub-partition)
-FP32_LANES_SM = 128      # FP32 lanes per SM
 
 
 def _gpu_props(dev):
@@ -749,8 +976,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cost", default="sqeuclid", choices=["sqeuclid", "l1"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--cpu-full", action="store_true",
+                    help="--impl reference: each step is one complete oracle solve (about two minutes)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the sub-records of the other workloads (config 1, config 2 breadth, d = 64, batch)")
     ap.add_argument("--no-sinkhorn", action="store_true",
                     help="skip the MDOT-Sinkhorn comparison solve on the headline workload")
     ap.add_argument("--profile-sweep", type=int, default=-1,

@@ -206,7 +206,9 @@ eot_status eot_round(eot_handle h, const eot_problem* prob, const double* u, con
  * u: device [n], v: device [m]: outputs (the last projected potentials at gamma_f).
  * When a cap (CG_MAXITER, LINESEARCH, MAXNEWTON, MAXSTAGES), a non-finite value
  * or the split range stops the solve, u and v still receive the last iterate (of
- * the stage in progress), which does not meet the requested tolerance.
+ * the stage in progress), which does not meet the requested tolerance, and stats
+ * (when given) the work done so far, with final_gamma = the temperature of that
+ * stage, grad_l1 = its last ||r~ - r(P)||_1 and marg_err_l1 = NaN.
  * stats: host, nullable; with stats->stage_records set (and stats->stage_records_cap
  * > 0) one eot_stage_record per stage of Alg. 1 is written there. Errors: any.
  * Synchronises. */

@@ -252,8 +252,12 @@ class Handle:
             stats._records = (EotStageRecord * stage_records)()  # kept alive with stats
             stats.stage_records = ctypes.cast(stats._records, ctypes.POINTER(EotStageRecord))
             stats.stage_records_cap = stage_records
-        self.check(self.lib.eot_solve(self.h, prob.ref(), ctypes.byref(params), _p(u), _p(v),
-                                      ctypes.byref(stats), _stream(stream)))
+        st = self.lib.eot_solve(self.h, prob.ref(), ctypes.byref(params), _p(u), _p(v),
+                                ctypes.byref(stats), _stream(stream))
+        if st != EOT_OK:
+            err = EotError(st, self.lib.eot_last_error(self.h).decode())
+            err.stats = stats.as_dict()  # the work done before the error (see include/eot.h)
+            raise err
         return stats
 
     def eot_backward(self, prob, u, v, gamma, grad_scale=1.0, dC=None, dX=None, dY=None,

@@ -202,6 +202,31 @@ void run_solve(eot_handle h, const eot_problem* P, const eot_params* prm_in, dou
     gamma = gamma_f;
     t = 0;
   }
+  // stats of the call; s == nullptr: stopped by an error (marg_err_l1 = NaN,
+  // final_gamma = the stage in progress)
+  auto fill_stats = [&](const double* s) {
+    if (!stats) return;
+    const SolveCounters& c = S.cnt;
+    stats->sweeps_cg = c.sweeps_cg;
+    stats->sweeps_newton = c.sweeps_newton;
+    stats->sweeps_linesearch = c.sweeps_ls;
+    stats->sweeps_sinkhorn = c.sweeps_sk;
+    stats->sweeps_total = c.sweeps_cg + c.sweeps_newton + c.sweeps_ls + c.sweeps_sk + c.sweeps_stage + c.sweeps_other;
+    stats->sweeps_stage = c.sweeps_stage;
+    stats->stage_records_len = stats->stage_records ? std::min<int32_t>(s ? t : t - 1, stats->stage_records_cap) : 0;
+    stats->stages = t;
+    stats->newton_steps = (int32_t)c.newton_steps;
+    stats->cg_iters = (int32_t)c.cg_iters;
+    stats->cg_solves = (int32_t)c.cg_solves;
+    stats->ls_trials = (int32_t)c.ls_trials;
+    stats->sinkhorn_iters = (int32_t)c.sk_iters;
+    stats->curvature_stops = (int32_t)c.curvature_stops;
+    stats->final_gamma = gamma;
+    stats->final_rho = s ? s[SC_RHOLAST] : h->h_sc[SC_RHOLAST];
+    stats->grad_l1 = s ? gl1 : h->h_sc[SC_GL1];
+    stats->marg_err_l1 = s ? s[SC_GL1] + s[SC_AUX1] : NAN;
+    stats->seconds = wall_now() - t0;
+  };
   try {
     for (; t > 0;) {
       const bool done = gamma == gamma_f;
@@ -262,11 +287,13 @@ void run_solve(eot_handle h, const eot_problem* P, const eot_params* prm_in, dou
     }
   } catch (const EotError& e) {
     // a cap or a non-finite value stopped Alg. 1: the caller still gets the last
-    // iterate (the stage in progress), e.g. to measure the error it reached
+    // iterate (the stage in progress) and the work done so far, e.g. to measure
+    // the error it reached at that stage's temperature
     if (e.st != EOT_ERR_CUDA && e.st != EOT_ERR_DEVICE_TIMEOUT) {
       S.copy(u, U, n);
       S.copy(v, V, m);
       cudaStreamSynchronize(st);
+      fill_stats(nullptr);
     }
     throw;
   }
@@ -285,29 +312,7 @@ void run_solve(eot_handle h, const eot_problem* P, const eot_params* prm_in, dou
   EOT_LAUNCH_CHECK();
   h->launches += 2;
   S.release_cost();
-  const double* s = S.read();
-  if (stats) {
-    const SolveCounters& c = S.cnt;
-    stats->sweeps_cg = c.sweeps_cg;
-    stats->sweeps_newton = c.sweeps_newton;
-    stats->sweeps_linesearch = c.sweeps_ls;
-    stats->sweeps_sinkhorn = c.sweeps_sk;
-    stats->sweeps_total = c.sweeps_cg + c.sweeps_newton + c.sweeps_ls + c.sweeps_sk + c.sweeps_stage + c.sweeps_other;
-    stats->sweeps_stage = c.sweeps_stage;
-    stats->stage_records_len = stats->stage_records ? std::min<int32_t>(t, stats->stage_records_cap) : 0;
-    stats->stages = t;
-    stats->newton_steps = (int32_t)c.newton_steps;
-    stats->cg_iters = (int32_t)c.cg_iters;
-    stats->cg_solves = (int32_t)c.cg_solves;
-    stats->ls_trials = (int32_t)c.ls_trials;
-    stats->sinkhorn_iters = (int32_t)c.sk_iters;
-    stats->curvature_stops = (int32_t)c.curvature_stops;
-    stats->final_gamma = gamma;
-    stats->final_rho = s[SC_RHOLAST];
-    stats->grad_l1 = gl1;
-    stats->marg_err_l1 = s[SC_GL1] + s[SC_AUX1];
-    stats->seconds = wall_now() - t0;
-  }
+  fill_stats(S.read());
 }
 
 template <class T>

@@ -34,6 +34,9 @@ def test_reference_arm_uses_the_recorded_oracle_trace():
     ops = bench.oracle_ops_of_workload()
     # priced as CG steps: the recorded CG iterations plus Alg. 2's two outer
     # products per Newton step; everything else as LSE updates
-    assert ops["cg_iters"] == t["cg_iters"] + 2 * t["newton_steps"]
-    assert ops["sweeps_total"] - ops["sweeps_cg"] >= 2 * t["stages"] + 2 * t["newton_steps"] + t["ls_trials"]
+    assert ops["cg_like"] == t["cg_iters"] + 2 * t["newton_steps"]
+    assert ops["lse_like"] == 2 * t["stages"] + 2 * t["newton_steps"] + t["ls_trials"] + 2 * t["sinkhorn_iters"]
     assert t["cg_iters"] > 0 and t["stages"] > 0
+    # the estimate prices those counts at the sampled per-operation times
+    est = bench.oracle_estimate({"t_lse": 2.0, "t_cg": 0.5}, ops)
+    assert est == 2.0 * ops["lse_like"] + 0.5 * ops["cg_like"]

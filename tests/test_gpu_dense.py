@@ -372,8 +372,9 @@ def test_plain_fp32_solve_floor_on_the_grid_workload(H):
     """The plain FP32 comparator on the 64 x 64 grid workload (gamma 2^4 -> 2^14):
     at tol_final = 1e-6 it stops with a documented cap status (its FP32 exponent
     cannot resolve the marginals at gamma = 2^14: reading R20) and leaves its last
-    iterate in (u, v); the FP64 oracle evaluates that iterate's marginal L1 error
-    (the floor), which stays above 1e-6. At gamma_f = 2^8 (exponents 64 times
+    iterate in (u, v) and the stage it stopped in in the stats; the FP64 oracle
+    evaluates that iterate's marginal L1 error at that stage's temperature (the
+    floor), which stays above 1e-6. At gamma_f = 2^8 (exponents 64 times
     smaller) and tol_final = 1e-4 the same path reaches its target as the oracle
     measures it, within the factor 2 its own FP32 evaluation of the stopping
     test allows."""
@@ -387,7 +388,11 @@ def test_plain_fp32_solve_floor_on_the_grid_workload(H):
     with pytest.raises(EotError) as ex:
         H.eot_solve(prob, default_params(gamma_i=16.0, gamma_f=16384.0, tol_final=1e-6), u, v)
     assert ex.value.status in (3, 4, 5, 6, 7)  # CG_MAXITER, LINESEARCH, MAXSTAGES, MAXNEWTON, RANGE
-    floor = O.marginal_l1_error(u.cpu().numpy(), v.cpu().numpy(), g, C64, p["r"], p["c"])
+    st = ex.value.stats  # the work done before the cap: the stage it stopped in
+    assert st["stages"] >= 1 and np.isnan(st["marg_err_l1"])
+    g_last = st["final_gamma"]
+    assert g_last <= g
+    floor = O.marginal_l1_error(u.cpu().numpy(), v.cpu().numpy(), g_last, C64, p["r"], p["c"])
     assert np.isfinite(floor) and floor > 1e-6
     st = H.eot_solve(prob, default_params(gamma_i=16.0, gamma_f=256.0, tol_final=1e-4), u, v).as_dict()
     err = O.marginal_l1_error(u.cpu().numpy(), v.cpu().numpy(), 256.0, C64, p["r"], p["c"])
