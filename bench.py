@@ -339,6 +339,26 @@ def record_cfg2_breadth(E, dev):
             "all_reached": all(r["reached_tol"] for r in out)}
 
 
+def record_next3(E, dev, alg2_seconds, alg2_sweeps):
+    """The full-system NewtonSolve (PCG on the (n + m) discounted Hessian, one
+    two-sided sweep per iteration) on the headline workload, measured against
+    Alg. 2's reduced system (the headline solve)."""
+    import torch
+    import workloads as W
+    p = W.grid_problem_4096(0, "sqeuclid")
+    h = E.Handle(0, N, N)
+    try:
+        prob = E.Problem(torch.from_numpy(p["C"]).to(dev), torch.from_numpy(p["r"]).to(dev),
+                         torch.from_numpy(p["c"]).to(dev), precision="mixed")
+        prm = E.default_params(gamma_i=GAMMA_I, gamma_f=GAMMA_F, tol_final=TOL, newton_system=E.NEWTON_FULL)
+        rec, _, _ = _solve_record(h, E, prob, prm, N, N, warm=1, reps=2)
+    finally:
+        h.close()
+    rec.update({"system": "full (n + m) discounted Hessian", "vs_alg2_time": round(rec["seconds"] / alg2_seconds, 4),
+                "vs_alg2_sweeps": round(rec["sweeps_total"] / alg2_sweeps, 4)})
+    return rec
+
+
 def record_d64(E, dev, peaks):
     """n = m = 16384 points in d = 64 (8-component mixtures), gamma 2^4 -> 2^10,
     tol 1e-6: the mixed path (tensor-core sweeps) against the plain FP32 comparator
@@ -620,6 +640,7 @@ def run_ours(args):
     if not args.no_extra and world == 1:
         for key, fn in (("cfg1_fp64", lambda: record_cfg1_fp64(E, dev)),
                         ("cfg2_breadth", lambda: record_cfg2_breadth(E, dev)),
+                        ("next3_full_system", lambda: record_next3(E, dev, sec, sweeps)),
                         ("d64", lambda: record_d64(E, dev, measured_peaks())),
                         ("batch256", lambda: record_batch256(E, dev))):
             try:

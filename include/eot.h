@@ -100,9 +100,16 @@ typedef struct {
                           default) or EOT_PROJECT_SINKHORN (alternating row/column fixes
                           until ||grad g||_1 <= eps: MDOT-Sinkhorn, Sec. 4) */
   int32_t max_sinkhorn; /* Sinkhorn iterations per projection; default 10^6 when 0 */
+  int32_t newton_system; /* the linear system of each NewtonSolve (dense costs):
+                            EOT_NEWTON_REDUCED (Alg. 2: CG on F_r(rho), default) or
+                            EOT_NEWTON_FULL (CG on the (n + m) discounted Hessian of
+                            Eq. discounted-hessian, one two-sided sweep per iteration;
+                            the same outer loop and forcing test) */
+  int32_t reserved;
 } eot_params;
 
 enum { EOT_PROJECT_NEWTON = 0, EOT_PROJECT_SINKHORN = 1 };
+enum { EOT_NEWTON_REDUCED = 0, EOT_NEWTON_FULL = 1 };
 
 /* One stage t of Alg. 1 in eot_solve: the temperature, the tolerance of its
  * Bregman projection, AdjustSchedule's input and output (Sec. 3.3, Eq. delta_k-
@@ -186,6 +193,23 @@ eot_status eot_newton_solve(eot_handle h, const eot_problem* prob, const double*
                             const double* v, double gamma, const double* r_target, double eta,
                             double rho0, int32_t max_cg, double* du_out, double* dv_out,
                             double* rho_out, int32_t* cg_iters_out, void* stream);
+
+/* NewtonSolve as eot_newton_solve, but each linear solve runs PCG on the full
+ * discounted system (Sec. 3.1, Eq. discounted-hessian)
+ *   [D(r(P)) d_u + sqrt(rho) P d_v ; sqrt(rho) P^T d_u + D(c(P)) d_v] = [-grad_u g ; 0]
+ * from 0 with the diagonal preconditioner (r(P), c(P)), to an L1 residual of the
+ * (n + m)-vector <= (eta/4) ||grad g||_1, keeping its u-block (in exact arithmetic
+ * the solution of F_r(rho) d_u = -grad_u g, the Schur complement of Eq.
+ * matrix-definitions). Each CG iteration is one fused two-sided sweep over C
+ * (Alg. 2's CG makes two); the outer test ||F_r(1) d_u + grad_u g||_1 <= eta
+ * ||grad g||_1 takes two more per linear solve. A different Krylov iteration,
+ * offered for measurement against Alg. 2. Dense costs only (EOT_ERR_UNSUPPORTED
+ * for points). Arguments and errors as eot_newton_solve; cg_iters_out counts
+ * full-system iterations. Synchronises. */
+eot_status eot_newton_solve_full(eot_handle h, const eot_problem* prob, const double* u,
+                                 const double* v, double gamma, const double* r_target, double eta,
+                                 double rho0, int32_t max_cg, double* du_out, double* dv_out,
+                                 double* rho_out, int32_t* cg_iters_out, void* stream);
 
 /* Round (Alg. 1's closing step; the paper cites Algorithm 2 of Altschuler, Weed and
  * Rigollet, 2017) of P = P(u, v; gamma) onto U(r, c), kept implicit:

@@ -6,7 +6,7 @@ ABI of include/eot.h); this package only builds it and marshals arguments.
 """
 from .binding import (COST_DENSE_F32, COST_DENSE_F64, COST_SQEUCLID_POINTS, PRECISIONS,  # noqa: F401
                       EotError, EotParams, EotProblem, EotStats, Handle, Problem,
-                      PROJECT_NEWTON, PROJECT_SINKHORN, default_params, load_library,
+                      PROJECT_NEWTON, PROJECT_SINKHORN, NEWTON_REDUCED, NEWTON_FULL, default_params, load_library,
                       solve_batched)
 from .buildlib import build  # noqa: F401
 

@@ -37,10 +37,12 @@ class EotParams(ctypes.Structure):
                 ("tol_final", ctypes.c_double), ("max_stages", ctypes.c_int32),
                 ("max_newton", ctypes.c_int32), ("max_cg", ctypes.c_int32),
                 ("max_ls", ctypes.c_int32), ("projector", ctypes.c_int32),
-                ("max_sinkhorn", ctypes.c_int32)]
+                ("max_sinkhorn", ctypes.c_int32), ("newton_system", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 PROJECT_NEWTON, PROJECT_SINKHORN = 0, 1
+NEWTON_REDUCED, NEWTON_FULL = 0, 1
 
 
 class EotStageRecord(ctypes.Structure):
@@ -77,7 +79,7 @@ EXPORTS = ["eot_create", "eot_destroy", "eot_last_error", "eot_status_string",
            "eot_params_default", "eot_marginals", "eot_hvp", "eot_newton_solve", "eot_solve",
            "eot_backward", "eot_sweep_bench", "eot_marginals_noalloc", "eot_kernel_launches",
            "eot_solve_batched", "eot_batch_last_config", "eot_round", "eot_value",
-           "eot_plan_argmax", "eot_plan_support"]
+           "eot_plan_argmax", "eot_plan_support", "eot_newton_solve_full"]
 
 _LIB = None
 
@@ -105,6 +107,7 @@ def load_library(path=None):
     L.eot_hvp.argtypes = [vp, P, vp, vp, dbl, dbl, vp, vp, vp, vp, vp, vp, vp]
     L.eot_newton_solve.argtypes = [vp, P, vp, vp, dbl, vp, dbl, dbl, i32, vp, vp,
                                    ctypes.POINTER(dbl), ctypes.POINTER(i32), vp]
+    L.eot_newton_solve_full.argtypes = L.eot_newton_solve.argtypes
     L.eot_solve.argtypes = [vp, P, ctypes.POINTER(EotParams), vp, vp, ctypes.POINTER(EotStats), vp]
     L.eot_backward.argtypes = [vp, P, vp, vp, dbl, dbl, vp, vp, vp, vp, vp, vp, vp]
     L.eot_value.argtypes = [vp, P, vp, vp, dbl, vp, vp]
@@ -123,7 +126,7 @@ def load_library(path=None):
     L.eot_kernel_launches.restype = i64
     for f in ("eot_create", "eot_destroy", "eot_marginals", "eot_hvp", "eot_newton_solve",
               "eot_solve", "eot_backward", "eot_sweep_bench", "eot_solve_batched", "eot_round",
-              "eot_value", "eot_plan_argmax", "eot_plan_support"):
+              "eot_value", "eot_plan_argmax", "eot_plan_support", "eot_newton_solve_full"):
         getattr(L, f).restype = ctypes.c_int
     if path == _build.LIBPATH:
         _LIB = L
@@ -235,13 +238,14 @@ class Handle:
                                     _stream(stream)))
 
     def eot_newton_solve(self, prob, u, v, gamma, r_target, eta, rho0, du_out, dv_out=None,
-                         max_cg=0, stream=None):
+                         max_cg=0, stream=None, full=False):
+        """NewtonSolve (Alg. 2); full=True: eot_newton_solve_full (the full discounted system)."""
         rho = ctypes.c_double(0.0)
         it = ctypes.c_int32(0)
-        self.check(self.lib.eot_newton_solve(self.h, prob.ref(), _p(u), _p(v), float(gamma),
-                                             _p(r_target), float(eta), float(rho0), int(max_cg),
-                                             _p(du_out), _p(dv_out), ctypes.byref(rho),
-                                             ctypes.byref(it), _stream(stream)))
+        fn = self.lib.eot_newton_solve_full if full else self.lib.eot_newton_solve
+        self.check(fn(self.h, prob.ref(), _p(u), _p(v), float(gamma), _p(r_target), float(eta),
+                      float(rho0), int(max_cg), _p(du_out), _p(dv_out), ctypes.byref(rho),
+                      ctypes.byref(it), _stream(stream)))
         return rho.value, it.value
 
     def eot_solve(self, prob, params, u, v, stream=None, stage_records=256):
@@ -330,9 +334,9 @@ class Handle:
         self.eot_hvp(prob, u, v, gamma, s, du, dv, ou, ov, r, c)
         return ou, ov, r, c
 
-    def newton_solve(self, prob, u, v, gamma, r_target, eta, rho0=0.0, max_cg=0):
+    def newton_solve(self, prob, u, v, gamma, r_target, eta, rho0=0.0, max_cg=0, full=False):
         du, dv = torch.empty_like(u), torch.empty_like(v)
-        rho, it = self.eot_newton_solve(prob, u, v, gamma, r_target, eta, rho0, du, dv, max_cg)
+        rho, it = self.eot_newton_solve(prob, u, v, gamma, r_target, eta, rho0, du, dv, max_cg, full=full)
         return du, dv, rho, it
 
     def solve(self, prob, params=None, **overrides):

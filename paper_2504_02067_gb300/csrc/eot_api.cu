@@ -60,7 +60,8 @@ void ensure_capacity(eot_handle h, int64_t n, int64_t m) {
                    &h->du, &h->x, &h->res, &h->z, &h->p, &h->q, &h->y, &h->Yx, &h->M,
                    &h->diag, &h->y0, &h->du0, &h->nt0, &h->nt1, &h->rPs, &h->U};
   for (double** p : nv) *p = (double*)dev_alloc(h, N * sizeof(double));
-  double** mv[] = {&h->Bl, &h->colfac, &h->cP, &h->logcP, &h->ct, &h->logct, &h->dv, &h->mt0, &h->mt1, &h->V, &h->wprev};
+  double** mv[] = {&h->Bl, &h->colfac, &h->cP, &h->logcP, &h->ct, &h->logct, &h->dv, &h->mt0, &h->mt1, &h->V, &h->wprev,
+                   &h->fxv, &h->frv, &h->fzv, &h->fpv, &h->fqv};
   for (double** p : mv) *p = (double*)dev_alloc(h, Mm * sizeof(double));
   void** ev[] = {&h->Ah, &h->Bh, &h->xw0, &h->xw1, &h->zf, &h->wsq, &h->ewr, &h->ewc};
   for (void** p : ev) *p = dev_alloc(h, L * sizeof(double));
@@ -265,6 +266,8 @@ eot_params eot_params_default(void) {
   p.max_ls = 30;
   p.projector = EOT_PROJECT_NEWTON;
   p.max_sinkhorn = 0;
+  p.newton_system = EOT_NEWTON_REDUCED;
+  p.reserved = 0;
   return p;
 }
 
@@ -321,8 +324,28 @@ eot_status eot_newton_solve(eot_handle h, const eot_problem* prob, const double*
       throw EotError{EOT_ERR_INVALID_ARG, "eta must be > 0 and rho0 in [0, 1)"};
     cudaStream_t st = (cudaStream_t)stream;
     int it = 0;
-    if (is_f64(prob)) run_newton<double>(h, prob, u, v, gamma, r_target, eta, rho0, max_cg, du_out, dv_out, rho_out, &it, st);
-    else run_newton<float>(h, prob, u, v, gamma, r_target, eta, rho0, max_cg, du_out, dv_out, rho_out, &it, st);
+    if (is_f64(prob)) run_newton<double>(h, prob, u, v, gamma, r_target, eta, rho0, max_cg, du_out, dv_out, rho_out, &it, false, st);
+    else run_newton<float>(h, prob, u, v, gamma, r_target, eta, rho0, max_cg, du_out, dv_out, rho_out, &it, false, st);
+    if (cg_iters_out) *cg_iters_out = it;
+  });
+}
+
+eot_status eot_newton_solve_full(eot_handle h, const eot_problem* prob, const double* u,
+                                 const double* v, double gamma, const double* r_target, double eta,
+                                 double rho0, int32_t max_cg, double* du_out, double* dv_out,
+                                 double* rho_out, int32_t* cg_iters_out, void* stream) {
+  return guarded(h, [&] {
+    check_problem(h, prob, false);
+    check_gamma(gamma);
+    if (prob->kind == EOT_COST_SQEUCLID_POINTS)
+      throw EotError{EOT_ERR_UNSUPPORTED, "the full-system NewtonSolve needs a dense cost"};
+    if (!u || !v || !r_target || !du_out) throw EotError{EOT_ERR_INVALID_ARG, "u, v, r_target, du_out are required"};
+    if (!(eta > 0.0) || !(rho0 >= 0.0 && rho0 < 1.0))
+      throw EotError{EOT_ERR_INVALID_ARG, "eta must be > 0 and rho0 in [0, 1)"};
+    cudaStream_t st = (cudaStream_t)stream;
+    int it = 0;
+    if (is_f64(prob)) run_newton<double>(h, prob, u, v, gamma, r_target, eta, rho0, max_cg, du_out, dv_out, rho_out, &it, true, st);
+    else run_newton<float>(h, prob, u, v, gamma, r_target, eta, rho0, max_cg, du_out, dv_out, rho_out, &it, true, st);
     if (cg_iters_out) *cg_iters_out = it;
   });
 }
@@ -337,7 +360,8 @@ eot_status eot_solve(eot_handle h, const eot_problem* prob, const eot_params* pa
     check_gamma(prm.gamma_i);
     if (!(prm.p >= 1.0) || !(prm.q1 > 1.0) || !(prm.w_r > 0.25 && prm.w_r < 0.5) ||
         !(prm.tol_final > 0.0) || prm.max_stages < 1 || prm.max_newton < 1 || prm.max_ls < 1 ||
-        (prm.projector != EOT_PROJECT_NEWTON && prm.projector != EOT_PROJECT_SINKHORN) || prm.max_sinkhorn < 0)
+        (prm.projector != EOT_PROJECT_NEWTON && prm.projector != EOT_PROJECT_SINKHORN) || prm.max_sinkhorn < 0 ||
+        (prm.newton_system != EOT_NEWTON_REDUCED && prm.newton_system != EOT_NEWTON_FULL))
       throw EotError{EOT_ERR_INVALID_ARG, "invalid eot_params"};
     if (stats) {
       // outputs cleared; the caller's record array (an input) kept

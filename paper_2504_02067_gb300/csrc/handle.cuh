@@ -78,6 +78,8 @@ struct eot_handle_s {
   double *logct = nullptr, *dv = nullptr, *mt0 = nullptr, *mt1 = nullptr;
   double* V = nullptr;
   double* wprev = nullptr;  // dense CG: P^T (rowfac p) of the previous iteration
+  // v-blocks of the full-system NewtonSolve's PCG vectors (x, res, z, p, q)
+  double *fxv = nullptr, *frv = nullptr, *fzv = nullptr, *fpv = nullptr, *fqv = nullptr;
   double* cgpart = nullptr; // dense CG: per-CTA (<res, z>, ||res||_1) partials of the update kernel
   // element-type vectors (8 bytes per entry, used as float or double)
   void *Ah = nullptr, *Bh = nullptr, *xw0 = nullptr, *xw1 = nullptr, *zf = nullptr;

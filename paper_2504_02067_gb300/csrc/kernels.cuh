@@ -689,6 +689,146 @@ __global__ void cg_update_fused_kernel(int64_t n, const double* p, const double*
   }
 }
 
+// ---- NewtonSolve on the full discounted system (Sec. 3.1, Eq. discounted-hessian) ----
+// H(rho) (du, dv) = (r(P) du + s P dv, s P^T du + c(P) dv) with s = sqrt(rho): PCG on
+// H(rho) x = (r~ - r(P), 0) from x = 0 with the diagonal preconditioner
+// (r(P), c(P)), one two-sided sweep per iteration; d_u is the u-block of x.
+
+// The fused two-sided sweep's epilogue: q = H(rho) p (column sums with row weights
+// rowfac p_u, row sums with column weights colfac p_v).
+struct FullHvpEpi {
+  static constexpr int kDot = 0;
+  const double *rowfac, *colfac, *rPs, *cP, *pu, *pv;
+  double *qu, *qv;
+  const double* sc;
+  __device__ void col(int64_t j, const double* t, double* d) {
+    qv[j] = cP[j] * pv[j] + sqrt(sc[SC_RHO]) * colfac[j] * t[0];
+  }
+  __device__ void row_part(int64_t i, const double* t) {
+    qu[i] = rPs[i] * pu[i] + sqrt(sc[SC_RHO]) * rowfac[i] * t[0];
+  }
+  __device__ void finish(const double*) {}
+};
+
+// Alg. 2's outer test for the full-system direction: ||F_r(1) x_u + grad_u g||_1 =
+// ||r(P) x_u - P D(c(P))^-1 P^T x_u - (r~ - r(P)_lse)||_1 into SC_CHK (row half of a
+// two-sweep F_r(1) product whose column half wrote zf).
+struct FullCheckRowEpi {
+  static constexpr int kDot = 1;
+  const double *rowfac, *rPs, *x, *rt, *rP;
+  double* sc;
+  __device__ void row(int64_t i, const double* s, double* d) {
+    d[0] = fabs(rPs[i] * x[i] - rowfac[i] * s[0] - (rt[i] - rP[i]));
+  }
+  __device__ void finish(const double* t) { sc[SC_CHK] = t[0]; }
+};
+
+// One (n + m)-vector of the full system, stored as a u-part [n] and a v-part [m].
+struct Split2 {
+  double* u;
+  double* v;
+  __device__ __forceinline__ double& at(int64_t k, int64_t n) { return k < n ? u[k] : v[k - n]; }
+};
+
+// Full-system PCG start: x = 0, res = (r~ - r(P), 0), z = res / (r(P), c(P)), p = z,
+// the sweep weights rowfac p_u and colfac p_v; <res, z> and ||res||_1 -> CgInitFinish.
+template <class T>
+__global__ void full_init_kernel(int64_t n, int64_t m, const double* rP, const double* rPs, const double* cP,
+                                 const double* rt, const double* rowfac, const double* colfac, Split2 x, Split2 res,
+                                 Split2 z, Split2 p, T* wu, T* wv, double* sc, double* dotpart, int* cnt,
+                                 cudaGraphConditionalHandle cond) {
+  pdl_wait();
+  double v[2] = {0.0, 0.0};
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n + m;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const bool up = k < n;
+    const int64_t i = up ? k : k - n;
+    const double b = up ? rt[i] - rP[i] : 0.0;
+    const double zi = b / (up ? rPs[i] : cP[i]);
+    x.at(k, n) = 0.0;
+    res.at(k, n) = b;
+    z.at(k, n) = zi;
+    p.at(k, n) = zi;
+    if (up) wu[i] = (T)(rowfac[i] * zi);
+    else wv[i] = (T)(colfac[i] * zi);
+    v[0] += b * zi;
+    v[1] += fabs(b);
+  }
+  CgInitFinish f{sc, cond};
+  vec_finish<2>(v, dotpart, cnt, f);
+}
+
+// <p, q> of the full system and alpha = <res, z> / <p, q> (a non-positive or
+// non-finite curvature stops CG, reading R21).
+struct FullPqFinish {
+  static constexpr int kDot = 1;
+  double* sc;
+  int* status;
+  __device__ void finish(const double* t) {
+    sc[SC_PQ] = t[0];
+    if (!(t[0] > 0.0) || !isfinite(t[0])) {
+      atomicOr(status, kStatCurv);
+      sc[SC_ACTIVE] = 0.0;
+      sc[SC_ALPHA] = 0.0;
+    } else {
+      sc[SC_ALPHA] = sc[SC_RZ] / t[0];
+    }
+  }
+};
+static __global__ void full_pq_kernel(int64_t n, int64_t m, Split2 p, Split2 q, double* sc, int* status,
+                                      double* dotpart, int* cnt) {
+  pdl_wait();
+  if (sc[SC_ACTIVE] == 0.0) return;
+  double v[2] = {0.0, 0.0};
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n + m;
+       k += (int64_t)gridDim.x * blockDim.x)
+    v[0] += p.at(k, n) * q.at(k, n);
+  FullPqFinish f{sc, status};
+  vec_finish<1>(v, dotpart, cnt, f);
+}
+
+// x += alpha p, res -= alpha q, z = res / (r(P), c(P)); beta and the stop test
+// (CgUpdateFinish: ||res||_1 <= tol or the iteration cap).
+static __global__ void full_update_kernel(int64_t n, int64_t m, Split2 p, Split2 q, const double* rPs,
+                                          const double* cP, Split2 x, Split2 res, Split2 z, double* sc,
+                                          double* dotpart, int* cnt, int* status, cudaGraphConditionalHandle cond) {
+  pdl_wait();
+  if (sc[SC_ACTIVE] == 0.0) {
+    if (cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, 0);
+    return;
+  }
+  const double alpha = sc[SC_ALPHA];
+  double v[2] = {0.0, 0.0};
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n + m;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    x.at(k, n) += alpha * p.at(k, n);
+    const double r = res.at(k, n) - alpha * q.at(k, n);
+    res.at(k, n) = r;
+    const double zi = r / (k < n ? rPs[k] : cP[k - n]);
+    z.at(k, n) = zi;
+    v[0] += r * zi;
+    v[1] += fabs(r);
+  }
+  CgUpdateFinish f{sc, status, cond};
+  vec_finish<2>(v, dotpart, cnt, f);
+}
+
+// p = z + beta p and the next sweep's weights rowfac p_u, colfac p_v.
+template <class T>
+__global__ void full_pupdate_kernel(int64_t n, int64_t m, Split2 z, Split2 p, const double* rowfac,
+                                    const double* colfac, T* wu, T* wv, const double* sc) {
+  pdl_wait();
+  if (sc[SC_ACTIVE] == 0.0) return;
+  const double beta = sc[SC_BETA];
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n + m;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const double pk = z.at(k, n) + beta * p.at(k, n);
+    p.at(k, n) = pk;
+    if (k < n) wu[k] = (T)(rowfac[k] * pk);
+    else wv[k - n] = (T)(colfac[k - n] * pk);
+  }
+}
+
 // Undiscounted Newton residual of the CG iterate: F_r(1) x + grad_u g
 // = -(res + (1 - rho) Yx), with Yx = P D(c)^-1 P^T x accumulated along the CG
 // steps. chk = ||.||_1 (Alg. 2's outer test).

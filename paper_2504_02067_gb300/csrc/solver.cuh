@@ -111,6 +111,10 @@ struct Solver {
   SolveCounters cnt;
   int64_t* sweep_bucket;
 
+  // NewtonSolve's linear system: Alg. 2's reduced F_r(rho) (false) or the full
+  // discounted Hessian (true, dense costs; measured against Alg. 2)
+  bool full_system = false;
+
   // point-cloud cost (C == nullptr): C_ij = sC |x_i - y_j|^2
   bool points = false;
   const float *X = nullptr, *Y = nullptr;
@@ -147,6 +151,15 @@ struct Solver {
     rg = row_grid(n);
     geo = col_geo(h, n, m, V);
     sweep_bucket = &cnt.sweeps_other;
+  }
+
+  // The full-system NewtonSolve (dense costs): its fused sweep needs the row
+  // partials of every strip (allocated here, before any program is captured).
+  void set_full_system(bool on) {
+    full_system = on;
+    if (!on) return;
+    if (points) throw EotError{EOT_ERR_UNSUPPORTED, "the full-system NewtonSolve needs a dense cost"};
+    ensure_rowpart(h, n, geo.S);
   }
 
   // ---- point-cloud geometry (pts_geo_of / tc_geo_of above the class) ----
@@ -588,7 +601,7 @@ struct Solver {
     ctl.sc = h->sc;
     ctl.status = h->status;
     ctl.fp64 = sizeof(T) == 8 ? 1 : 0;
-    ctl.fused_cg = points ? 0 : 1;
+    ctl.fused_cg = (points || full_system) ? 0 : 1;
     ctl.floor32 = armijo_floor32(n, m);
     int64_t* saved = sweep_bucket;
     sweep_bucket = &discard;
@@ -605,7 +618,8 @@ struct Solver {
     uint64_t sbits;
     std::memcpy(&sbits, &sC, sizeof(sbits));
     const uintptr_t src = points ? ((uintptr_t)X ^ ((uintptr_t)Y << 1) ^ (uintptr_t)sbits) : (uintptr_t)C;
-    const ProgKey key{tag | ((int)sizeof(T) << 4) | ((plain ? 1 : 0) << 8) | ((points ? 1 : 0) << 9) | (d << 10),
+    const ProgKey key{tag | ((int)sizeof(T) << 4) | ((plain ? 1 : 0) << 8) | ((points ? 1 : 0) << 9) | (d << 10) |
+                          ((full_system ? 1 : 0) << 20),
                       V | ((tc_on ? 1 : 0) << 4) | ((keep_l2 ? 1 : 0) << 5), 0, n, m, ldc, src};
     auto it = h->graphs.find(key);
     if (it == h->graphs.end()) {
@@ -687,7 +701,10 @@ struct Solver {
     cnt.newton_steps += dd(SC_N_NEWTON);
     cnt.ls_trials += dd(SC_N_LSTRIAL);
     cnt.sk_iters += dd(SC_N_SK);
-    cnt.sweeps_cg += 2 * dd(SC_N_CGIT) + 2 * dd(SC_N_CURV);
+    if (full_system)  // one fused sweep per iteration, two for each solve's outer test
+      cnt.sweeps_cg += dd(SC_N_CGIT) + dd(SC_N_CURV) + 2 * dd(SC_N_CGSOLVE);
+    else
+      cnt.sweeps_cg += 2 * dd(SC_N_CGIT) + 2 * dd(SC_N_CURV);
     cnt.sweeps_newton += 3 * dd(SC_N_GO);
     cnt.sweeps_sk += 2 * dd(SC_N_SK);
     cnt.sweeps_ls += dd(SC_N_LSTRIAL) + dd(SC_N_LSDEC) + dd(SC_N_UPD);
@@ -730,6 +747,7 @@ struct Solver {
   // h->cP, the Armijo slope in SC_SLOPE and the rho of the last CG solve in
   // SC_RHOSTEP (SC_RAN = 1 if a CG solve ran).
   void emit_newton(const double* u, const double* v, const double* rt) {
+    if (full_system && points) throw EotError{EOT_ERR_UNSUPPORTED, "the full-system NewtonSolve needs a dense cost"};
     // factorisation P = rowfac * colfac * E with row shift = running row max
     split_rows(u, nullptr, 0.0, h->rowmax, h->Al, nullptr, h->rowfac, h->rowmax);
     split_cols(v, nullptr, 0.0, nullptr, h->Bl, ewc(), h->colfac, nullptr);
@@ -753,23 +771,27 @@ struct Solver {
       row<3, false, 2>(a, e);
     }
     ctl_launch(ctl_cg_begin);
-    loop_while(F_CGOUT, [&] {
-      if (points)
-        launch_k(cg_init_kernel<T>, dim3(vg_n), dim3(kOnThreads), st, n, h->rP, h->rPs, rt, h->diag, h->rowfac,
-                 h->M, h->x, h->res, h->z, h->p, h->Yx, xw0(), h->sc, h->dotpart, h->cnt_dot, cond(F_CG));
-      else
-        launch_k(cg_init_fused_kernel<T>, dim3(vg_n), dim3(kOnThreads), st, n, h->rP, h->rPs, rt, h->diag,
-                 h->rowfac, h->M, h->x, h->res, h->z, h->p, h->Yx, xw0(), h->sc, h->cgpart, cond(F_CG));
-      EOT_LAUNCH_CHECK();
-      h->launches++;
-      loop_while(F_CG, [&] {
-        for (int b = 0; b < kCgBody; ++b) cg_iteration();
+    if (full_system) {
+      emit_full_cg(rt);
+    } else {
+      loop_while(F_CGOUT, [&] {
+        if (points)
+          launch_k(cg_init_kernel<T>, dim3(vg_n), dim3(kOnThreads), st, n, h->rP, h->rPs, rt, h->diag, h->rowfac,
+                   h->M, h->x, h->res, h->z, h->p, h->Yx, xw0(), h->sc, h->dotpart, h->cnt_dot, cond(F_CG));
+        else
+          launch_k(cg_init_fused_kernel<T>, dim3(vg_n), dim3(kOnThreads), st, n, h->rP, h->rPs, rt, h->diag,
+                   h->rowfac, h->M, h->x, h->res, h->z, h->p, h->Yx, xw0(), h->sc, h->cgpart, cond(F_CG));
+        EOT_LAUNCH_CHECK();
+        h->launches++;
+        loop_while(F_CG, [&] {
+          for (int b = 0; b < kCgBody; ++b) cg_iteration();
+        });
+        launch_k(cg_check_kernel, dim3(vg_n), dim3(kOnThreads), st, n, h->res, h->Yx, h->sc, h->dotpart, h->cnt_dot);
+        EOT_LAUNCH_CHECK();
+        h->launches++;
+        ctl_launch(ctl_cg_end);
       });
-      launch_k(cg_check_kernel, dim3(vg_n), dim3(kOnThreads), st, n, h->res, h->Yx, h->sc, h->dotpart, h->cnt_dot);
-      EOT_LAUNCH_CHECK();
-      h->launches++;
-      ctl_launch(ctl_cg_end);
-    });
+    }
     launch_k(select_du_kernel, dim3(vg_n), dim3(kOnThreads), st, n, (const double*)h->x, (const double*)h->du0, h->du,
              (const double*)h->sc);
     // d_u modulo the gauge, d_v = -(P^T d_u) / c(P) and the Armijo slope <r~ - r(P), d_u>
@@ -785,6 +807,59 @@ struct Solver {
       DvColEpi e{h->colfac, h->cP, h->dv};
       col<1, false, 0>(a, e);
     }
+  }
+
+  // Alg. 2's anneal loop with each linear solve on the full discounted system
+  // (NEXT-3): PCG from 0 on H(rho) x = (r~ - r(P), 0), each iteration one fused
+  // two-sided sweep (P p_v and P^T p_u in one pass) and three O(n + m) kernels;
+  // after each solve the outer test ||F_r(1) x_u + grad_u g||_1 by two sweeps.
+  void emit_full_cg(const double* rt) {
+    const int vg = on_grid(n + m, h->sms, h->dot_slots);
+    const Split2 X{h->x, h->fxv}, R{h->res, h->frv}, Z{h->z, h->fzv}, Pv{h->p, h->fpv}, Q{h->q, h->fqv};
+    loop_while(F_CGOUT, [&] {
+      launch_k(full_init_kernel<T>, dim3(vg), dim3(kOnThreads), st, n, m, (const double*)h->rP,
+               (const double*)h->rPs, (const double*)h->cP, rt, (const double*)h->rowfac, (const double*)h->colfac,
+               X, R, Z, Pv, xw0(), wsq(), h->sc, h->dotpart, h->cnt_dot, cond(F_CG));
+      EOT_LAUNCH_CHECK();
+      h->launches++;
+      loop_while(F_CG, [&] {
+        for (int b = 0; b < kCgBody; ++b) {
+          SweepArgs<T> a = args();
+          a.wr[0] = xw0();
+          a.wc[0] = wsq();
+          a.active = h->sc + SC_ACTIVE;
+          FullHvpEpi e{h->rowfac, h->colfac, h->rPs, h->cP, h->p, h->fpv, h->q, h->fqv, h->sc};
+          const dim3 grid((unsigned)geo.S, (unsigned)geo.R);
+          if (V == VEC) launch_k(col_sweep_kernel<T, VEC, 1, false, 1, FullHvpEpi>, grid, dim3(kThreads), st, a, e);
+          else launch_k(col_sweep_kernel<T, 1, 1, false, 1, FullHvpEpi>, grid, dim3(kThreads), st, a, e);
+          launch_k(full_pq_kernel, dim3(vg), dim3(kOnThreads), st, n, m, Pv, Q, h->sc, h->status, h->dotpart,
+                   h->cnt_dot);
+          launch_k(full_update_kernel, dim3(vg), dim3(kOnThreads), st, n, m, Pv, Q, (const double*)h->rPs,
+                   (const double*)h->cP, X, R, Z, h->sc, h->dotpart, h->cnt_dot, h->status, cond(F_CG));
+          launch_k(full_pupdate_kernel<T>, dim3(vg), dim3(kOnThreads), st, n, m, Z, Pv, (const double*)h->rowfac,
+                   (const double*)h->colfac, xw0(), wsq(), (const double*)h->sc);
+          EOT_LAUNCH_CHECK();
+          h->launches += 4;
+        }
+      });
+      // the outer test: F_r(1) x_u by a column and a row sweep
+      launch_k(weight_kernel<T>, dim3(vg_n), dim3(kOnThreads), st, n, (const double*)h->rowfac, (const double*)h->x,
+               xw0());
+      EOT_LAUNCH_CHECK();
+      h->launches++;
+      {
+        SweepArgs<T> a = args();
+        a.wr[0] = xw0();
+        launch_col_dense<1, false>(st, a, CgColEpi<T>{h->colfac, h->cP, zf()});
+      }
+      {
+        SweepArgs<T> a = args();
+        a.wc[0] = zf();
+        launch_row_dense<1, false, 0>(st, a, FullCheckRowEpi{h->rowfac, h->rPs, h->x, rt, h->rP, h->sc});
+      }
+      h->launches += 2;
+      ctl_launch(ctl_cg_end);
+    });
   }
 
   // One CG iteration, each kernel a no-op once the device stop flag SC_ACTIVE
@@ -960,7 +1035,7 @@ void run_hvp(eot_handle h, const eot_problem* P, const double* u, const double* 
 template <class T>
 void run_newton(eot_handle h, const eot_problem* P, const double* u, const double* v,
                 double gamma, const double* rtarget, double eta, double rho0, int max_cg,
-                double* du_out, double* dv_out, double* rho_out, int* iters_out, cudaStream_t st);
+                double* du_out, double* dv_out, double* rho_out, int* iters_out, bool full, cudaStream_t st);
 template <class T>
 void run_solve(eot_handle h, const eot_problem* P, const eot_params* prm, double* u, double* v,
                eot_stats* stats, cudaStream_t st);

@@ -9,7 +9,7 @@ template void run_value<float>(eot_handle, const eot_problem*, const double*, co
 template void run_hvp<float>(eot_handle, const eot_problem*, const double*, const double*, double, double,
                           const double*, const double*, double*, double*, double*, double*, cudaStream_t);
 template void run_newton<float>(eot_handle, const eot_problem*, const double*, const double*, double,
-                             const double*, double, double, int, double*, double*, double*, int*,
+                             const double*, double, double, int, double*, double*, double*, int*, bool,
                              cudaStream_t);
 template void run_solve<float>(eot_handle, const eot_problem*, const eot_params*, double*, double*,
                             eot_stats*, cudaStream_t);

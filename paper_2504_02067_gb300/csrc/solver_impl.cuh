@@ -114,10 +114,11 @@ void run_hvp(eot_handle h, const eot_problem* P, const double* u, const double* 
 template <class T>
 void run_newton(eot_handle h, const eot_problem* P, const double* u, const double* v,
                 double gamma, const double* rtarget, double eta, double rho0, int max_cg,
-                double* du_out, double* dv_out, double* rho_out, int* iters_out, cudaStream_t st) {
+                double* du_out, double* dv_out, double* rho_out, int* iters_out, bool full, cudaStream_t st) {
   Solver<T> S(h, P, st);
+  S.set_full_system(full);
   EOT_CUDA(cudaMemsetAsync(h->status, 0, sizeof(int), st));
-  if (max_cg <= 0) max_cg = (int)std::min<int64_t>(4 * P->n, 2000);
+  if (max_cg <= 0) max_cg = (int)std::min<int64_t>(4 * (full ? P->n + P->m : P->n), 2000);
   S.init_control(1, 1, max_cg);
   S.set_scalar(SC_GAMMA, round_gamma<T>(gamma));
   // the program runs on the handle's buffers (a captured graph keeps their addresses)
@@ -148,7 +149,8 @@ void run_solve(eot_handle h, const eot_problem* P, const eot_params* prm_in, dou
   const eot_params prm = *prm_in;
   Solver<T> S(h, P, st);
   const int64_t n = P->n, m = P->m;
-  const int max_cg = prm.max_cg > 0 ? prm.max_cg : (int)std::min<int64_t>(4 * n, 2000);
+  S.set_full_system(prm.newton_system == EOT_NEWTON_FULL);
+  const int max_cg = prm.max_cg > 0 ? prm.max_cg : (int)std::min<int64_t>(4 * (S.full_system ? n + m : n), 2000);
   EOT_CUDA(cudaMemsetAsync(h->status, 0, sizeof(int), st));
   S.init_control(prm.max_newton, prm.max_ls, max_cg);
   // Alg. 1 runs on the handle's working potentials (h->U, h->V); u, v receive them at the end
