@@ -49,10 +49,12 @@ typedef enum {
   EOT_ERR_RANGE = 7,          /* |potential| >= 2^19: outside the mixed-precision split */
   EOT_ERR_CUDA = 8,           /* a CUDA runtime call failed; destroy the handle */
   EOT_ERR_UNSUPPORTED = 9,    /* combination of cost kind and precision not built */
-  EOT_ERR_DEVICE_TIMEOUT = 10 /* a bounded device-side wait (an mbarrier of the tensor-core
+  EOT_ERR_DEVICE_TIMEOUT = 10, /* a bounded device-side wait (an mbarrier of the tensor-core
                                  sweeps or a group barrier of eot_solve_batched) ran out:
                                  the kernel recorded it and returned, its outputs are not
                                  valid, and the handle stays usable */
+  EOT_ERR_TIME_LIMIT = 11     /* eot_solve reached eot_params.max_seconds (checked before
+                                 each Newton step and each stage) */
 } eot_status;
 
 typedef enum {
@@ -106,6 +108,9 @@ typedef struct {
                             Eq. discounted-hessian, one two-sided sweep per iteration;
                             the same outer loop and forcing test) */
   int32_t reserved;
+  double max_seconds;  /* wall-clock budget of eot_solve (<= 0: none); checked on the
+                          device before each Newton step and on the host before each
+                          stage, so a call may overrun it by one Newton step */
 } eot_params;
 
 enum { EOT_PROJECT_NEWTON = 0, EOT_PROJECT_SINKHORN = 1 };

@@ -17,7 +17,7 @@ EOT_OK = 0
 STATUS_NAMES = {0: "EOT_OK", 1: "EOT_ERR_INVALID_ARG", 2: "EOT_ERR_NONFINITE",
                 3: "EOT_ERR_CG_MAXITER", 4: "EOT_ERR_LINESEARCH", 5: "EOT_ERR_MAXSTAGES",
                 6: "EOT_ERR_MAXNEWTON", 7: "EOT_ERR_RANGE", 8: "EOT_ERR_CUDA",
-                9: "EOT_ERR_UNSUPPORTED", 10: "EOT_ERR_DEVICE_TIMEOUT"}
+                9: "EOT_ERR_UNSUPPORTED", 10: "EOT_ERR_DEVICE_TIMEOUT", 11: "EOT_ERR_TIME_LIMIT"}
 
 COST_DENSE_F32, COST_DENSE_F64, COST_SQEUCLID_POINTS = 0, 1, 2
 PRECISIONS = {"fp64": 0, "mixed": 1, "plain_fp32": 2}
@@ -38,7 +38,7 @@ class EotParams(ctypes.Structure):
                 ("max_newton", ctypes.c_int32), ("max_cg", ctypes.c_int32),
                 ("max_ls", ctypes.c_int32), ("projector", ctypes.c_int32),
                 ("max_sinkhorn", ctypes.c_int32), ("newton_system", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("reserved", ctypes.c_int32), ("max_seconds", ctypes.c_double)]
 
 
 PROJECT_NEWTON, PROJECT_SINKHORN = 0, 1

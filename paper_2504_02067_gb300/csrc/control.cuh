@@ -44,12 +44,25 @@ enum ScCtl : int {
   // cumulative counters of the call (doubles, exact below 2^53)
   SC_N_CGIT, SC_N_CGSOLVE, SC_N_CURV, SC_N_NEWTON, SC_N_LSTRIAL, SC_N_LSDEC, SC_N_UPD, SC_N_SK,
   SC_N_CGPASS, SC_N_NLOOP, SC_N_GO,
+  SC_DEADLINE,      // %globaltimer value (ns) after which no Newton step starts (0: none)
   SC_FL0,           // SC_FL0 + Flag: the flags as doubles (read by the host executor)
   SC_CTL_END = SC_FL0 + F_COUNT
 };
 static_assert((int)SC_CTL_END <= (int)SC_TOTAL, "device scalar array too small for the stage control");
 
-enum Err : int { E_NONE = 0, E_MAXNEWTON, E_CHISK, E_CGMAX, E_RHO, E_LS };
+enum Err : int { E_NONE = 0, E_MAXNEWTON, E_CHISK, E_CGMAX, E_RHO, E_LS, E_TIME };
+
+__device__ __forceinline__ double global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return (double)t;
+}
+
+// SC_DEADLINE = now + seconds (the call's wall-clock budget; seconds <= 0: none).
+static __global__ void set_deadline_kernel(double* sc, double seconds) {
+  pdl_wait();
+  sc[SC_DEADLINE] = seconds > 0.0 ? global_ns() + seconds * 1e9 : 0.0;
+}
 
 constexpr int kMaxChiSinkhorn = 2000;  // ChiSinkhorn iterations per Newton step
 constexpr int kMaxAnneal = 60;         // rho annealings per NewtonSolve
@@ -91,11 +104,13 @@ EOT_CTL_KERNEL(ctl_stage_init) {
   set_flag(c, F_NEWTON, sc[SC_GL1] > sc[SC_EPS]);
 }
 
-// Start of a Newton-loop pass: the max_newton cap, then Alg. 3's test.
+// Start of a Newton-loop pass: the max_newton cap and the wall-clock budget,
+// then Alg. 3's test.
 EOT_CTL_KERNEL(ctl_step_a) {
   EOT_CTL_BEGIN
   sc[SC_N_NLOOP] += 1.0;
   if (sc[SC_STEPS] >= sc[SC_MAXNEWTON]) fail(c, E_MAXNEWTON);
+  if (sc[SC_DEADLINE] > 0.0 && global_ns() > sc[SC_DEADLINE]) fail(c, E_TIME);
   sc[SC_SKC] = 0.0;
   set_flag(c, F_SK, ok(c) && sc[SC_CHI2] > sc[SC_EPSCHI]);
 }

@@ -248,6 +248,7 @@ const char* eot_status_string(eot_status s) {
     case EOT_ERR_CUDA: return "EOT_ERR_CUDA";
     case EOT_ERR_UNSUPPORTED: return "EOT_ERR_UNSUPPORTED";
     case EOT_ERR_DEVICE_TIMEOUT: return "EOT_ERR_DEVICE_TIMEOUT";
+    case EOT_ERR_TIME_LIMIT: return "EOT_ERR_TIME_LIMIT";
   }
   return "unknown status";
 }
@@ -268,6 +269,7 @@ eot_params eot_params_default(void) {
   p.max_sinkhorn = 0;
   p.newton_system = EOT_NEWTON_REDUCED;
   p.reserved = 0;
+  p.max_seconds = 0.0;
   return p;
 }
 
@@ -361,7 +363,8 @@ eot_status eot_solve(eot_handle h, const eot_problem* prob, const eot_params* pa
     if (!(prm.p >= 1.0) || !(prm.q1 > 1.0) || !(prm.w_r > 0.25 && prm.w_r < 0.5) ||
         !(prm.tol_final > 0.0) || prm.max_stages < 1 || prm.max_newton < 1 || prm.max_ls < 1 ||
         (prm.projector != EOT_PROJECT_NEWTON && prm.projector != EOT_PROJECT_SINKHORN) || prm.max_sinkhorn < 0 ||
-        (prm.newton_system != EOT_NEWTON_REDUCED && prm.newton_system != EOT_NEWTON_FULL))
+        (prm.newton_system != EOT_NEWTON_REDUCED && prm.newton_system != EOT_NEWTON_FULL) ||
+        !std::isfinite(prm.max_seconds))
       throw EotError{EOT_ERR_INVALID_ARG, "invalid eot_params"};
     if (stats) {
       // outputs cleared; the caller's record array (an input) kept

@@ -728,6 +728,7 @@ struct Solver {
       case E_CGMAX: throw EotError{EOT_ERR_CG_MAXITER, "linear CG reached max_cg" + where};
       case E_RHO: throw EotError{EOT_ERR_CG_MAXITER, "rho annealing did not meet the forcing test" + where};
       case E_LS: throw EotError{EOT_ERR_LINESEARCH, "Armijo backtracking exhausted" + where};
+      case E_TIME: throw EotError{EOT_ERR_TIME_LIMIT, "max_seconds reached before a Newton step" + where};
       default: throw EotError{EOT_ERR_CUDA, "unknown stage error" + where};
     }
   }

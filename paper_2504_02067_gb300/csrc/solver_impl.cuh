@@ -150,9 +150,15 @@ void run_solve(eot_handle h, const eot_problem* P, const eot_params* prm_in, dou
   Solver<T> S(h, P, st);
   const int64_t n = P->n, m = P->m;
   S.set_full_system(prm.newton_system == EOT_NEWTON_FULL);
+  const bool capped = prm.max_seconds > 0.0;
   const int max_cg = prm.max_cg > 0 ? prm.max_cg : (int)std::min<int64_t>(4 * (S.full_system ? n + m : n), 2000);
   EOT_CUDA(cudaMemsetAsync(h->status, 0, sizeof(int), st));
   S.init_control(prm.max_newton, prm.max_ls, max_cg);
+  if (capped) {
+    launch_k(set_deadline_kernel, dim3(1), dim3(1), st, h->sc, prm.max_seconds);
+    EOT_LAUNCH_CHECK();
+    h->launches++;
+  }
   // Alg. 1 runs on the handle's working potentials (h->U, h->V); u, v receive them at the end
   double* const U = h->U;
   double* const V = h->V;
@@ -231,6 +237,8 @@ void run_solve(eot_handle h, const eot_problem* P, const eot_params* prm_in, dou
   };
   try {
     for (; t > 0;) {
+      if (capped && wall_now() - t0 > prm.max_seconds)
+        throw EotError{EOT_ERR_TIME_LIMIT, "max_seconds reached before stage " + std::to_string(t)};
       const bool done = gamma == gamma_f;
       double eps_d = H / std::pow(gamma, prm.p);
       if (done) eps_d = std::min(eps_d, 2.0 * prm.tol_final / 3.0);

@@ -55,7 +55,7 @@ def test_library_loads_and_binding_matches(libpath):
     for code, name in binding.STATUS_NAMES.items():
         assert L.eot_status_string(code) == name.encode()
     assert ctypes.sizeof(binding.EotProblem) == 88
-    assert ctypes.sizeof(binding.EotParams) == 80
+    assert ctypes.sizeof(binding.EotParams) == 88
     assert ctypes.sizeof(binding.EotStats) == 136
 
 

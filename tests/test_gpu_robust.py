@@ -28,8 +28,8 @@ def H():
     h.close()
 
 
-def t(x):
-    return torch.as_tensor(np.ascontiguousarray(x)).to(device=DEV, dtype=torch.float64)
+def t(x, dtype=None):
+    return torch.as_tensor(np.ascontiguousarray(x)).to(device=DEV, dtype=dtype or torch.float64)
 
 
 def problem(seed=23, n=120, m=100):
@@ -112,3 +112,24 @@ def test_one_row_or_column_is_the_independence_coupling(H, shape):
     P = O.plan(u.cpu().numpy(), v.cpu().numpy(), 1024.0, C)
     np.testing.assert_allclose(P, np.outer(r, c), rtol=1e-12, atol=1e-15)
     assert st["stages"] == 0 and math.isfinite(st["marg_err_l1"])
+
+
+def test_wall_clock_budget_stops_the_solve(H):
+    """eot_params.max_seconds: a budget that has run out before the first Newton
+    step stops eot_solve with EOT_ERR_TIME_LIMIT, leaves the last iterate and the
+    work done so far, and the handle solves normally afterwards."""
+    from paper_2504_02067_gb300 import EotError, Problem, default_params
+    rng = np.random.default_rng(3)
+    n, m = 200, 150
+    C = rng.uniform(0, 1, size=(n, m)).astype(np.float32)
+    r, c = rng.dirichlet(np.ones(n)), rng.dirichlet(np.ones(m))
+    prob = Problem(t(C, torch.float32), t(r), t(c))
+    u = torch.empty(n, dtype=torch.float64, device=DEV)
+    v = torch.empty(m, dtype=torch.float64, device=DEV)
+    with pytest.raises(EotError) as ex:
+        H.eot_solve(prob, default_params(gamma_f=4096.0, max_seconds=1e-9), u, v)
+    assert ex.value.status == 11
+    assert ex.value.stats["stages"] >= 1 and np.isnan(ex.value.stats["marg_err_l1"])
+    assert torch.isfinite(u).all() and torch.isfinite(v).all()
+    st = H.eot_solve(prob, default_params(gamma_f=4096.0, max_seconds=600.0), u, v).as_dict()
+    assert st["marg_err_l1"] <= 1e-6
