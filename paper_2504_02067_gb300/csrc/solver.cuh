@@ -70,8 +70,10 @@ inline TcGeo tc_geo_of(eot_handle h, int64_t n_own, int64_t n_oth) {
 }
 // digit slices and per-point data of both clouds for the tensor-core sweeps
 inline size_t tc_mem_bytes(int64_t n, int64_t m) {
-  auto side = [](int64_t np) { return (size_t)np * (tc::kSlices * 64 * 2 + 3 * 4) + 1024; };
-  return side(tc::pad_rows(n)) + side(tc::pad_rows(m));
+  auto side = [](int64_t np) {
+    return (size_t)np * (tc::kSlices * 64 * 2 + sizeof(double) + sizeof(float4) + sizeof(tc::OwnRec)) + 4 * 256;
+  };
+  return 256 + side(tc::pad_rows(n)) + side(tc::pad_rows(m));
 }
 inline void ensure_tc_mem(eot_handle h, int64_t n, int64_t m, cudaStream_t st) {
   const size_t need = tc_mem_bytes(n, m);
@@ -184,25 +186,43 @@ struct Solver {
     const int64_t npX = tc::pad_rows(n), npY = tc::pad_rows(m);
     ensure_tc_mem(h, n, m, st);
     unsigned char* b = (unsigned char*)h->tc_mem;
-    auto carve = [&](tc::Side& sd, int64_t np, const float* P, int64_t len) {
-      __nv_bfloat16* sl = (__nv_bfloat16*)b;
-      b += (size_t)np * tc::kSlices * 64 * 2;
-      float* sc = (float*)b;
-      b += (size_t)np * 4;
-      float* nxh = (float*)b;
-      b += (size_t)np * 4;
-      float* nxl = (float*)b;
-      b += (size_t)np * 4;
-      b = (unsigned char*)(((uintptr_t)b + 255) & ~(uintptr_t)255);
-      sd = tc::Side{sl, sc, nxh, nxl, np};
-      const int64_t threads = np * 32;
-      launch_k(tc::tc_prep_kernel, dim3((unsigned)((threads + kThreads - 1) / kThreads)), dim3(kThreads), st, P,
-               len, d, np, X /* the first point of X is the common centre */, sl, sc, nxh, nxl);
+    unsigned long long* emax = (unsigned long long*)b;  // [2]
+    targs.emax = emax;
+    targs.kappa = (float*)(b + 2 * sizeof(unsigned long long));
+    b += 256;
+    EOT_CUDA(cudaMemsetAsync(emax, 0, 2 * sizeof(unsigned long long), st));
+    auto take = [&](size_t bytes) {
+      unsigned char* p = b;
+      b += (bytes + 255) / 256 * 256;
+      return p;
+    };
+    auto carve = [&](tc::Side& sd, int64_t np) {
+      sd.slices = (const __nv_bfloat16*)take((size_t)np * tc::kSlices * 64 * 2);
+      sd.nx = (const double*)take((size_t)np * sizeof(double));
+      sd.rec = (float4*)take((size_t)np * sizeof(float4));
+      sd.own = (tc::OwnRec*)take((size_t)np * sizeof(tc::OwnRec));
+      sd.npad = np;
+    };
+    carve(targs.X, npX);
+    carve(targs.Y, npY);
+    // the first point of X is the common centre of both clouds
+    auto extent = [&](const float* P, int64_t len, unsigned long long* em) {
+      const int64_t blocks = std::min<int64_t>((len * d + kThreads - 1) / kThreads, 4 * (int64_t)h->sms);
+      launch_k(tc::tc_extent_kernel, dim3((unsigned)blocks), dim3(kThreads), st, P, len, d, X, em);
       EOT_LAUNCH_CHECK();
       h->launches++;
     };
-    carve(targs.X, npX, X, n);
-    carve(targs.Y, npY, Y, m);
+    extent(X, n, emax);
+    extent(Y, m, emax + 1);
+    auto digits = [&](const tc::Side& sd, const float* P, int64_t len, const unsigned long long* em) {
+      const int64_t threads = sd.npad * 32;
+      launch_k(tc::tc_prep_kernel, dim3((unsigned)((threads + kThreads - 1) / kThreads)), dim3(kThreads), st, P,
+               len, d, sd.npad, X, em, (__nv_bfloat16*)sd.slices, (double*)sd.nx);
+      EOT_LAUNCH_CHECK();
+      h->launches++;
+    };
+    digits(targs.X, X, n, emax);
+    digits(targs.Y, Y, m, emax + 1);
     targs.err = h->status;
     for (bool rows : {true, false}) {
       const TcGeo g = tc_geo(rows);
@@ -230,6 +250,12 @@ struct Solver {
     if ((int64_t)NP * g.S * (ROWS ? n : m) > h->cap_rowpart || g.B > h->rowblk_slots)
       throw EotError{EOT_ERR_INVALID_ARG, "tensor-core sweep scratch smaller than the launch needs"};
     tc_attr<NR, LSE, SQM, ROWS, Epi>();
+    // per-sweep records of both sides, then the sweep (counted by the caller)
+    const int64_t np = targs.X.npad + targs.Y.npad;
+    launch_k(tc::tc_sweep_prep_kernel<LSE ? 1 : NR, LSE ? 0 : SQM, ROWS>, dim3((unsigned)((np + kThreads - 1) / kThreads)),
+             dim3(kThreads), s, a, targs);
+    EOT_LAUNCH_CHECK();
+    h->launches++;
     launch_kd(tc::tc_sweep_kernel<NR, LSE, SQM, ROWS, Epi>, dim3((unsigned)g.B, (unsigned)g.S),
               dim3(tc::kTcThreads), (size_t)tc::kSmemBytes, s, a, targs, e);
   }

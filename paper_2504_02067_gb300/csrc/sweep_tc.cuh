@@ -3,34 +3,52 @@
 // larger d (up to 64 coordinates).
 //
 // Exactness (an exact-slice / Ozaki-style splitting). Both point sets are moved
-// by one common centre (exact in FP64; distances are unchanged). Each point x is then scaled by
-// 2^-e (e from its largest coordinate, so |x_k| < 2^e) and each coordinate cut
-// into five signed 8-bit digits:  x_k = 2^e sum_s d_sk 2^-8(s+1)  (to 2^-40 of
-// the largest coordinate). A digit is an integer of magnitude <= 255, exact in
-// BF16; a digit product is an integer below 2^16, and a dot product over 64
-// coordinates stays below 2^22, so every MMA of digit slices is EXACT in the FP32
-// accumulator. The 15 slice pairs (s, t) with s + t <= 4 are added into five
-// "level" accumulators S_L = sum_{s+t=L} D_s D_t^T, each below 5 * 2^22 < 2^24 and
-// still exact; then
-//     x . y = 2^(e_x + e_y - 16) (S_0 + 2^-8 S_1 + 2^-16 S_2 + 2^-24 S_3 + 2^-32 S_4)
-// to ~2^-38 relative (pairs with s + t >= 5 and the 2^-40 digit truncation).
-// The epilogue forms |x - y|^2 = |x|^2 + |y|^2 - 2 x.y as an FP32 pair (TwoSum,
-// with |x|^2 precomputed as an FP32 pair from FP64), then the exponent exactly
-// as the SIMT point sweep does (expo), exp, and the reductions.
+// by one common centre c (the first point of X; exact in FP64, distances do not
+// change). Each cloud gets one exponent E (every centred coordinate |x_k| < 2^E)
+// and every coordinate is cut into five signed 8-bit digits
+//     x_k = 2^E sum_s d_sk 2^-8(s+1)      (to 2^(E-40)).
+// A digit is an integer of magnitude <= 255, exact in BF16; a digit product is an
+// integer below 2^16 and a dot product over 64 coordinates stays below 2^22, so
+// every MMA of two digit slices is exact in the FP32 accumulator. The 15 slice
+// pairs (s, t) with s + t <= 4 are added into five "level" accumulators
+// S_L = sum_{s+t=L} D_s D_t^T (levels 0-3 hold at most four pairs, below 2^24,
+// and stay exact; level 4 may round by one unit, 2^-32 of a level-0 unit), and
+//     x . y = 2^(Ex + Ey - 16) G,   G = S_0 + 2^-8 S_1 + 2^-16 S_2 + 2^-24 S_3 + 2^-32 S_4
+// to about 2^-38 of the largest |x||y| (the dropped pairs s + t >= 5 and the
+// digit truncation).
 //
-// CTA roles (320 threads, one CTA per SM: 177 KB of shared memory):
+// Exponent algebra. In base-2 units (t2 = t log2 e) the exponent of the plan is
+//     t2_ij = P_i + Q_j + kappa G_ij,   P_i = (A_i - K |x_i|^2) log2 e,
+//     Q_j = (B_j - K |y_j|^2) log2 e,   kappa = 2 K 2^(Ex+Ey-16) log2 e,
+// with K = gamma s_C and A, B the high parts of the potentials. A small kernel
+// before each sweep (tc_sweep_prep_kernel) forms P and Q in FP64 and splits each
+// into a high part on the 1/8 grid and a low part below 1/16: the other side's
+// low part is folded into its weights (w_j 2^ql_j, one record of 16 bytes per
+// point: {Qh, w0, w1, w2}) and the own side's into one FP64 factor 2^pl_i that
+// the finishing CTA applies to the row's total. Per entry the epilogue then
+// needs G as an FP32 pair (Fast2Sum of the two top levels plus three FMAs) and
+//     t2 = fma(kh, gh, Ph + Qh) + fma(kl, gh, kh gl)
+// (Ph + Qh exact on the grid, the big product exact inside the FMA): about a
+// dozen FP32 instructions and one MUFU ex2, t2 rounded twice at its own scale.
+//
+// Tile width. A tcgen05.mma of M = 128, K = 16 costs about 50 cycles whatever
+// its N up to ~96 (measured on GB300: 55 cycles at N = 32, 48 and 96; 96 at
+// N = 192), so the tile is 96 points wide: the five level accumulators then
+// fill 480 of the 512 TMEM columns, one buffer, handed over level by level.
+//
+// CTA roles (448 threads, one CTA per SM: about 215 KB of shared memory):
 //   warp 0, lane 0: bulk copies (the own 128 points' slices once; the other
-//     side's 48-point tiles into two buffers) and the MMAs of each tile into one
-//     of two TMEM accumulator buffers (5 levels x 48 columns each);
+//     side's 96-point tiles into two slice buffers and their records into four
+//     record slots) and the 60 MMAs of each tile, level by level, with a
+//     commit per level;
 //   warp 1: TMEM allocation (512 columns) and release;
-//   warps 2-9: epilogue. Warp w reads TMEM lanes 32 (w mod 4) .. +31 (one own
-//     point per thread) and half (24) of the tile's 48 columns.
-// The other side's per-point data (h, scale, |y|^2, weights) are read by the
-// epilogue straight from global memory (the same address in all lanes: one L1
-// broadcast).
-// Hand-offs are mbarriers: full[b] (copies landed), mmad[b] (MMAs of buffer b
-// done: accumulators readable and the slice buffer reusable), tfree[b] (the 8
-// epilogue warps have read buffer b). Every wait is bounded (tc.cuh).
+//   warps 2-13: epilogue. Warp w reads TMEM lanes 32 (w mod 4) .. +31 (one own
+//     point per thread) and a third (32) of the tile's 96 columns.
+// Hand-offs are mbarriers: full[sb] (slices landed), sfree[sb] (the MMAs
+// reading slice buffer sb are done), rec[s] (records landed), lvl[L] (the MMAs
+// of level L are done: accumulator readable), lfree[L] (the 12 epilogue warps
+// have loaded level L into registers; the next tile's level-L MMAs may
+// overwrite it). Every wait is bounded (tc.cuh).
 #pragma once
 #include <cuda_bf16.h>
 
@@ -41,50 +59,92 @@ namespace eot {
 namespace tc {
 
 constexpr int kM = 128;     // own points per CTA = TMEM lanes = MMA M
-constexpr int kN = 48;      // other-side points per tile = MMA N
+constexpr int kN = 96;      // other-side points per tile = MMA N
 constexpr int kSlices = 5;  // 8-bit digits per coordinate
 constexpr int kLevels = 5;  // s + t = 0 .. 4
-constexpr int kEpiWarps = 8;                  // 2 per TMEM lane quarter
+constexpr int kEpiWarps = 12;                  // 3 per TMEM lane quarter
 constexpr int kParts = kEpiWarps / 4;          // column parts of a tile
-constexpr int kPartCols = kN / kParts;         // 24 columns per epilogue warp and tile
+constexpr int kPartCols = kN / kParts;         // 32 columns per epilogue warp and tile
+constexpr int kGroups = kPartCols / 8;         // groups of 8 columns in the arithmetic
 constexpr int kTcThreads = 32 * (2 + kEpiWarps);
 constexpr int kTcWarps = kTcThreads / 32;
 constexpr uint32_t kRowB = 128;    // bytes per point and slice: 64 BF16 coordinates
 constexpr uint32_t kOwnSlice = kM * kRowB;                          // 16 KB
-constexpr uint32_t kOthSlice = kN * kRowB;                          // 6 KB
+constexpr uint32_t kOthSlice = kN * kRowB;                          // 12 KB
 constexpr uint32_t kOffOth = kSlices * kOwnSlice;                   // 80 KB
-constexpr int kSliceBufs = 3;                                       // tile tt: slice buffer tt % 3
-constexpr uint32_t kOffCol = kOffOth + kSliceBufs * kSlices * kOthSlice;  // + 90 KB
-constexpr uint32_t kOffBar = kOffCol;
-constexpr uint32_t kSmemBytes = kOffBar + 128 + 1024;               // barriers + 1024-byte alignment slack
-constexpr int kBufCols = kLevels * kN;                              // 240 TMEM columns per buffer
-constexpr uint32_t kTmemCols = 512;
+constexpr int kSliceBufs = 2;                                       // tile tt: slice buffer tt % 2
+constexpr int kRecSlots = 4;                                        // tile tt: record slot tt % 4
+constexpr uint32_t kRecBytes = kN * 16;                             // 1.5 KB
+constexpr uint32_t kOffRec = kOffOth + kSliceBufs * kSlices * kOthSlice;  // + 120 KB
+constexpr uint32_t kOffBar = kOffRec + kRecSlots * kRecBytes;            // + 6 KB
+constexpr uint32_t kSmemBytes = kOffBar + 256 + 1024;               // barriers, TMEM slot; 1024-byte alignment slack
+constexpr uint32_t kTmemCols = 512;                                 // 5 levels x 96 columns used
 constexpr int64_t kPadRows = 384;                                   // lcm(kM, kN)
 constexpr uint32_t kIdesc = idesc_bf16_f32(kM, kN);
+static_assert(kLevels * kN <= (int)kTmemCols, "level accumulators exceed TMEM");
 constexpr int kMinD = 17;  // the tensor-core path serves d >= kMinD
+constexpr double kLog2eD = 1.4426950408889634;
+constexpr double kLn2D = 0.6931471805599453;
+constexpr float kTheta2 = 12.0f;       // lazy-rescale threshold of the online max (base 2)
+constexpr float kPadQ = -8388608.0f;   // -2^23: Qh of padded points (weights 0), and the LSE max's start
+constexpr double kQLimit = 1048576.0;  // |P|, |Q| < 2^20: sums of grid values stay exact in FP32
 
-// Precomputed per point set (fixed for a problem).
+// Per-sweep data of an own point (written by tc_sweep_prep_kernel).
+struct OwnRec {
+  float ph;   // high part of P on the 1/8 grid
+  float pad;
+  double pl;  // P - ph, |pl| <= 1/16
+  double f1;  // 2^pl
+  double f2;  // 2^(2 pl): sums of squared entries
+};
+
+// Per point set: the fixed digit slices and |x - c|^2 (per problem), and the
+// per-sweep records of the point set in either role.
 struct Side {
   const __nv_bfloat16* slices;  // [kSlices][npad][64], 128-byte swizzle per 8-row atom
-  const float* sc;              // [npad] 2^e
-  const float* nxh;             // [npad] |x|^2 as an FP32 pair
-  const float* nxl;
+  const double* nx;             // [npad] |x - c|^2 (0 for padding)
+  float4* rec;                  // [npad] as the other side: {Qh, w0 2^ql, w1 2^ql, w2 2^ql}
+  OwnRec* own;                  // [npad] as the own side
   int64_t npad;
 };
 struct TcArgs {
   Side X, Y;
-  int* err;  // status word: kStatTimeout on a wait that ran out
+  const unsigned long long* emax;  // [2] bits of the FP64 max |x_k - c_k| of X and of Y
+  float* kappa;                    // [2] kappa as an FP32 pair (per sweep)
+  int* err;                        // status word: kStatTimeout on a wait that ran out, kStatRange
 };
 
 __host__ __device__ inline int64_t pad_rows(int64_t n) { return (n + kPadRows - 1) / kPadRows * kPadRows; }
 
-// One warp per point (rows >= n and coordinates >= d are zero). Both point sets
-// are first moved by the same centre (the first point of X): |x - y|^2 does not
-// change, but |x|^2, |y|^2 and x.y become bounded by the data's extent, so the
-// expansion |x|^2 + |y|^2 - 2 x.y keeps its relative accuracy however far the
-// clouds lie from the origin. The differences are exact in FP64.
+// E with every centred coordinate |x_k| < 2^E (0 for a cloud of one point).
+__device__ __forceinline__ int cloud_exp(unsigned long long bits) {
+  const double mx = __longlong_as_double((long long)bits);
+  int e = 0;
+  if (mx > 0.0) frexp(mx, &e);  // mx = f 2^e, f in [0.5, 1)
+  return e;
+}
+
+// max_{i,k} |x_ik - c_k| of one cloud (FP64, exact differences) into *emax as
+// the bits of a non-negative double (ordered like the values). *emax starts at 0.
+static __global__ void tc_extent_kernel(const float* X, int64_t n, int d, const float* centre,
+                                        unsigned long long* emax) {
+  pdl_wait();
+  double mx = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n * d;
+       i += (int64_t)gridDim.x * blockDim.x)
+    mx = fmax(mx, fabs((double)X[i] - (double)centre[i % d]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0 && mx > 0.0) atomicMax(emax, (unsigned long long)__double_as_longlong(mx));
+}
+
+// One warp per point (rows >= n and coordinates >= d are zero): the five digit
+// slices in the swizzled K-major layout and |x - c|^2 in FP64. Centring keeps
+// |x|^2, |y|^2 and x.y bounded by the data's extent, so the expansion
+// |x|^2 + |y|^2 - 2 x.y keeps its accuracy however far the clouds lie from the
+// origin.
 static __global__ void tc_prep_kernel(const float* X, int64_t n, int d, int64_t npad, const float* centre,
-                                      __nv_bfloat16* sl, float* sc, float* nxh, float* nxl) {
+                                      const unsigned long long* emax, __nv_bfloat16* sl, double* nx) {
   pdl_wait();
   const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -94,21 +154,11 @@ static __global__ void tc_prep_kernel(const float* X, int64_t n, int d, int64_t 
     if (lane < d) xv[0] = (double)X[row * d + lane] - (double)centre[lane];
     if (lane + 32 < d) xv[1] = (double)X[row * d + lane + 32] - (double)centre[lane + 32];
   }
-  double mx = fmax(fabs(xv[0]), fabs(xv[1]));
   double q = xv[0] * xv[0] + xv[1] * xv[1];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    q += __shfl_xor_sync(0xffffffffu, q, o);
-  }
-  int e = 0;
-  if (mx > 0.0) frexp(mx, &e);  // mx = f 2^e, f in [0.5, 1): every |x_k| < 2^e
-  if (lane == 0) {
-    sc[row] = ldexpf(1.f, e);
-    const float h = (float)q;
-    nxh[row] = h;
-    nxl[row] = (float)(q - (double)h);
-  }
+  for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+  const int e = cloud_exp(*emax);
+  if (lane == 0) nx[row] = q;
 #pragma unroll
   for (int c = 0; c < 2; ++c) {
     const int k = lane + 32 * c;
@@ -125,17 +175,88 @@ static __global__ void tc_prep_kernel(const float* X, int64_t n, int d, int64_t 
   }
 }
 
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = add_rn(a, b);
-  const float z = sub_rn(s, a);
-  e = add_rn(sub_rn(a, sub_rn(s, z)), sub_rn(b, z));
+// Before each sweep: kappa, the other side's records (all npad of them; padded
+// points get Qh = -2^23 and weights 0, so no tile needs a mask) and the own
+// side's P split. The same gamma as the sweep: (float) of the device value.
+template <int NR, int SQM, bool ROWS>
+__global__ void tc_sweep_prep_kernel(SweepArgs<float> a, TcArgs ta) {
+  pdl_wait();
+  if (a.active && *a.active == 0.0) return;
+  const Side so = ROWS ? ta.X : ta.Y;
+  const Side sq = ROWS ? ta.Y : ta.X;
+  const int64_t n_own = ROWS ? a.n : a.m, n_oth = ROWS ? a.m : a.n;
+  const float g = a.gamma_dev ? (float)*a.gamma_dev : a.gamma;
+  const double K = (double)g * a.sC;
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i == 0) {
+    const double kap = 2.0 * K * ldexp(1.0, cloud_exp(ta.emax[0]) + cloud_exp(ta.emax[1]) - 16) * kLog2eD;
+    const float kh = (float)kap;
+    ta.kappa[0] = kh;
+    ta.kappa[1] = (float)(kap - (double)kh);
+  }
+  if (i < sq.npad) {
+    float4 r = make_float4(kPadQ, 0.f, 0.f, 0.f);
+    if (i < n_oth) {
+      const float* hq = ROWS ? a.Bh : a.Ah;
+      const double Q = ((double)hq[i] - K * sq.nx[i]) * kLog2eD;
+      if (!(fabs(Q) < kQLimit)) atomicOr(ta.err, kStatRange);
+      const double qh = rint(Q * 8.0) * kGrid;
+      const double ql = Q - qh;
+      const double f1 = exp2(ql);
+      const double f2 = SQM ? exp2(2.0 * ql) : 0.0;
+      const float* const* wt = ROWS ? a.wc : a.wr;
+      r.x = (float)qh;
+      r.y = (float)((double)wt[0][i] * ((SQM & 1) ? f2 : f1));
+      if constexpr (NR > 1) r.z = (float)((double)wt[1][i] * ((SQM & 2) ? f2 : f1));
+      if constexpr (NR > 2) r.w = (float)((double)wt[2][i] * ((SQM & 4) ? f2 : f1));
+    }
+    sq.rec[i] = r;
+  } else if (i < sq.npad + so.npad) {
+    const int64_t e = i - sq.npad;
+    OwnRec o{0.f, 0.f, 0.0, 1.0, 1.0};
+    if (e < n_own) {
+      const float* ho = ROWS ? a.Ah : a.Bh;
+      const double P = ((double)ho[e] - K * so.nx[e]) * kLog2eD;
+      if (!(fabs(P) < kQLimit)) atomicOr(ta.err, kStatRange);
+      const double ph = rint(P * 8.0) * kGrid;
+      o.ph = (float)ph;
+      o.pl = P - ph;
+      o.f1 = exp2(o.pl);
+      o.f2 = SQM ? exp2(2.0 * o.pl) : 1.0;
+    }
+    so.own[e] = o;
+  }
+}
+
+// t2 = hq + kappa G with hq = Ph + Qh (or Ph - max + Qh), exact on the grid.
+__device__ __forceinline__ float entry_t2(float hq, float gh, float gl, float kh, float kl) {
+  const float b = fmaf(kh, gh, hq);
+  const float c = fmaf(kl, gh, __fmul_rn(kh, gl));
+  return __fadd_rn(b, c);
+}
+
+// Base-2 log-sum-exp pairs (m on the 1/8 grid, s >= 0; s == 0: empty). The
+// exponent difference is exact, so the FP32 ex2 rounds once.
+__device__ __forceinline__ void lse2_add(double& M, double& s, double qm, double qs) {
+  if (!(qs > 0.0)) return;
+  if (!(s > 0.0)) {
+    M = qm;
+    s = qs;
+    return;
+  }
+  const double Mn = fmax(M, qm);
+  s = s * (double)ex2_approx((float)(M - Mn)) + qs * (double)ex2_approx((float)(qm - Mn));
+  M = Mn;
 }
 
 // Waits by lane 0 only, result broadcast: keeps the warp converged before the
 // .sync.aligned TMEM loads.
+// Each poll may sleep up to kEpiSleepNs, so that waiting epilogue warps leave
+// the issue slots of their SM sub-partition to the MMA-issuing thread.
+constexpr uint32_t kEpiSleepNs = 200;
 __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, int* err) {
   int ok = 1;
-  if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, err, kStatTimeout) ? 1 : 0;
+  if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, err, kStatTimeout, kTcWaitNs, kEpiSleepNs) ? 1 : 0;
   return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }
 
@@ -143,13 +264,14 @@ template <int NR, bool LSE, int SQM, bool ROWS, class Epi>
 __global__ void __launch_bounds__(kTcThreads, 1) tc_sweep_kernel(SweepArgs<float> a, TcArgs ta, Epi epi) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* full = (uint64_t*)(sm + kOffBar);  // [3] per slice buffer
-  uint64_t* mmad = full + 3;                   // [2] per TMEM buffer
-  uint64_t* tfree = full + 5;                  // [2] per TMEM buffer
-  uint64_t* ownf = full + 7;
-  uint32_t* tslot = (uint32_t*)(full + 8);
+  uint64_t* full = (uint64_t*)(sm + kOffBar);  // [2] slices of the slice buffer landed
+  uint64_t* sfree = full + 2;                  // [2] MMAs reading the slice buffer done
+  uint64_t* lvl = full + 4;                    // [5] MMAs of level L done (accumulator readable)
+  uint64_t* lfree = full + 9;                  // [5] level L loaded by all epilogue warps
+  uint64_t* recf = full + 14;                  // [4] records of the slot landed
+  uint64_t* ownf = full + 18;
+  uint32_t* tslot = (uint32_t*)(full + 19);
   constexpr int NA = LSE ? 1 : NR;
-  constexpr int NW = LSE ? 1 : NR;
   constexpr int ND = Epi::kDot;
   __shared__ float hsum[kParts - 1][NA][kM], hcmp[kParts - 1][NA][kM], hmax[kParts - 1][kM];
   __shared__ int last_blk;
@@ -163,13 +285,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_sweep_kernel(SweepArgs<float
   const int T = (int)((j1 - j0 + kN - 1) / kN);
 
   if (threadIdx.x == 0) {
-    mbar_init(&full[0], 1);
-    mbar_init(&full[1], 1);
-    mbar_init(&full[2], 1);
-    mbar_init(&mmad[0], 1);
-    mbar_init(&mmad[1], 1);
-    mbar_init(&tfree[0], kEpiWarps);
-    mbar_init(&tfree[1], kEpiWarps);
+    for (int k = 0; k < kSliceBufs; ++k) {
+      mbar_init(&full[k], 1);
+      mbar_init(&sfree[k], 1);
+    }
+    for (int L = 0; L < kLevels; ++L) {
+      mbar_init(&lvl[L], 1);
+      mbar_init(&lfree[L], kEpiWarps);
+    }
+    for (int k = 0; k < kRecSlots; ++k) mbar_init(&recf[k], 1);
     mbar_init(ownf, 1);
     mbar_fence_init();
   }
@@ -190,16 +314,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_sweep_kernel(SweepArgs<float
   const int r = 32 * q + lane;
   const int64_t e = blk * kM + r;
   const bool ev = warp >= 2 && e < n_own;
-  float Sa[NA], Ca[NA], mx = 0.f;
-  bool mx_set = false;
+  float Sa[NA], Ca[NA], mx = kPadQ;
 #pragma unroll
   for (int k = 0; k < NA; ++k) {
     Sa[k] = 0.f;
     Ca[k] = 0.f;
   }
 
-  const float* ht = ROWS ? a.Bh : a.Ah;
-  const float* const* wt = ROWS ? a.wc : a.wr;
   if (warp == 0) {
     // ---------------- copies and MMAs (one thread) ----------------
     if (lane == 0) {
@@ -208,158 +329,212 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_sweep_kernel(SweepArgs<float
       mbar_arrive_expect_tx(ownf, kSlices * kOwnSlice);
       for (int s = 0; s < kSlices; ++s)
         bulk_g2s(sm + s * kOwnSlice, own_src + (int64_t)s * so.npad * kRowB, kOwnSlice, ownf);
-      // tile tt: its slices into buffer tt % 2, its per-point data into slot tt % 4
-      // (48 floats per array; the arrays hold at least 47 entries past n, and
-      // the epilogue masks j >= j1)
+      // tile tt: its slices into buffer tt % 2, its records into slot tt % 4
+      // (the record arrays hold npad >= every tile's last point)
       auto issue = [&](int tt) {
-        const int sb = tt % kSliceBufs;
+        const int sb = tt % kSliceBufs, rs = tt % kRecSlots;
         const int64_t jt = j0 + (int64_t)tt * kN;
         mbar_arrive_expect_tx(&full[sb], kSlices * kOthSlice);
         const unsigned char* src = oth_src + jt * kRowB;
         for (int s = 0; s < kSlices; ++s)
           bulk_g2s(sm + kOffOth + (sb * kSlices + s) * kOthSlice, src + (int64_t)s * sq.npad * kRowB, kOthSlice,
                    &full[sb]);
+        mbar_arrive_expect_tx(&recf[rs], kRecBytes);
+        bulk_g2s(sm + kOffRec + rs * kRecBytes, sq.rec + jt, kRecBytes, &recf[rs]);
       };
-      // Schedule: tiles 0 and 1 are prefetched; after committing tile tt the
-      // copies of tile tt + 2 go into the slice buffer of tile tt - 1 once its
-      // MMAs are done (queued before tile tt's, so the tensor pipe stays busy)
-      // and into the column slot of tile tt - 2, whose epilogue finished before
-      // the MMAs of tile tt were issued.
-      int issued = 0, landed = 0, committed = 0, retired = 0;
+      // Schedule. Tiles 0 and 1 are prefetched. The MMAs of tile tt go level by
+      // level, each level once the epilogue has loaded that level of tile
+      // tt - 1 (lfree), with a commit per level (lvl) and one for the slice
+      // buffer (sfree). After queueing tile tt, the copies of tile tt + 1 go
+      // into the buffer of tile tt - 1 once its MMAs are done, and into the
+      // record slot of tile tt - 3: the epilogue loaded tile tt - 1 before the
+      // MMAs of tile tt were issued, so it had finished every tile up to tt - 2.
+      int issued = 0, landed = 0, committed = 0, freed = 0;
       for (; issued < 2 && issued < T; ++issued) issue(issued);
       const bool own_ok = mbar_wait(ownf, 0, ta.err, kStatTimeout);
-      const uint32_t own_s = smem_u32(sm);
-      for (int tt = 0; own_ok && tt < T; ++tt) {
-        const int b = tt & 1, sb = tt % kSliceBufs;
+      // descriptors of the first own slice and of the first other-side slice;
+      // every MMA of a tile adds a compile-time offset (all 60 unrolled)
+      const uint64_t adesc0 = desc_sw128(smem_u32(sm));
+      const uint64_t bdesc0 = desc_sw128(smem_u32(sm + kOffOth));
+      bool ok = own_ok;
+      for (int tt = 0; ok && tt < T; ++tt) {
+        const int sb = tt % kSliceBufs;
         if (!mbar_wait(&full[sb], (tt / kSliceBufs) & 1, ta.err, kStatTimeout)) break;
         landed = tt + 1;
-        if (tt >= 2 && !mbar_wait(&tfree[b], ((tt - 2) >> 1) & 1, ta.err, kStatTimeout)) break;
-        tc_fence_after();
-        const uint32_t oth_s = smem_u32(sm + kOffOth + sb * kSlices * kOthSlice);
-#pragma unroll 1
-        for (int L = 0; L < kLevels; ++L) {
-          const uint32_t d_tmem = tbase + (uint32_t)(b * kBufCols + L * kN);
-          uint32_t acc = 0;
-          for (int s = (L > kSlices - 1 ? L - (kSlices - 1) : 0); s <= L && s < kSlices; ++s) {
-            const int t = L - s;
+        const uint64_t bdesc = bdesc0 + (uint64_t)((sb * kSlices * kOthSlice) >> 4);
 #pragma unroll
-            for (int k4 = 0; k4 < 4; ++k4) {
-              mma_bf16(d_tmem, desc_sw128(own_s + s * kOwnSlice + k4 * 32),
-                       desc_sw128(oth_s + t * kOthSlice + k4 * 32), kIdesc, acc);
-              acc = 1;
+        for (int L = 0; L < kLevels; ++L) {
+          if (tt >= 1 && !mbar_wait(&lfree[L], (tt - 1) & 1, ta.err, kStatTimeout)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+#pragma unroll
+          for (int k4 = 0; k4 < 4; ++k4)
+#pragma unroll
+            for (int s = 0; s < kSlices; ++s) {
+              const int t = L - s;
+              if (t < 0 || t >= kSlices) continue;
+              mma_bf16(tbase + (uint32_t)(L * kN), adesc0 + (uint64_t)((s * kOwnSlice + k4 * 32) >> 4),
+                       bdesc + (uint64_t)((t * kOthSlice + k4 * 32) >> 4), kIdesc,
+                       (k4 == 0 && s == (L > kSlices - 1 ? L - (kSlices - 1) : 0)) ? 0u : 1u);
             }
-          }
+          mma_commit(&lvl[L]);
         }
-        mma_commit(&mmad[b]);
+        if (!ok) break;
+        mma_commit(&sfree[sb]);
         committed = tt + 1;
-        if (tt + 2 < T) {
+        if (tt + 1 < T && tt + 1 >= issued) {
           if (tt >= 1) {
-            if (!mbar_wait(&mmad[(tt - 1) & 1], ((tt - 1) >> 1) & 1, ta.err, kStatTimeout)) break;
-            retired = tt;
+            if (!mbar_wait(&sfree[(tt - 1) % kSliceBufs], ((tt - 1) / kSliceBufs) & 1, ta.err, kStatTimeout)) break;
+            freed = tt;
           }
-          issue(tt + 2);
+          issue(tt + 1);
           ++issued;
         }
       }
       // leave nothing in flight (bounded waits that ignore the error flag):
-      // copies issued but not seen landed, and the MMAs not seen retired
+      // slices issued but not seen landed, the records of the last four tiles
+      // issued (an earlier slot was reused only after the epilogue had read
+      // it), and the MMAs of the tiles whose buffer was not seen free. A tile
+      // whose levels were only partly issued ends with the commits issued.
       if (!own_ok) mbar_wait(ownf, 0, ta.err, 0, kTcDrainNs);
       for (int tt = landed; tt < issued; ++tt)
         mbar_wait(&full[tt % kSliceBufs], (tt / kSliceBufs) & 1, ta.err, 0, kTcDrainNs);
-      for (int tt = (retired > committed - 2 ? retired : committed - 2); tt < committed; ++tt)
-        if (tt >= 0) mbar_wait(&mmad[tt & 1], (tt >> 1) & 1, ta.err, 0, kTcDrainNs);
+      for (int tt = (issued > kRecSlots ? issued - kRecSlots : 0); tt < issued; ++tt)
+        mbar_wait(&recf[tt % kRecSlots], (tt / kRecSlots) & 1, ta.err, 0, kTcDrainNs);
+      for (int tt = freed; tt < committed; ++tt)
+        mbar_wait(&sfree[tt % kSliceBufs], (tt / kSliceBufs) & 1, ta.err, 0, kTcDrainNs);
+      if (!ok && landed > committed) {  // a partly issued tile: wait for its MMAs too
+        mma_commit(&sfree[(landed - 1) % kSliceBufs]);
+        mbar_wait(&sfree[(landed - 1) % kSliceBufs], ((landed - 1) / kSliceBufs) & 1, ta.err, 0, kTcDrainNs);
+      }
     }
     __syncwarp();
   } else if (warp >= 2) {
     // ---------------- epilogue ----------------
-    const float* ho = ROWS ? a.Ah : a.Bh;
-    const float h = ev ? ho[e] : 0.f;
-    float hm = h;
-    const float sc_own = so.sc[e], nxh = so.nxh[e], nxl = so.nxl[e];  // e < npad
-    const float g = a.gamma_dev ? (float)*a.gamma_dev : a.gamma;
-    float Kh, Kl;
-    split_k<float>((double)g * a.sC, Kh, Kl);
-    const uint32_t lane_base = (uint32_t)(32 * q) << 16;
+    const float ph = so.own[e].ph;  // e < npad: padded rows have records
+    const float kh = ta.kappa[0], kl = ta.kappa[1];
+    // LSE: hm = ph - mx. The max starts at -2^23, far below every entry, so the
+    // first group of columns raises it to its own maximum (the one inexact step,
+    // it only chooses the shift); from then on ph and mx are on the grid and
+    // hm is exact.
+    float hm = LSE ? ph - mx : ph;
+    const uint32_t tcol = tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(part * kPartCols);
+    const float4* recs = (const float4*)(sm + kOffRec);
     for (int tt = 0; tt < T; ++tt) {
-      const int b = tt & 1;
-      if (!warp_wait(&mmad[b], (tt >> 1) & 1, ta.err)) break;  // also covers the tile's copies
+      const uint32_t par = (uint32_t)tt & 1u;
+      // G as an FP32 pair per column, folded level by level; each level goes
+      // back to the MMAs of the next tile as soon as it is in registers
+      uint32_t gh[kPartCols], gl[kPartCols], u[kPartCols];
+      if (!warp_wait(&lvl[0], par, ta.err)) break;
       tc_fence_after();
-      const int64_t jt = j0 + (int64_t)tt * kN;
-#pragma unroll 1
-      for (int c = 0; c < kPartCols / 8; ++c) {
-        const int col0 = part * kPartCols + c * 8;
-        uint32_t lv[kLevels][8];
+      tmem_ld32(tcol, gh);
+      if (!warp_wait(&lvl[1], par, ta.err)) break;
+      tc_fence_after();
+      tmem_ld32(tcol + (uint32_t)kN, gl);
+      tmem_ld_wait();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(&lfree[0]);
+        mbar_arrive(&lfree[1]);
+      }
+      // G = S_0 + 2^-8 S_1 + ... as an FP32 pair (gh, gl). S_0 is an integer
+      // below 2^22 and 2^-8 S_1 a multiple of 2^-8 below 2^15: where
+      // |S_0| >= |2^-8 S_1| Fast2Sum is exact, and otherwise the sum lies below
+      // 2^16 on the 2^-8 grid and is exact already (z = 2^-8 S_1, error 0).
 #pragma unroll
-        for (int L = 0; L < kLevels; ++L)
-          tmem_ld8(tbase + lane_base + (uint32_t)(b * kBufCols + L * kN + col0), lv[L]);
+      for (int c = 0; c < kPartCols; ++c) {
+        const float s0 = __uint_as_float(gh[c]), s1 = __uint_as_float(gl[c]);
+        const float h = fmaf(s1, 0x1p-8f, s0);
+        const float z = __fsub_rn(h, s0);
+        gh[c] = __float_as_uint(h);
+        gl[c] = __float_as_uint(fmaf(s1, 0x1p-8f, -z));
+      }
+      bool ok = true;
+#pragma unroll
+      for (int L = 2; L < kLevels; ++L) {
+        if (!warp_wait(&lvl[L], par, ta.err)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        tmem_ld32(tcol + (uint32_t)(L * kN), u);
         tmem_ld_wait();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&lfree[L]);
+        const float sc = L == 2 ? 0x1p-16f : (L == 3 ? 0x1p-24f : 0x1p-32f);
+#pragma unroll
+        for (int c = 0; c < kPartCols; ++c)
+          gl[c] = __float_as_uint(fmaf(__uint_as_float(u[c]), sc, __uint_as_float(gl[c])));
+      }
+      if (!ok) break;
+      const int rs = tt % kRecSlots;
+      if (!warp_wait(&recf[rs], (uint32_t)(tt / kRecSlots) & 1u, ta.err)) break;
+      const float4* rt = recs + rs * kN + part * kPartCols;
+#pragma unroll
+      for (int c = 0; c < kGroups; ++c) {
         float acc[NA];
 #pragma unroll
         for (int k = 0; k < NA; ++k) acc[k] = 0.f;
+        if constexpr (!LSE) {
 #pragma unroll
-        for (int jj = 0; jj < 8; ++jj) {
-          const int cj = col0 + jj;
-          if (j0 + (int64_t)tt * kN + cj >= j1) break;  // uniform across the warp
-          const int64_t j = jt + cj;
-          const float hb = ht[j];
-          const float f = sc_own * sq.sc[j] * 0x1p-16f;  // powers of two: exact
-          float gh, gl;
-          two_sum(__uint_as_float(lv[0][jj]), __uint_as_float(lv[1][jj]) * 0x1p-8f, gh, gl);
-          gl += __uint_as_float(lv[2][jj]) * 0x1p-16f +
-                (__uint_as_float(lv[3][jj]) * 0x1p-24f + __uint_as_float(lv[4][jj]) * 0x1p-32f);
-          gh *= f;
-          gl *= f;
-          float s1, e1, Dh, e2;
-          two_sum(nxh, sq.nxh[j], s1, e1);
-          two_sum(s1, -2.f * gh, Dh, e2);
-          const float Dl = e2 + ((e1 + (nxl + sq.nxl[j])) - 2.f * gl);
-          if constexpr (!LSE) {
-            const float ex = expT(expo<true>(h + hb, Kh, Kl, Dh, Dl));
+          for (int jj = 0; jj < 8; ++jj) {
+            const float4 R = rt[c * 8 + jj];
+            const float ex = ex2_approx(entry_t2(__fadd_rn(hm, R.x), __uint_as_float(gh[c * 8 + jj]),
+                                                 __uint_as_float(gl[c * 8 + jj]), kh, kl));
+            const float ws[3] = {R.y, R.z, R.w};
 #pragma unroll
-            for (int k = 0; k < NR; ++k) {
-              const float w = wt[k][j];
-              if ((SQM >> k) & 1) acc[k] = fmaf(ex * ex, w, acc[k]);
-              else acc[k] = fmaf(ex, w, acc[k]);
-            }
-          } else {
-            if (!mx_set) {  // the running max starts at the first element
-              mx = ceil_grid(expo<true>(h + hb, Kh, Kl, Dh, Dl));
-              hm = h - mx;
-              mx_set = true;
-            }
-            float tv = expo<true>(hm + hb, Kh, Kl, Dh, Dl);
-            for (int k = 0; k < 4 && tv > kTheta; ++k) {
-              const float dlt = ceil_grid(tv);
-              mx += dlt;
-              hm = h - mx;
-              const float fsc = expT(-dlt);
-              acc[0] *= fsc;
-              Sa[0] *= fsc;
-              Ca[0] *= fsc;
-              tv = expo<true>(hm + hb, Kh, Kl, Dh, Dl);
-            }
-            acc[0] = fmaf(expT(tv), wt[0][j], acc[0]);
+            for (int k = 0; k < NR; ++k) acc[k] = fmaf(((SQM >> k) & 1) ? ex * ex : ex, ws[k], acc[k]);
           }
+        } else {
+          float qh[8], w[8], t[8];
+          float tmax = -3.0e38f;
+#pragma unroll
+          for (int jj = 0; jj < 8; ++jj) {
+            const float4 R = rt[c * 8 + jj];
+            qh[jj] = R.x;
+            w[jj] = R.y;
+            t[jj] = entry_t2(__fadd_rn(hm, qh[jj]), __uint_as_float(gh[c * 8 + jj]),
+                             __uint_as_float(gl[c * 8 + jj]), kh, kl);
+            tmax = fmaxf(tmax, t[jj]);
+          }
+          for (int k = 0; k < 4 && tmax > kTheta2; ++k) {  // raise the max (rare after the first group)
+            const float dlt = ceil_grid(tmax);
+            mx += dlt;
+            hm = ph - mx;
+            const float f = ex2_approx(-dlt);
+            Sa[0] *= f;
+            Ca[0] *= f;
+            tmax = -3.0e38f;
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj) {
+              t[jj] = entry_t2(__fadd_rn(hm, qh[jj]), __uint_as_float(gh[c * 8 + jj]),
+                               __uint_as_float(gl[c * 8 + jj]), kh, kl);
+              tmax = fmaxf(tmax, t[jj]);
+            }
+          }
+#pragma unroll
+          for (int jj = 0; jj < 8; ++jj) acc[0] = fmaf(ex2_approx(t[jj]), w[jj], acc[0]);
         }
 #pragma unroll
         for (int k = 0; k < NA; ++k) kadd(Sa[k], Ca[k], acc[k]);
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&tfree[b]);
     }
-    if (part > 0) {  // parts 1-3 hand their sums to part 0
+    if (part > 0) {  // parts 1 and 2 hand their sums to part 0
 #pragma unroll
       for (int k = 0; k < NA; ++k) {
         hsum[part - 1][k][r] = Sa[k];
         hcmp[part - 1][k][r] = Ca[k];
       }
-      hmax[part - 1][r] = mx_set ? mx : 0.f;
+      hmax[part - 1][r] = mx;
     }
   }
   pdl_trigger();
   tc_fence_before();
-  __syncthreads();  // every TMEM read and MMA is done; the halves are in shared memory
+  __syncthreads();  // every TMEM read and MMA is done; the parts are in shared memory
   if (warp == 1) {
     tc_fence_after();
     tmem_free(tbase, kTmemCols);
@@ -374,16 +549,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_sweep_kernel(SweepArgs<float
         a.rowpart[((int64_t)k * S + sidx) * n_own + e] = v;
       }
     } else {
-      LsePair p{0.0, 0.0};
-      const double s0 = (double)Sa[0] + (double)Ca[0];
-      if (s0 > 0.0) p = lse_combine<float>(p, LsePair{(double)mx, s0});
+      double M = 0.0, s = 0.0;
+      lse2_add(M, s, (double)mx, (double)Sa[0] + (double)Ca[0]);
 #pragma unroll
-      for (int pp = 0; pp < kParts - 1; ++pp) {
-        const double sp = (double)hsum[pp][0][r] + (double)hcmp[pp][0][r];
-        if (sp > 0.0) p = lse_combine<float>(p, LsePair{(double)hmax[pp][r], sp});
-      }
-      a.rowpart[((int64_t)0 * S + sidx) * n_own + e] = p.m;
-      a.rowpart[((int64_t)1 * S + sidx) * n_own + e] = p.s;
+      for (int pp = 0; pp < kParts - 1; ++pp)
+        lse2_add(M, s, (double)hmax[pp][r], (double)hsum[pp][0][r] + (double)hcmp[pp][0][r]);
+      a.rowpart[((int64_t)0 * S + sidx) * n_own + e] = M;
+      a.rowpart[((int64_t)1 * S + sidx) * n_own + e] = s;
     }
   }
   __syncthreads();
@@ -402,23 +574,25 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_sweep_kernel(SweepArgs<float
   if (threadIdx.x < kM) {
     const int64_t ee = blk * kM + threadIdx.x;
     if (ee < n_own) {
+      const OwnRec o = so.own[ee];
       DotArr<ND> dd;
       if constexpr (!LSE) {
         double tot[NR];
 #pragma unroll
         for (int k = 0; k < NR; ++k) {
           double v = 0.0;
-          ordered_loads(a.rowpart + (int64_t)k * S * n_own + ee, n_own, S, [&](double q) { v += q; });
-          tot[k] = v;
+          ordered_loads(a.rowpart + (int64_t)k * S * n_own + ee, n_own, S, [&](double qv) { v += qv; });
+          tot[k] = v * (((SQM >> k) & 1) ? o.f2 : o.f1);
         }
         if constexpr (ROWS) epi.row(ee, tot, dd.v);
         else epi.col(ee, tot, dd.v);
       } else {
-        LsePair p{0.0, 0.0};
+        double M = 0.0, s = 0.0;
         ordered_loads2(a.rowpart + ee, a.rowpart + S * n_own + ee, n_own, S,
-                       [&](double qm, double qs) { p = lse_combine<float>(p, LsePair{qm, qs}); });
-        if constexpr (ROWS) epi.row_lse(ee, p.m, p.s, dd.v);
-        else epi.col_lse(ee, p.m, p.s, dd.v);
+                       [&](double qm, double qs) { lse2_add(M, s, qm, qs); });
+        const double m_nat = s > 0.0 ? (M + o.pl) * kLn2D : 0.0;
+        if constexpr (ROWS) epi.row_lse(ee, m_nat, s, dd.v);
+        else epi.col_lse(ee, m_nat, s, dd.v);
       }
 #pragma unroll
       for (int k = 0; k < ND; ++k) wd[k] = dd.v[k];

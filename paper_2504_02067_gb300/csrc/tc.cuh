@@ -50,6 +50,19 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+// The same test, letting the thread sleep up to hint_ns while the phase is open
+// (for consumers whose wait is long compared with a poll).
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, uint32_t parity, uint32_t hint_ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+      : "memory");
+  return ok != 0;
+}
 // Waits for the completion of the phase with the given parity; false (and *err
 // set) if that takes longer than kTcWaitNs or *err is already set.
 // The bound needs both kMinPolls polls and limit_ns of %globaltimer (the timer
@@ -57,12 +70,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 // always end the wait (in case the timer stands still).
 constexpr uint32_t kMinPolls = 1u << 20;
 constexpr uint32_t kMaxPolls = 1u << 28;
+// With sleep_ns > 0 each poll may sleep that long while the phase is open.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, int err_bit,
-                                          unsigned long long limit_ns = kTcWaitNs) {
+                                          unsigned long long limit_ns = kTcWaitNs, uint32_t sleep_ns = 0) {
   const unsigned long long t0 = now_ns();
   const uint32_t min_polls = limit_ns < kTcWaitNs ? kMinPolls >> 6 : kMinPolls;
   for (uint32_t it = 0;; ++it) {
-    if (mbar_try_wait(bar, parity)) return true;
+    if (sleep_ns ? mbar_try_wait_sleep(bar, parity, sleep_ns) : mbar_try_wait(bar, parity)) return true;
     if ((it & 15u) == 15u) {
       if (*(volatile int*)err & err_bit) return false;
       if ((it >= min_polls && now_ns() - t0 > limit_ns) || it >= kMaxPolls) {
@@ -102,7 +116,9 @@ __device__ __forceinline__ void tc_fence_after() {
 }
 
 // D[tmem] (+)= A[smem] x B[smem]^T, kind::f16 (BF16 in, FP32 accumulate), issued
-// by one thread; accumulate = 0 overwrites D.
+// by one thread; accumulate = 0 overwrites D. A descriptor's start-address field
+// is linear in the address: desc(addr + off) = desc(addr) + off / 16 while the
+// address stays below 256 KB.
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                          uint32_t accumulate) {
   asm volatile(
@@ -126,6 +142,18 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
                  "=r"(r[7])
                : "r"(taddr)
                : "memory");
+}
+// 32 lanes x 32 consecutive 32-bit columns.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
+      "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
 }
 // 32 lanes x 4 consecutive 32-bit columns.
 __device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&r)[4]) {
