@@ -37,18 +37,21 @@
 // fill 480 of the 512 TMEM columns, one buffer, handed over level by level.
 //
 // CTA roles (448 threads, one CTA per SM: about 215 KB of shared memory):
-//   warp 0, lane 0: bulk copies (the own 128 points' slices once; the other
-//     side's 96-point tiles into two slice buffers and their records into four
-//     record slots) and the 60 MMAs of each tile, level by level, with a
-//     commit per level;
-//   warp 1: TMEM allocation (512 columns) and release;
+//   warp 0, lane 0: the 60 MMAs of each tile, level by level, with a commit per
+//     level. A tcgen05.mma blocks its thread while the tensor unit's short
+//     queue is full, so this thread does nothing else: any other work in it
+//     leaves the tensor unit idle;
+//   warp 1: TMEM allocation (512 columns) and release; lane 0 issues the bulk
+//     copies (the own 128 points' slices once; the other side's 96-point
+//     tiles into two slice buffers and their records into four record slots);
 //   warps 2-13: epilogue. Warp w reads TMEM lanes 32 (w mod 4) .. +31 (one own
 //     point per thread) and a third (32) of the tile's 96 columns.
-// Hand-offs are mbarriers: full[sb] (slices landed), sfree[sb] (the MMAs
-// reading slice buffer sb are done), rec[s] (records landed), lvl[L] (the MMAs
-// of level L are done: accumulator readable), lfree[L] (the 12 epilogue warps
-// have loaded level L into registers; the next tile's level-L MMAs may
-// overwrite it). Every wait is bounded (tc.cuh).
+// Hand-offs are mbarriers: full[sb] (the slices of buffer sb landed), sfree[sb]
+// (the MMAs reading buffer sb are done), rec[s] (records landed), lvl[g] (the
+// MMAs of level group g = {0,1}, {2,3}, {4} are done: accumulators readable),
+// lfree[0] / lfree[1] (the 12 epilogue warps have loaded levels 0-3 / level 4
+// into registers; the next tile's MMAs may overwrite them). Every wait is
+// bounded (tc.cuh).
 #pragma once
 #include <cuda_bf16.h>
 
@@ -264,13 +267,13 @@ template <int NR, bool LSE, int SQM, bool ROWS, class Epi>
 __global__ void __launch_bounds__(kTcThreads, 1) tc_sweep_kernel(SweepArgs<float> a, TcArgs ta, Epi epi) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* full = (uint64_t*)(sm + kOffBar);  // [2] slices of the slice buffer landed
+  uint64_t* full = (uint64_t*)(sm + kOffBar);  // [2] the five slices of the slice buffer landed
   uint64_t* sfree = full + 2;                  // [2] MMAs reading the slice buffer done
-  uint64_t* lvl = full + 4;                    // [5] MMAs of level L done (accumulator readable)
-  uint64_t* lfree = full + 9;                  // [5] level L loaded by all epilogue warps
-  uint64_t* recf = full + 14;                  // [4] records of the slot landed
-  uint64_t* ownf = full + 18;
-  uint32_t* tslot = (uint32_t*)(full + 19);
+  uint64_t* lvl = full + 4;                    // [3] MMAs of levels {0,1}, {2,3}, {4} done
+  uint64_t* lfree = full + 7;                  // [2] levels 0-3, level 4 loaded by all epilogue warps
+  uint64_t* recf = full + 9;                   // [4] records of the slot landed
+  uint64_t* ownf = full + 13;
+  uint32_t* tslot = (uint32_t*)(full + 14);
   constexpr int NA = LSE ? 1 : NR;
   constexpr int ND = Epi::kDot;
   __shared__ float hsum[kParts - 1][NA][kM], hcmp[kParts - 1][NA][kM], hmax[kParts - 1][kM];
@@ -289,10 +292,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_sweep_kernel(SweepArgs<float
       mbar_init(&full[k], 1);
       mbar_init(&sfree[k], 1);
     }
-    for (int L = 0; L < kLevels; ++L) {
-      mbar_init(&lvl[L], 1);
-      mbar_init(&lfree[L], kEpiWarps);
-    }
+    for (int g = 0; g < 3; ++g) mbar_init(&lvl[g], 1);
+    for (int g = 0; g < 2; ++g) mbar_init(&lfree[g], kEpiWarps);
     for (int k = 0; k < kRecSlots; ++k) mbar_init(&recf[k], 1);
     mbar_init(ownf, 1);
     mbar_fence_init();
@@ -321,94 +322,109 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_sweep_kernel(SweepArgs<float
     Ca[k] = 0.f;
   }
 
-  if (warp == 0) {
-    // ---------------- copies and MMAs (one thread) ----------------
+  if (warp == 1) {
+    // ---------------- bulk copies (one thread) ----------------
+    // The own 128 points' slices once; tile tt's five slices into buffer tt % 2
+    // and its records into slot tt % 4. Tiles 0 and 1 go at once; tile tt >= 2 once the MMAs of tile
+    // tt - 2 are done (sfree), by when the epilogue had loaded tile tt - 3 and
+    // so finished tile tt - 4, the previous user of the record slot.
     if (lane == 0) {
       const unsigned char* own_src = (const unsigned char*)so.slices + blk * (int64_t)kM * kRowB;
       const unsigned char* oth_src = (const unsigned char*)sq.slices;
       mbar_arrive_expect_tx(ownf, kSlices * kOwnSlice);
       for (int s = 0; s < kSlices; ++s)
         bulk_g2s(sm + s * kOwnSlice, own_src + (int64_t)s * so.npad * kRowB, kOwnSlice, ownf);
-      // tile tt: its slices into buffer tt % 2, its records into slot tt % 4
-      // (the record arrays hold npad >= every tile's last point)
-      auto issue = [&](int tt) {
+      int issued = 0;
+      for (int tt = 0; tt < T; ++tt) {
         const int sb = tt % kSliceBufs, rs = tt % kRecSlots;
+        if (tt >= kSliceBufs &&
+            !mbar_wait(&sfree[sb], ((tt - kSliceBufs) / kSliceBufs) & 1, ta.err, kStatTimeout, kTcWaitNs, kEpiSleepNs))
+          break;
         const int64_t jt = j0 + (int64_t)tt * kN;
-        mbar_arrive_expect_tx(&full[sb], kSlices * kOthSlice);
         const unsigned char* src = oth_src + jt * kRowB;
+        mbar_arrive_expect_tx(&full[sb], kSlices * kOthSlice);
         for (int s = 0; s < kSlices; ++s)
           bulk_g2s(sm + kOffOth + (sb * kSlices + s) * kOthSlice, src + (int64_t)s * sq.npad * kRowB, kOthSlice,
                    &full[sb]);
         mbar_arrive_expect_tx(&recf[rs], kRecBytes);
         bulk_g2s(sm + kOffRec + rs * kRecBytes, sq.rec + jt, kRecBytes, &recf[rs]);
-      };
-      // Schedule. Tiles 0 and 1 are prefetched. The MMAs of tile tt go level by
-      // level, each level once the epilogue has loaded that level of tile
-      // tt - 1 (lfree), with a commit per level (lvl) and one for the slice
-      // buffer (sfree). After queueing tile tt, the copies of tile tt + 1 go
-      // into the buffer of tile tt - 1 once its MMAs are done, and into the
-      // record slot of tile tt - 3: the epilogue loaded tile tt - 1 before the
-      // MMAs of tile tt were issued, so it had finished every tile up to tt - 2.
-      int issued = 0, landed = 0, committed = 0, freed = 0;
-      for (; issued < 2 && issued < T; ++issued) issue(issued);
+        issued = tt + 1;
+      }
+      // leave no copy in flight (bounded waits that ignore the error flag): the
+      // own slices, the slices of the last two tiles issued (a buffer was
+      // reused only after the MMAs had read its previous tile) and the records
+      // of the last four
+      mbar_wait(ownf, 0, ta.err, 0, kTcDrainNs);
+      for (int tt = (issued > kSliceBufs ? issued - kSliceBufs : 0); tt < issued; ++tt)
+        mbar_wait(&full[tt % kSliceBufs], (tt / kSliceBufs) & 1, ta.err, 0, kTcDrainNs);
+      for (int tt = (issued > kRecSlots ? issued - kRecSlots : 0); tt < issued; ++tt)
+        mbar_wait(&recf[tt % kRecSlots], (tt / kRecSlots) & 1, ta.err, 0, kTcDrainNs);
+    }
+    __syncwarp();
+  } else if (warp == 0) {
+    // ---------------- MMAs (one thread) ----------------
+    // Per tile: one wait for its slices and one for the epilogue to have
+    // loaded levels 0-3 of the previous tile; levels 0-1 and 2-3 with a commit
+    // each (lvl); one wait for level 4 of the previous tile to be loaded;
+    // level 4, its commit and the slice buffer's (sfree). A tcgen05.mma blocks
+    // while the tensor unit's short queue is full, so every other step of this
+    // thread is kept short and few.
+    if (lane == 0) {
       const bool own_ok = mbar_wait(ownf, 0, ta.err, kStatTimeout);
       // descriptors of the first own slice and of the first other-side slice;
       // every MMA of a tile adds a compile-time offset (all 60 unrolled)
       const uint64_t adesc0 = desc_sw128(smem_u32(sm));
       const uint64_t bdesc0 = desc_sw128(smem_u32(sm + kOffOth));
+      auto level = [&](uint64_t bdesc, int L) {
+#pragma unroll
+        for (int k4 = 0; k4 < 4; ++k4)
+#pragma unroll
+          for (int s = 0; s < kSlices; ++s) {
+            const int t = L - s;
+            if (t < 0 || t >= kSlices) continue;
+            mma_bf16(tbase + (uint32_t)(L * kN), adesc0 + (uint64_t)((s * kOwnSlice + k4 * 32) >> 4),
+                     bdesc + (uint64_t)((t * kOthSlice + k4 * 32) >> 4), kIdesc,
+                     (k4 == 0 && s == (L > kSlices - 1 ? L - (kSlices - 1) : 0)) ? 0u : 1u);
+          }
+      };
+      int committed = 0;
       bool ok = own_ok;
       for (int tt = 0; ok && tt < T; ++tt) {
         const int sb = tt % kSliceBufs;
-        if (!mbar_wait(&full[sb], (tt / kSliceBufs) & 1, ta.err, kStatTimeout)) break;
-        landed = tt + 1;
+        const uint32_t fpar = (uint32_t)(tt / kSliceBufs) & 1u;
+        const uint32_t ppar = (uint32_t)(tt - 1) & 1u;
         const uint64_t bdesc = bdesc0 + (uint64_t)((sb * kSlices * kOthSlice) >> 4);
-#pragma unroll
-        for (int L = 0; L < kLevels; ++L) {
-          if (tt >= 1 && !mbar_wait(&lfree[L], (tt - 1) & 1, ta.err, kStatTimeout)) {
-            ok = false;
-            break;
-          }
+        if (!mbar_wait(&full[sb], fpar, ta.err, kStatTimeout) ||
+            (tt >= 1 && !mbar_wait(&lfree[0], ppar, ta.err, kStatTimeout))) {
+          ok = false;
+        } else {
           tc_fence_after();
-#pragma unroll
-          for (int k4 = 0; k4 < 4; ++k4)
-#pragma unroll
-            for (int s = 0; s < kSlices; ++s) {
-              const int t = L - s;
-              if (t < 0 || t >= kSlices) continue;
-              mma_bf16(tbase + (uint32_t)(L * kN), adesc0 + (uint64_t)((s * kOwnSlice + k4 * 32) >> 4),
-                       bdesc + (uint64_t)((t * kOthSlice + k4 * 32) >> 4), kIdesc,
-                       (k4 == 0 && s == (L > kSlices - 1 ? L - (kSlices - 1) : 0)) ? 0u : 1u);
-            }
-          mma_commit(&lvl[L]);
-        }
-        if (!ok) break;
-        mma_commit(&sfree[sb]);
-        committed = tt + 1;
-        if (tt + 1 < T && tt + 1 >= issued) {
-          if (tt >= 1) {
-            if (!mbar_wait(&sfree[(tt - 1) % kSliceBufs], ((tt - 1) / kSliceBufs) & 1, ta.err, kStatTimeout)) break;
-            freed = tt;
+          level(bdesc, 0);
+          level(bdesc, 1);
+          mma_commit(&lvl[0]);
+          level(bdesc, 2);
+          level(bdesc, 3);
+          mma_commit(&lvl[1]);
+          if (tt >= 1 && !mbar_wait(&lfree[1], ppar, ta.err, kStatTimeout)) {
+            ok = false;
+          } else {
+            tc_fence_after();
+            level(bdesc, 4);
+            mma_commit(&lvl[2]);
           }
-          issue(tt + 1);
-          ++issued;
+        }
+        mma_commit(&sfree[sb]);  // also after a partly issued tile: its MMAs end before the CTA does
+        if (ok) {
+          committed = tt + 1;
+        } else {  // that commit covers every MMA issued: wait for it alone
+          mbar_wait(&sfree[sb], fpar, ta.err, 0, kTcDrainNs);
+          committed = 0;
         }
       }
-      // leave nothing in flight (bounded waits that ignore the error flag):
-      // slices issued but not seen landed, the records of the last four tiles
-      // issued (an earlier slot was reused only after the epilogue had read
-      // it), and the MMAs of the tiles whose buffer was not seen free. A tile
-      // whose levels were only partly issued ends with the commits issued.
-      if (!own_ok) mbar_wait(ownf, 0, ta.err, 0, kTcDrainNs);
-      for (int tt = landed; tt < issued; ++tt)
-        mbar_wait(&full[tt % kSliceBufs], (tt / kSliceBufs) & 1, ta.err, 0, kTcDrainNs);
-      for (int tt = (issued > kRecSlots ? issued - kRecSlots : 0); tt < issued; ++tt)
-        mbar_wait(&recf[tt % kRecSlots], (tt / kRecSlots) & 1, ta.err, 0, kTcDrainNs);
-      for (int tt = freed; tt < committed; ++tt)
+      // the MMAs of the last two committed tiles (earlier ones were seen done
+      // by the copy thread before it reused their buffer, or end before these)
+      for (int tt = (committed > kSliceBufs ? committed - kSliceBufs : 0); tt < committed; ++tt)
         mbar_wait(&sfree[tt % kSliceBufs], (tt / kSliceBufs) & 1, ta.err, 0, kTcDrainNs);
-      if (!ok && landed > committed) {  // a partly issued tile: wait for its MMAs too
-        mma_commit(&sfree[(landed - 1) % kSliceBufs]);
-        mbar_wait(&sfree[(landed - 1) % kSliceBufs], ((landed - 1) / kSliceBufs) & 1, ta.err, 0, kTcDrainNs);
-      }
     }
     __syncwarp();
   } else if (warp >= 2) {
@@ -427,19 +443,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_sweep_kernel(SweepArgs<float
       // G as an FP32 pair per column, folded level by level; each level goes
       // back to the MMAs of the next tile as soon as it is in registers
       uint32_t gh[kPartCols], gl[kPartCols], u[kPartCols];
-      if (!warp_wait(&lvl[0], par, ta.err)) break;
+      if (!warp_wait(&lvl[0], par, ta.err)) break;  // levels 0 and 1
       tc_fence_after();
       tmem_ld32(tcol, gh);
-      if (!warp_wait(&lvl[1], par, ta.err)) break;
-      tc_fence_after();
       tmem_ld32(tcol + (uint32_t)kN, gl);
       tmem_ld_wait();
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) {
-        mbar_arrive(&lfree[0]);
-        mbar_arrive(&lfree[1]);
-      }
       // G = S_0 + 2^-8 S_1 + ... as an FP32 pair (gh, gl). S_0 is an integer
       // below 2^22 and 2^-8 S_1 a multiple of 2^-8 below 2^15: where
       // |S_0| >= |2^-8 S_1| Fast2Sum is exact, and otherwise the sum lies below
@@ -452,19 +460,25 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_sweep_kernel(SweepArgs<float
         gh[c] = __float_as_uint(h);
         gl[c] = __float_as_uint(fmaf(s1, 0x1p-8f, -z));
       }
+      if (!warp_wait(&lvl[1], par, ta.err)) break;  // levels 2 and 3
+      tc_fence_after();
       bool ok = true;
 #pragma unroll
       for (int L = 2; L < kLevels; ++L) {
-        if (!warp_wait(&lvl[L], par, ta.err)) {
-          ok = false;
-          break;
+        if (L == 4) {
+          if (!warp_wait(&lvl[2], par, ta.err)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
         }
-        tc_fence_after();
         tmem_ld32(tcol + (uint32_t)(L * kN), u);
         tmem_ld_wait();
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&lfree[L]);
+        if (L >= 3) {  // levels 0-3, then level 4, go back to the MMAs
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&lfree[L - 3]);
+        }
         const float sc = L == 2 ? 0x1p-16f : (L == 3 ? 0x1p-24f : 0x1p-32f);
 #pragma unroll
         for (int c = 0; c < kPartCols; ++c)

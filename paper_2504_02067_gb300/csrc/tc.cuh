@@ -50,6 +50,18 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+// Non-blocking test of the same phase (no suspension).
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
 // The same test, letting the thread sleep up to hint_ns while the phase is open
 // (for consumers whose wait is long compared with a poll).
 __device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, uint32_t parity, uint32_t hint_ns) {
@@ -73,6 +85,7 @@ constexpr uint32_t kMaxPolls = 1u << 28;
 // With sleep_ns > 0 each poll may sleep that long while the phase is open.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, int err_bit,
                                           unsigned long long limit_ns = kTcWaitNs, uint32_t sleep_ns = 0) {
+  if (mbar_test_wait(bar, parity)) return true;  // fast path: no timer read
   const unsigned long long t0 = now_ns();
   const uint32_t min_polls = limit_ns < kTcWaitNs ? kMinPolls >> 6 : kMinPolls;
   for (uint32_t it = 0;; ++it) {
