@@ -199,7 +199,7 @@ struct Solver {
     auto carve = [&](tc::Side& sd, int64_t np) {
       sd.slices = (const __nv_bfloat16*)take((size_t)np * tc::kSlices * 64 * 2);
       sd.nx = (const double*)take((size_t)np * sizeof(double));
-      sd.rec = (float4*)take((size_t)np * sizeof(float4));
+      sd.rec = (float*)take((size_t)np * sizeof(float4));
       sd.own = (tc::OwnRec*)take((size_t)np * sizeof(tc::OwnRec));
       sd.npad = np;
     };

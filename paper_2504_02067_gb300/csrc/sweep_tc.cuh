@@ -23,8 +23,8 @@
 // with K = gamma s_C and A, B the high parts of the potentials. A small kernel
 // before each sweep (tc_sweep_prep_kernel) forms P and Q in FP64 and splits each
 // into a high part on the 1/8 grid and a low part below 1/16: the other side's
-// low part is folded into its weights (w_j 2^ql_j, one record of 16 bytes per
-// point: {Qh, w0, w1, w2}) and the own side's into one FP64 factor 2^pl_i that
+// low part is folded into its weights (w_j 2^ql_j, one record per point:
+// {Qh, w0} in 8 bytes for one weight, {Qh, w0, w1, w2} in 16) and the own side's into one FP64 factor 2^pl_i that
 // the finishing CTA applies to the row's total. Per entry the epilogue then
 // needs G as an FP32 pair (Fast2Sum of the two top levels plus three FMAs) and
 //     t2 = fma(kh, gh, Ph + Qh) + fma(kl, gh, kh gl)
@@ -77,7 +77,7 @@ constexpr uint32_t kOthSlice = kN * kRowB;                          // 12 KB
 constexpr uint32_t kOffOth = kSlices * kOwnSlice;                   // 80 KB
 constexpr int kSliceBufs = 2;                                       // tile tt: slice buffer tt % 2
 constexpr int kRecSlots = 4;                                        // tile tt: record slot tt % 4
-constexpr uint32_t kRecBytes = kN * 16;                             // 1.5 KB
+constexpr uint32_t kRecBytes = kN * 16;                             // 1.5 KB: a slot at the widest record
 constexpr uint32_t kOffRec = kOffOth + kSliceBufs * kSlices * kOthSlice;  // + 120 KB
 constexpr uint32_t kOffBar = kOffRec + kRecSlots * kRecBytes;            // + 6 KB
 constexpr uint32_t kSmemBytes = kOffBar + 256 + 1024;               // barriers, TMEM slot; 1024-byte alignment slack
@@ -106,7 +106,7 @@ struct OwnRec {
 struct Side {
   const __nv_bfloat16* slices;  // [kSlices][npad][64], 128-byte swizzle per 8-row atom
   const double* nx;             // [npad] |x - c|^2 (0 for padding)
-  float4* rec;                  // [npad] as the other side: {Qh, w0 2^ql, w1 2^ql, w2 2^ql}
+  float* rec;                   // [npad][rec_floats(NR)] as the other side: {Qh, w0 2^ql[, w1 2^ql, w2 2^ql]}
   OwnRec* own;                  // [npad] as the own side
   int64_t npad;
 };
@@ -118,6 +118,9 @@ struct TcArgs {
 };
 
 __host__ __device__ inline int64_t pad_rows(int64_t n) { return (n + kPadRows - 1) / kPadRows * kPadRows; }
+// Floats per record: sweeps with one weight (the CG halves, the LSE sweeps)
+// read 8 bytes per column, so one 16-byte shared load serves two columns.
+__host__ __device__ constexpr int rec_floats(int nr) { return nr == 1 ? 2 : 4; }
 
 // E with every centred coordinate |x_k| < 2^E (0 for a cloud of one point).
 __device__ __forceinline__ int cloud_exp(unsigned long long bits) {
@@ -198,6 +201,7 @@ __global__ void tc_sweep_prep_kernel(SweepArgs<float> a, TcArgs ta) {
     ta.kappa[1] = (float)(kap - (double)kh);
   }
   if (i < sq.npad) {
+    constexpr int RW = rec_floats(NR);
     float4 r = make_float4(kPadQ, 0.f, 0.f, 0.f);
     if (i < n_oth) {
       const float* hq = ROWS ? a.Bh : a.Ah;
@@ -213,7 +217,8 @@ __global__ void tc_sweep_prep_kernel(SweepArgs<float> a, TcArgs ta) {
       if constexpr (NR > 1) r.z = (float)((double)wt[1][i] * ((SQM & 2) ? f2 : f1));
       if constexpr (NR > 2) r.w = (float)((double)wt[2][i] * ((SQM & 4) ? f2 : f1));
     }
-    sq.rec[i] = r;
+    if constexpr (RW == 2) reinterpret_cast<float2*>(sq.rec)[i] = make_float2(r.x, r.y);
+    else reinterpret_cast<float4*>(sq.rec)[i] = r;
   } else if (i < sq.npad + so.npad) {
     const int64_t e = i - sq.npad;
     OwnRec o{0.f, 0.f, 0.0, 1.0, 1.0};
@@ -276,6 +281,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_sweep_kernel(SweepArgs<float
   uint32_t* tslot = (uint32_t*)(full + 14);
   constexpr int NA = LSE ? 1 : NR;
   constexpr int ND = Epi::kDot;
+  constexpr int RW = rec_floats(NR);
+  constexpr uint32_t kTileRec = kN * RW * 4;  // record bytes of a tile
   __shared__ float hsum[kParts - 1][NA][kM], hcmp[kParts - 1][NA][kM], hmax[kParts - 1][kM];
   __shared__ int last_blk;
 
@@ -346,8 +353,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_sweep_kernel(SweepArgs<float
         for (int s = 0; s < kSlices; ++s)
           bulk_g2s(sm + kOffOth + (sb * kSlices + s) * kOthSlice, src + (int64_t)s * sq.npad * kRowB, kOthSlice,
                    &full[sb]);
-        mbar_arrive_expect_tx(&recf[rs], kRecBytes);
-        bulk_g2s(sm + kOffRec + rs * kRecBytes, sq.rec + jt, kRecBytes, &recf[rs]);
+        mbar_arrive_expect_tx(&recf[rs], kTileRec);
+        bulk_g2s(sm + kOffRec + rs * kRecBytes, sq.rec + jt * RW, kTileRec, &recf[rs]);
         issued = tt + 1;
       }
       // leave no copy in flight (bounded waits that ignore the error flag): the
@@ -437,7 +444,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_sweep_kernel(SweepArgs<float
     // hm is exact.
     float hm = LSE ? ph - mx : ph;
     const uint32_t tcol = tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(part * kPartCols);
-    const float4* recs = (const float4*)(sm + kOffRec);
+    const float* recs = (const float*)(sm + kOffRec);
     for (int tt = 0; tt < T; ++tt) {
       const uint32_t par = (uint32_t)tt & 1u;
       // G as an FP32 pair per column, folded level by level; each level goes
@@ -487,30 +494,46 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_sweep_kernel(SweepArgs<float
       if (!ok) break;
       const int rs = tt % kRecSlots;
       if (!warp_wait(&recf[rs], (uint32_t)(tt / kRecSlots) & 1u, ta.err)) break;
-      const float4* rt = recs + rs * kN + part * kPartCols;
+      const float* rt = recs + rs * (kRecBytes / 4) + part * kPartCols * RW;
 #pragma unroll
       for (int c = 0; c < kGroups; ++c) {
         float acc[NA];
 #pragma unroll
         for (int k = 0; k < NA; ++k) acc[k] = 0.f;
+        // the group's records: Qh and the weights of its 8 columns
+        float qh[8], w[NR][8];
+        if constexpr (RW == 2) {
+#pragma unroll
+          for (int jj = 0; jj < 8; jj += 2) {
+            const float4 R = *reinterpret_cast<const float4*>(rt + (c * 8 + jj) * 2);
+            qh[jj] = R.x;
+            w[0][jj] = R.y;
+            qh[jj + 1] = R.z;
+            w[0][jj + 1] = R.w;
+          }
+        } else {
+#pragma unroll
+          for (int jj = 0; jj < 8; ++jj) {
+            const float4 R = *reinterpret_cast<const float4*>(rt + (c * 8 + jj) * 4);
+            qh[jj] = R.x;
+            const float ws[3] = {R.y, R.z, R.w};
+#pragma unroll
+            for (int k = 0; k < NR; ++k) w[k][jj] = ws[k];
+          }
+        }
         if constexpr (!LSE) {
 #pragma unroll
           for (int jj = 0; jj < 8; ++jj) {
-            const float4 R = rt[c * 8 + jj];
-            const float ex = ex2_approx(entry_t2(__fadd_rn(hm, R.x), __uint_as_float(gh[c * 8 + jj]),
+            const float ex = ex2_approx(entry_t2(__fadd_rn(hm, qh[jj]), __uint_as_float(gh[c * 8 + jj]),
                                                  __uint_as_float(gl[c * 8 + jj]), kh, kl));
-            const float ws[3] = {R.y, R.z, R.w};
 #pragma unroll
-            for (int k = 0; k < NR; ++k) acc[k] = fmaf(((SQM >> k) & 1) ? ex * ex : ex, ws[k], acc[k]);
+            for (int k = 0; k < NR; ++k) acc[k] = fmaf(((SQM >> k) & 1) ? ex * ex : ex, w[k][jj], acc[k]);
           }
         } else {
-          float qh[8], w[8], t[8];
+          float t[8];
           float tmax = -3.0e38f;
 #pragma unroll
           for (int jj = 0; jj < 8; ++jj) {
-            const float4 R = rt[c * 8 + jj];
-            qh[jj] = R.x;
-            w[jj] = R.y;
             t[jj] = entry_t2(__fadd_rn(hm, qh[jj]), __uint_as_float(gh[c * 8 + jj]),
                              __uint_as_float(gl[c * 8 + jj]), kh, kl);
             tmax = fmaxf(tmax, t[jj]);
@@ -531,7 +554,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_sweep_kernel(SweepArgs<float
             }
           }
 #pragma unroll
-          for (int jj = 0; jj < 8; ++jj) acc[0] = fmaf(ex2_approx(t[jj]), w[jj], acc[0]);
+          for (int jj = 0; jj < 8; ++jj) acc[0] = fmaf(ex2_approx(t[jj]), w[0][jj], acc[0]);
         }
 #pragma unroll
         for (int k = 0; k < NA; ++k) kadd(Sa[k], Ca[k], acc[k]);
