@@ -1020,6 +1020,46 @@ def run_profile_sweep(args):
     h.close()
 
 
+def run_profile_solve(args):
+    """One solve of the 64 x 64 grid workload for a profiler's launch list: a
+    warm-up solve, then one solve between cudaProfilerStart and Stop (capture
+    with ncu --profile-from-start off). Kernels inside CUDA graphs with
+    conditional nodes are not listed by ncu, so run it with EOT_GRAPH=0: the same
+    kernels in the same order, launched directly."""
+    import torch
+
+    import paper_2504_02067_gb300 as E
+    import workloads as W
+
+    E.build()
+    dev = torch.device("cuda", 0)
+    p = W.grid_problem_4096(0, args.cost)
+    C = torch.from_numpy(p["C"]).to(dev)
+    r = torch.from_numpy(p["r"]).to(dev)
+    c = torch.from_numpy(p["c"]).to(dev)
+    h = E.Handle(0, N, N)
+    prob = E.Problem(C, r, c, precision="mixed")
+    prm = E.default_params(gamma_i=GAMMA_I, gamma_f=GAMMA_F, tol_final=TOL)
+    u = torch.empty(N, dtype=torch.float64, device=dev)
+    v = torch.empty(N, dtype=torch.float64, device=dev)
+    h.eot_solve(prob, prm, u, v)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    flush.zero_()
+    torch.cuda.synchronize()
+    l0 = h.launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.profiler.start()
+    e0.record()
+    st = h.eot_solve(prob, prm, u, v).as_dict()
+    e1.record()
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    print(json.dumps({"graph": os.environ.get("EOT_GRAPH", "1") != "0", "ms": round(e0.elapsed_time(e1), 3),
+                      "launches": h.launches() - l0, "cg_iters": st["cg_iters"],
+                      "sweeps": st["sweeps_total"]}))
+    h.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1041,6 +1081,8 @@ def main():
     ap.add_argument("--profile-iters", type=int, default=3)
     ap.add_argument("--profile-cold", action="store_true",
                     help="with --profile-sweep: time each launch alone after an L2 overwrite")
+    ap.add_argument("--profile-solve", action="store_true",
+                    help="one solve of the grid workload between profiler start and stop (for ncu)")
     ap.add_argument("--profile-points", type=int, default=-1,
                     help="run only eot_sweep_bench of this kind on the d = 64 point workload")
     ap.add_argument("--solve", action="store_true", help="--workload colour: a full solve to the paper's eps_d")
@@ -1050,6 +1092,9 @@ def main():
     args = ap.parse_args()
     if args.profile_sweep >= 0:
         run_profile_sweep(args)
+        return
+    if args.profile_solve:
+        run_profile_solve(args)
         return
     if args.profile_points >= 0:
         run_profile_points(args)

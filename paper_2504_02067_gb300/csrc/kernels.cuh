@@ -648,6 +648,20 @@ __global__ void cg_update_fused_kernel(int64_t n, const double* p, const double*
     if (cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, 0);
     return;
   }
+  // the operands of this thread's first element are loaded before the sum of
+  // the partials (they do not depend on alpha): one memory round trip less
+  const int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double p0 = 0.0, q0 = 0.0, y0 = 0.0, m0 = 0.0, f0 = 0.0, x0 = 0.0, r0 = 0.0, u0 = 0.0;
+  if (i0 < n) {
+    p0 = p[i0];
+    q0 = q[i0];
+    y0 = y[i0];
+    m0 = Minv[i0];
+    f0 = rowfac[i0];
+    x0 = x[i0];
+    r0 = res[i0];
+    u0 = Yx[i0];
+  }
   double pq = 0.0;
   for (int k = threadIdx.x; k < nrow; k += 32) pq += __ldcg(rowpart + 2 * k);
   pq = warp_sum(pq);
@@ -663,15 +677,17 @@ __global__ void cg_update_fused_kernel(int64_t n, const double* p, const double*
   }
   const double alpha = sc[SC_RZ] / pq;
   double a = 0.0, b1 = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    x[i] += alpha * p[i];
-    const double r = res[i] - alpha * q[i];
+  for (int64_t i = i0; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const bool first = i == i0;
+    const double pi = first ? p0 : p[i], qi = first ? q0 : q[i], yi = first ? y0 : y[i];
+    const double mi = first ? m0 : Minv[i], fi = first ? f0 : rowfac[i];
+    x[i] = (first ? x0 : x[i]) + alpha * pi;
+    const double r = (first ? r0 : res[i]) - alpha * qi;
     res[i] = r;
-    Yx[i] += alpha * y[i];
-    const double zi = r * Minv[i];
+    Yx[i] = (first ? u0 : Yx[i]) + alpha * yi;
+    const double zi = r * mi;
     z[i] = zi;
-    xw[i] = (T)(rowfac[i] * zi);
+    xw[i] = (T)(fi * zi);
     a += r * zi;
     b1 += fabs(r);
   }
