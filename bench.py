@@ -1021,11 +1021,13 @@ def run_profile_sweep(args):
 
 
 def run_profile_solve(args):
-    """One solve of the 64 x 64 grid workload for a profiler's launch list: a
-    warm-up solve, then one solve between cudaProfilerStart and Stop (capture
-    with ncu --profile-from-start off). Kernels inside CUDA graphs with
-    conditional nodes are not listed by ncu, so run it with EOT_GRAPH=0: the same
-    kernels in the same order, launched directly."""
+    """One solve for a profiler's launch list: a warm-up solve, then one solve
+    between cudaProfilerStart and Stop (capture with ncu --profile-from-start
+    off). `grid4096`: the headline 64 x 64 grid workload (mixed precision);
+    `grid784`: the 28 x 28 grid in FP64, gamma 2^4 -> 2^12 (the FP64 record).
+    Kernels inside CUDA graphs with conditional nodes are not listed by ncu, so
+    run it with EOT_GRAPH=0: the same kernels in the same order, launched
+    directly."""
     import torch
 
     import paper_2504_02067_gb300 as E
@@ -1033,15 +1035,17 @@ def run_profile_solve(args):
 
     E.build()
     dev = torch.device("cuda", 0)
-    p = W.grid_problem_4096(0, args.cost)
+    small = args.profile_solve == "grid784"
+    nn = 784 if small else N
+    p = W.grid_problem_784(0) if small else W.grid_problem_4096(0, args.cost)
     C = torch.from_numpy(p["C"]).to(dev)
     r = torch.from_numpy(p["r"]).to(dev)
     c = torch.from_numpy(p["c"]).to(dev)
-    h = E.Handle(0, N, N)
-    prob = E.Problem(C, r, c, precision="mixed")
-    prm = E.default_params(gamma_i=GAMMA_I, gamma_f=GAMMA_F, tol_final=TOL)
-    u = torch.empty(N, dtype=torch.float64, device=dev)
-    v = torch.empty(N, dtype=torch.float64, device=dev)
+    h = E.Handle(0, nn, nn)
+    prob = E.Problem(C, r, c, precision="fp64" if small else "mixed")
+    prm = E.default_params(gamma_i=GAMMA_I, gamma_f=4096.0 if small else GAMMA_F, tol_final=TOL)
+    u = torch.empty(nn, dtype=torch.float64, device=dev)
+    v = torch.empty(nn, dtype=torch.float64, device=dev)
     h.eot_solve(prob, prm, u, v)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     flush.zero_()
@@ -1054,9 +1058,45 @@ def run_profile_solve(args):
     e1.record()
     torch.cuda.synchronize()
     torch.cuda.profiler.stop()
-    print(json.dumps({"graph": os.environ.get("EOT_GRAPH", "1") != "0", "ms": round(e0.elapsed_time(e1), 3),
+    print(json.dumps({"workload": args.profile_solve, "graph": os.environ.get("EOT_GRAPH", "1") != "0",
+                      "ms": round(e0.elapsed_time(e1), 3),
                       "launches": h.launches() - l0, "cg_iters": st["cg_iters"],
                       "sweeps": st["sweeps_total"]}))
+    h.close()
+
+
+def run_profile_batch(args):
+    """One eot_solve_batched launch on the first `args.profile_batch` problems of
+    the batch256 workload, between cudaProfilerStart and Stop, after a warm-up
+    launch that autotunes the configuration (for ncu --profile-from-start off)."""
+    import torch
+
+    import paper_2504_02067_gb300 as E
+    import workloads as W
+
+    E.build()
+    dev = torch.device("cuda", 0)
+    sizes = W.batch_sizes(0)[: args.profile_batch]
+    ps = [W.uniform_points_problem(1000 + k, int(nk)) for k, nk in enumerate(sizes)]
+    devs = [{k: torch.from_numpy(p[k]).to(dev) for k in ("X", "Y", "r", "c")} for p in ps]
+    probs = [E.Problem(X=d["X"], Y=d["Y"], r=d["r"], c=d["c"], precision="mixed", cost_scale=0.0) for d in devs]
+    us = [torch.empty(int(nk), dtype=torch.float64, device=dev) for nk in sizes]
+    vs = [torch.empty(int(nk), dtype=torch.float64, device=dev) for nk in sizes]
+    h = E.Handle(0, 64, 64)
+    prm = E.default_params(gamma_i=16.0, gamma_f=4096.0, tol_final=TOL)
+    h.eot_solve_batched(probs, prm, us, vs)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.profiler.start()
+    e0.record()
+    st, stats = h.eot_solve_batched(probs, prm, us, vs)
+    e1.record()
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    G, ro, groups = h.batch_last_config()
+    print(json.dumps({"problems": len(sizes), "sizes": [int(x) for x in sizes], "ms": round(e0.elapsed_time(e1), 3),
+                      "all_ok": all(x == 0 for x in st), "config": [G, ro, groups],
+                      "sweeps": sum(sm["sweeps_total"] for sm in stats)}))
     h.close()
 
 
@@ -1081,8 +1121,10 @@ def main():
     ap.add_argument("--profile-iters", type=int, default=3)
     ap.add_argument("--profile-cold", action="store_true",
                     help="with --profile-sweep: time each launch alone after an L2 overwrite")
-    ap.add_argument("--profile-solve", action="store_true",
-                    help="one solve of the grid workload between profiler start and stop (for ncu)")
+    ap.add_argument("--profile-solve", nargs="?", const="grid4096", default=None, choices=["grid4096", "grid784"],
+                    help="one solve between profiler start and stop (for ncu)")
+    ap.add_argument("--profile-batch", type=int, default=0,
+                    help="one eot_solve_batched launch on the first K batch256 problems (for ncu)")
     ap.add_argument("--profile-points", type=int, default=-1,
                     help="run only eot_sweep_bench of this kind on the d = 64 point workload")
     ap.add_argument("--solve", action="store_true", help="--workload colour: a full solve to the paper's eps_d")
@@ -1095,6 +1137,9 @@ def main():
         return
     if args.profile_solve:
         run_profile_solve(args)
+        return
+    if args.profile_batch > 0:
+        run_profile_batch(args)
         return
     if args.profile_points >= 0:
         run_profile_points(args)
