@@ -394,7 +394,8 @@ def record_d64(E, dev, peaks):
         best = max(rates["cg_col_sweep"]["p_entries_per_s"], rates["cg_row_sweep"]["p_entries_per_s"])
         out["tc_sweeps"] = rates
         out["tc_roofline"] = {
-            "bound": "alu", "kernel": "tc_sweep_kernel (CG halves)", "achieved_entries_per_s": best,
+            "bound": "tensor", "kernel": "tc_sweep_kernel (CG halves)", "achieved_entries_per_s": best,
+            "frac": round(best / (bf16 / flop_per_entry), 4),
             "peak_tensor_entries_per_s": round(bf16 / flop_per_entry, 1),
             "peak_ex2_entries_per_s": round(ex2, 1),
             "fp32_issue_per_s": round(fp32_issue, 1),

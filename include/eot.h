@@ -363,9 +363,10 @@ eot_status eot_marginals_noalloc(const eot_problem* prob, const double* u, const
                                  double gamma, double* r_out, double* c_out, int32_t* status_out,
                                  void* stream);
 
-/* Number of this library's kernel launches issued on the handle so far
- * (graph-launched kernels counted once per launched node execution estimate:
- * CG kernels count 4 per CG iteration). For launch accounting in benchmarks. */
+/* Number of this library's kernel launches issued on the handle so far. The
+ * kernels of a captured program count once per execution: the body of each of
+ * its loops times the trip count the device recorded. For launch accounting in
+ * benchmarks. */
 int64_t eot_kernel_launches(eot_handle h);
 
 #ifdef __cplusplus

@@ -32,14 +32,14 @@ def _inputs(seed, n, m, gamma, f32):
     return C, u, v
 
 
-@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+@pytest.mark.parametrize("prec", ["mixed", "plain_fp32", "fp64"])
 def test_noalloc_matches_allocating_entry_point_twice(prec):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     import paper_2504_02067_gb300 as E
     from paper_2504_02067_gb300.binding import eot_marginals_noalloc
     E.build()
-    f32 = prec == "mixed"
+    f32 = prec != "fp64"
     gamma = 512.0
     tol = 1e-6 if f32 else 1e-12
     h = E.Handle(0, 64, 64)
