@@ -36,18 +36,19 @@
 // N = 192), so the tile is 96 points wide: the five level accumulators then
 // fill 480 of the 512 TMEM columns, one buffer, handed over level by level.
 //
-// CTA roles (448 threads, one CTA per SM: about 215 KB of shared memory):
-//   warp 0, lane 0: the 60 MMAs of each tile, level by level, with a commit per
-//     level. A tcgen05.mma blocks its thread while the tensor unit's short
-//     queue is full, so this thread does nothing else: any other work in it
-//     leaves the tensor unit idle;
+// CTA roles (480 threads, one CTA per SM: about 215 KB of shared memory):
+//   warp 0, lane 0 and warp 14, lane 0: the 60 MMAs of each tile, level by
+//     level (levels 0, 1, 4 and levels 2, 3), with a commit per level group. A
+//     tcgen05.mma blocks its thread while the tensor unit's short queue is
+//     full, so these threads do nothing else: any other work in them, or a
+//     lost issue slot, leaves the tensor unit idle;
 //   warp 1: TMEM allocation (512 columns) and release; lane 0 issues the bulk
 //     copies (the own 128 points' slices once; the other side's 96-point
 //     tiles into two slice buffers and their records into four record slots);
 //   warps 2-13: epilogue. Warp w reads TMEM lanes 32 (w mod 4) .. +31 (one own
 //     point per thread) and a third (32) of the tile's 96 columns.
-// Hand-offs are mbarriers: full[sb] (the slices of buffer sb landed), sfree[sb]
-// (the MMAs reading buffer sb are done), rec[s] (records landed), lvl[g] (the
+// Hand-offs are mbarriers: full[sb] (the slices of buffer sb landed), sfree[sb][i]
+// (issuer i's MMAs reading buffer sb are done), rec[s] (records landed), lvl[g] (the
 // MMAs of level group g = {0,1}, {2,3}, {4} are done: accumulators readable),
 // lfree[0] / lfree[1] (the 12 epilogue warps have loaded levels 0-3 / level 4
 // into registers; the next tile's MMAs may overwrite them). Every wait is
@@ -69,7 +70,8 @@ constexpr int kEpiWarps = 12;                  // 3 per TMEM lane quarter
 constexpr int kParts = kEpiWarps / 4;          // column parts of a tile
 constexpr int kPartCols = kN / kParts;         // 32 columns per epilogue warp and tile
 constexpr int kGroups = kPartCols / 8;         // groups of 8 columns in the arithmetic
-constexpr int kTcThreads = 32 * (2 + kEpiWarps);
+constexpr int kMmaWarpB = 2 + kEpiWarps;      // the second MMA-issuing warp (after the epilogue warps)
+constexpr int kTcThreads = 32 * (3 + kEpiWarps);
 constexpr int kTcWarps = kTcThreads / 32;
 constexpr uint32_t kRowB = 128;    // bytes per point and slice: 64 BF16 coordinates
 constexpr uint32_t kOwnSlice = kM * kRowB;                          // 16 KB
@@ -273,12 +275,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_sweep_kernel(SweepArgs<float
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = (uint64_t*)(sm + kOffBar);  // [2] the five slices of the slice buffer landed
-  uint64_t* sfree = full + 2;                  // [2] MMAs reading the slice buffer done
-  uint64_t* lvl = full + 4;                    // [3] MMAs of levels {0,1}, {2,3}, {4} done
-  uint64_t* lfree = full + 7;                  // [2] levels 0-3, level 4 loaded by all epilogue warps
-  uint64_t* recf = full + 9;                   // [4] records of the slot landed
-  uint64_t* ownf = full + 13;
-  uint32_t* tslot = (uint32_t*)(full + 14);
+  uint64_t* sfree = full + 2;                  // [2][2] per issuer: its MMAs reading the slice buffer done
+  uint64_t* lvl = full + 6;                    // [3] MMAs of levels {0,1}, {2,3}, {4} done
+  uint64_t* lfree = full + 9;                  // [2] levels 0-3, level 4 loaded by all epilogue warps
+  uint64_t* recf = full + 11;                  // [4] records of the slot landed
+  uint64_t* ownf = full + 15;
+  uint32_t* tslot = (uint32_t*)(full + 16);
   constexpr int NA = LSE ? 1 : NR;
   constexpr int ND = Epi::kDot;
   constexpr int RW = rec_floats(NR);
@@ -297,7 +299,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_sweep_kernel(SweepArgs<float
   if (threadIdx.x == 0) {
     for (int k = 0; k < kSliceBufs; ++k) {
       mbar_init(&full[k], 1);
-      mbar_init(&sfree[k], 1);
+      mbar_init(&sfree[2 * k], 1);
+      mbar_init(&sfree[2 * k + 1], 1);
     }
     for (int g = 0; g < 3; ++g) mbar_init(&lvl[g], 1);
     for (int g = 0; g < 2; ++g) mbar_init(&lfree[g], kEpiWarps);
@@ -318,10 +321,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_sweep_kernel(SweepArgs<float
   }
 
   // per-thread results of the epilogue (own point r of this CTA, one column part)
-  const int q = warp & 3, part = warp >= 2 ? (warp - 2) >> 2 : 0;
+  const bool epi_warp = warp >= 2 && warp < 2 + kEpiWarps;
+  const int q = warp & 3, part = epi_warp ? (warp - 2) >> 2 : 0;
   const int r = 32 * q + lane;
   const int64_t e = blk * kM + r;
-  const bool ev = warp >= 2 && e < n_own;
+  const bool ev = epi_warp && e < n_own;
   float Sa[NA], Ca[NA], mx = kPadQ;
 #pragma unroll
   for (int k = 0; k < NA; ++k) {
@@ -344,8 +348,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_sweep_kernel(SweepArgs<float
       int issued = 0;
       for (int tt = 0; tt < T; ++tt) {
         const int sb = tt % kSliceBufs, rs = tt % kRecSlots;
+        const uint32_t opar = (uint32_t)((tt - kSliceBufs) / kSliceBufs) & 1u;  // tile tt - 2's phase
         if (tt >= kSliceBufs &&
-            !mbar_wait(&sfree[sb], ((tt - kSliceBufs) / kSliceBufs) & 1, ta.err, kStatTimeout, kTcWaitNs, kEpiSleepNs))
+            (!mbar_wait(&sfree[2 * sb], opar, ta.err, kStatTimeout, kTcWaitNs, kEpiSleepNs) ||
+             !mbar_wait(&sfree[2 * sb + 1], opar, ta.err, kStatTimeout, kTcWaitNs, kEpiSleepNs)))
           break;
         const int64_t jt = j0 + (int64_t)tt * kN;
         const unsigned char* src = oth_src + jt * kRowB;
@@ -368,18 +374,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_sweep_kernel(SweepArgs<float
         mbar_wait(&recf[tt % kRecSlots], (tt / kRecSlots) & 1, ta.err, 0, kTcDrainNs);
     }
     __syncwarp();
-  } else if (warp == 0) {
-    // ---------------- MMAs (one thread) ----------------
-    // Per tile: one wait for its slices and one for the epilogue to have
-    // loaded levels 0-3 of the previous tile; levels 0-1 and 2-3 with a commit
-    // each (lvl); one wait for level 4 of the previous tile to be loaded;
-    // level 4, its commit and the slice buffer's (sfree). A tcgen05.mma blocks
-    // while the tensor unit's short queue is full, so every other step of this
-    // thread is kept short and few.
+  } else if (warp == 0 || warp == kMmaWarpB) {
+    // ---------------- MMAs (two threads) ----------------
+    // Issuer A (warp 0) owns levels 0, 1 and 4, issuer B (the last warp)
+    // levels 2 and 3: each level's accumulation chain stays in one thread, and
+    // with the issuers on two SM sub-partitions the tensor unit's short queue
+    // stays fed while the epilogue warps compete for issue slots (one issuer
+    // loses ~25 % of the MMA rate to them). Per tile each waits for the slices
+    // and for the epilogue to have loaded levels 0-3 of the previous tile; A
+    // commits levels {0,1}, waits for level 4 of the previous tile to be loaded,
+    // and commits level 4; B commits levels {2,3}; each commits its use of the
+    // slice buffer (sfree[buffer][issuer]).
     if (lane == 0) {
+      const int who = warp == 0 ? 0 : 1;
       const bool own_ok = mbar_wait(ownf, 0, ta.err, kStatTimeout);
       // descriptors of the first own slice and of the first other-side slice;
-      // every MMA of a tile adds a compile-time offset (all 60 unrolled)
+      // every MMA adds a compile-time offset (all unrolled)
       const uint64_t adesc0 = desc_sw128(smem_u32(sm));
       const uint64_t bdesc0 = desc_sw128(smem_u32(sm + kOffOth));
       auto level = [&](uint64_t bdesc, int L) {
@@ -404,14 +414,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_sweep_kernel(SweepArgs<float
         if (!mbar_wait(&full[sb], fpar, ta.err, kStatTimeout) ||
             (tt >= 1 && !mbar_wait(&lfree[0], ppar, ta.err, kStatTimeout))) {
           ok = false;
-        } else {
+        } else if (who == 0) {
           tc_fence_after();
           level(bdesc, 0);
           level(bdesc, 1);
           mma_commit(&lvl[0]);
-          level(bdesc, 2);
-          level(bdesc, 3);
-          mma_commit(&lvl[1]);
           if (tt >= 1 && !mbar_wait(&lfree[1], ppar, ta.err, kStatTimeout)) {
             ok = false;
           } else {
@@ -419,22 +426,28 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_sweep_kernel(SweepArgs<float
             level(bdesc, 4);
             mma_commit(&lvl[2]);
           }
+        } else {
+          tc_fence_after();
+          level(bdesc, 2);
+          level(bdesc, 3);
+          mma_commit(&lvl[1]);
         }
-        mma_commit(&sfree[sb]);  // also after a partly issued tile: its MMAs end before the CTA does
+        uint64_t* sf = &sfree[2 * sb + who];
+        mma_commit(sf);  // also after a partly issued tile: its MMAs end before the CTA does
         if (ok) {
           committed = tt + 1;
-        } else {  // that commit covers every MMA issued: wait for it alone
-          mbar_wait(&sfree[sb], fpar, ta.err, 0, kTcDrainNs);
+        } else {  // that commit covers every MMA this thread issued: wait for it alone
+          mbar_wait(sf, fpar, ta.err, 0, kTcDrainNs);
           committed = 0;
         }
       }
-      // the MMAs of the last two committed tiles (earlier ones were seen done
-      // by the copy thread before it reused their buffer, or end before these)
+      // this issuer's MMAs of the last two committed tiles (earlier ones were
+      // seen done by the copy thread before it reused their buffer)
       for (int tt = (committed > kSliceBufs ? committed - kSliceBufs : 0); tt < committed; ++tt)
-        mbar_wait(&sfree[tt % kSliceBufs], (tt / kSliceBufs) & 1, ta.err, 0, kTcDrainNs);
+        mbar_wait(&sfree[2 * (tt % kSliceBufs) + who], (tt / kSliceBufs) & 1, ta.err, 0, kTcDrainNs);
     }
     __syncwarp();
-  } else if (warp >= 2) {
+  } else if (epi_warp) {
     // ---------------- epilogue ----------------
     const float ph = so.own[e].ph;  // e < npad: padded rows have records
     const float kh = ta.kappa[0], kl = ta.kappa[1];
@@ -576,7 +589,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_sweep_kernel(SweepArgs<float
     tc_fence_after();
     tmem_free(tbase, kTmemCols);
   }
-  if (warp >= 2 && part == 0 && ev) {
+  if (epi_warp && part == 0 && ev) {
     if constexpr (!LSE) {
 #pragma unroll
       for (int k = 0; k < NR; ++k) {
