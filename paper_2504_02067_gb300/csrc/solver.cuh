@@ -43,14 +43,20 @@ inline PtsGeo pts_geo_of(eot_handle h, int64_t n_own, int64_t n_oth, int d) {
   return g;
 }
 // tensor-core sweeps: own blocks of 128 points x S chunks of the other side
-// (multiples of 48), S chosen so that B S fills whole waves of one-CTA-per-SM blocks
+// (multiples of 96), one CTA per SM. A CTA pays a fixed cost besides its tiles
+// (its own slices and first tile before the first MMA, the last tile's
+// arithmetic, the partials and the finishing CTA's combine), about two tiles'
+// time: at n = m = 16384 a CG sweep took 0.392, 0.363, 0.404 and 0.397 ms with
+// 13, 7, 4 and 1 chunks, which that cost fits. S minimises
+// waves x (that cost + tiles per CTA).
 struct TcGeo {
   int64_t B, S, chunk;
 };
+constexpr int64_t kTcCtaOverheadTiles = 2;
 inline TcGeo tc_geo_of(eot_handle h, int64_t n_own, int64_t n_oth) {
   TcGeo g;
   g.B = (n_own + tc::kM - 1) / tc::kM;
-  double best = -1.0;
+  int64_t best = -1;
   g.S = 1;
   g.chunk = (n_oth + tc::kN - 1) / tc::kN * tc::kN;
   for (int64_t S = 1; S <= 128; ++S) {
@@ -59,9 +65,9 @@ inline TcGeo tc_geo_of(eot_handle h, int64_t n_own, int64_t n_oth) {
     if (Sr != S) continue;
     if (S > 1 && chunk < 2 * tc::kN) break;
     const int64_t ctas = g.B * S, waves = (ctas + h->sms - 1) / h->sms;
-    const double eff = (double)ctas / (double)(waves * h->sms) - 0.002 * (double)S;  // prefer fewer chunks
-    if (eff > best) {
-      best = eff;
+    const int64_t cost = waves * (kTcCtaOverheadTiles + chunk / tc::kN);
+    if (best < 0 || cost < best) {  // ties keep the fewer chunks
+      best = cost;
       g.S = S;
       g.chunk = chunk;
     }
