@@ -165,12 +165,11 @@ __device__ __forceinline__ typename VecOf<T>::type pack(const T (&x)[16 / sizeof
 }
 
 // In-order combine of a strided sequence base[k * stride], k < cnt, written by
-// earlier CTAs: the loads go out in batches of 8 (independent L2 round trips
+// earlier CTAs: the loads go out in batches of B (independent L2 round trips
 // overlap) and f(value) consumes them in index order, so the result is the same
 // as a plain sequential loop.
-template <class V, class F>
+template <int B = 8, class V, class F>
 __device__ __forceinline__ void ordered_loads(const V* base, int64_t stride, int64_t cnt, F&& f) {
-  constexpr int B = 8;
   for (int64_t k0 = 0; k0 < cnt; k0 += B) {
     V q[B];
 #pragma unroll
@@ -182,9 +181,8 @@ __device__ __forceinline__ void ordered_loads(const V* base, int64_t stride, int
   }
 }
 // The same for two sequences read in step: f(a_k, b_k).
-template <class V, class W, class F>
+template <int B = 8, class V, class W, class F>
 __device__ __forceinline__ void ordered_loads2(const V* a, const W* b, int64_t stride, int64_t cnt, F&& f) {
-  constexpr int B = 8;
   for (int64_t k0 = 0; k0 < cnt; k0 += B) {
     V qa[B];
     W qb[B];

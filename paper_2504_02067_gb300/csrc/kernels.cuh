@@ -160,6 +160,8 @@ constexpr int kCgMaxStrip = 128;   // columns of one strip of the column sweep (
 struct CgStage {
   double part[2 * kCgMaxParts];   // (<res, z>, ||res||_1) partials
   double wprev[kCgMaxStrip];      // w_prev of the CTA's strip
+  double colfac[kCgMaxStrip];     // colfac and c(P) of the strip (read by the finisher)
+  double cP[kCgMaxStrip];
   double iters, rzprev;           // SC_ITERS, SC_RZPREV
 };
 __device__ __forceinline__ CgStage& cg_stage_smem() {
@@ -178,7 +180,8 @@ __device__ __forceinline__ void cp_async8(void* dst, const void* src) {
 // Column half: w_j = (P^T (rowfac z))_j + beta w_prev_j; zf_j = colfac_j^2 w_j / c(P)_j,
 // with beta = <res, z> / <res, z>_prev (0 on the first iteration). begin(): warp 0
 // starts asynchronous copies of what the strip's epilogue needs (the update
-// kernel's partials, w_prev of the strip's columns, two scalars) into shared
+// kernel's partials, w_prev, colfac and c(P) of the strip's columns, two
+// scalars) into shared
 // memory, where they land while the CTA sweeps; drain(): warp 0 waits for them;
 // prepare() (the CTAs that finish a strip): beta and the stop test ||res||_1 <=
 // tol or the iteration cap, published by the finisher of strip 0. When the test
@@ -207,8 +210,15 @@ struct CgColFusedEpi {
       // w_prev of the strip (pairs of columns: the strip start is a multiple of 32 V >= 32)
       const int w = (int)min((int64_t)sw, m - strip0);
       for (int k = 2 * threadIdx.x; k < w; k += 64) {
-        if (k + 1 < w) cp_async16(s.wprev + k, wprev + strip0 + k);
-        else cp_async8(s.wprev + k, wprev + strip0 + k);
+        if (k + 1 < w) {
+          cp_async16(s.wprev + k, wprev + strip0 + k);
+          cp_async16(s.colfac + k, colfac + strip0 + k);
+          cp_async16(s.cP + k, cP + strip0 + k);
+        } else {
+          cp_async8(s.wprev + k, wprev + strip0 + k);
+          cp_async8(s.colfac + k, colfac + strip0 + k);
+          cp_async8(s.cP + k, cP + strip0 + k);
+        }
       }
       if (threadIdx.x == 0) {
         cp_async8(&s.iters, sc + SC_ITERS);
@@ -253,10 +263,12 @@ struct CgColFusedEpi {
     first = sfirst != 0;
   }
   __device__ void col(int64_t j, const double* s, double* d) {
-    const double w = first ? s[0] : s[0] + beta * cg_stage_smem().wprev[j - j0];
+    const CgStage& st = cg_stage_smem();
+    const int64_t k = j - j0;
+    const double w = first ? s[0] : s[0] + beta * st.wprev[k];
     wprev[j] = w;
-    const double f = colfac[j];
-    zf[j] = (T)(f * f * w / cP[j]);
+    const double f = st.colfac[k];
+    zf[j] = (T)(f * f * w / st.cP[k]);
   }
   __device__ void finish(const double*) {}
 };

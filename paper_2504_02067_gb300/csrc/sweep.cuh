@@ -184,7 +184,9 @@ __device__ __forceinline__ void col_combine_f32(const float2* cp2, int R, int64_
 #pragma unroll
     for (int k = 0; k < NC; ++k) {
       float s0 = 0.f, c0 = 0.f;
-      ordered_loads(cp2 + (int64_t)k * R * m + jj, m, R, [&](float2 q) {
+      // up to 16 row blocks in one batch of loads: one L2 round trip at the
+      // usual R = 9 (the finisher's latency is the column sweep's tail)
+      ordered_loads<16>(cp2 + (int64_t)k * R * m + jj, m, R, [&](float2 q) {
         kadd(s0, c0, q.x);
         c0 += q.y;
       });
