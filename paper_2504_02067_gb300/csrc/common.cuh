@@ -18,6 +18,7 @@ namespace eot {
 constexpr int kWarps = 8;            // warps per CTA of every sweep kernel
 constexpr int kThreads = kWarps * 32;
 constexpr int kColCtasPerSm = 2;     // resident column-sweep CTAs per SM (register bound)
+constexpr int kColClusterMax = 8;    // row blocks of a strip in one cluster (the portable cluster size)
 constexpr double kGrid = 0.125;      // split grid of the high parts
 constexpr double kSplitLimit = 524288.0;  // |A|, |B| < 2^19 keeps Ah + Bh exact in FP32
 constexpr float kLog2e = 1.4426950408889634f;
@@ -87,6 +88,26 @@ __device__ __forceinline__ void ld_stream(const float* p, float (&c)[1], uint64_
 }
 __device__ __forceinline__ void ld_stream(const double* p, double (&c)[1], uint64_t pol) {
   asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(c[0]) : "l"(p), "l"(pol));
+}
+
+// Thread-block clusters: a barrier over the cluster's CTAs (every thread of
+// every CTA arrives; writes before it are visible to reads after it), the CTA's
+// rank in its cluster, and a read of another CTA's shared memory.
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ float2 ld_cluster_f2(const float2* p, uint32_t rank) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+  uint32_t ra;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
+  float2 v;
+  asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(ra) : "memory");
+  return v;
 }
 
 // read-only vector loads of V consecutive elements (aligned when V > 1)

@@ -46,7 +46,10 @@ enum ScCtl : int {
   SC_N_CGPASS, SC_N_NLOOP, SC_N_GO,
   SC_DEADLINE,      // %globaltimer value (ns) after which no Newton step starts (0: none)
   SC_FL0,           // SC_FL0 + Flag: the flags as doubles (read by the host executor)
-  SC_CTL_END = SC_FL0 + F_COUNT
+  SC_ACTIVE_COL = SC_FL0 + F_COUNT,  // dense CG: the column half's stop decision, committed to
+                                     // SC_ACTIVE by the update kernel (SC_ACTIVE never changes
+                                     // while a column half runs)
+  SC_CTL_END
 };
 static_assert((int)SC_CTL_END <= (int)SC_TOTAL, "device scalar array too small for the stage control");
 

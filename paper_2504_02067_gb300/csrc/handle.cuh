@@ -139,6 +139,28 @@ inline void launch_kd(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t sm
   if (e != cudaSuccess)
     throw EotError{EOT_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e)};
 }
+// launch_k in thread-block clusters of (1, cy, 1) CTAs
+template <typename... KArgs, typename... Args>
+inline void launch_kc(void (*kernel)(KArgs...), dim3 grid, dim3 block, unsigned cy, cudaStream_t st,
+                      Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute at[2];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 1;
+  at[0].val.clusterDim.y = cy;
+  at[0].val.clusterDim.z = 1;
+  at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[1].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1 + pdl_attrs();
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+  if (e != cudaSuccess)
+    throw EotError{EOT_ERR_CUDA, std::string("cluster kernel launch: ") + cudaGetErrorString(e)};
+}
 template <typename... KArgs, typename... Args>
 inline void launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t st, Args&&... args) {
   cudaLaunchConfig_t cfg = {};
@@ -173,7 +195,7 @@ struct ColGeo {
   int64_t S;
   int R, BR;
 };
-inline ColGeo col_geo(eot_handle h, int64_t n, int64_t m, int V) {
+inline ColGeo col_geo(eot_handle h, int64_t n, int64_t m, int V, int64_t rcap = 1 << 30) {
   ColGeo g;
   g.S = (m + 32 * V - 1) / (32 * V);
   // one wave: S * R <= resident CTAs
@@ -182,6 +204,7 @@ inline ColGeo col_geo(eot_handle h, int64_t n, int64_t m, int V) {
   int64_t rmax = (n + 31) / 32;
   if (R > rmax) R = rmax;
   if (R > h->max_rowblk) R = h->max_rowblk;
+  if (R > rcap) R = rcap;
   if (R < 1) R = 1;
   int64_t BR = (n + R - 1) / R;
   BR = (BR + 31) / 32 * 32;

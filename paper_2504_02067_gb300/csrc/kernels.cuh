@@ -202,6 +202,7 @@ struct CgColFusedEpi {
   double beta;
   bool first;
   int64_t j0;          // first column of the strip
+  int acol;            // slot of the stop decision: the row half reads it, the update kernel commits it
   __device__ void begin(int64_t strip0, int sw, int64_t m) {
     j0 = strip0;
     if (threadIdx.x < 32) {
@@ -252,7 +253,7 @@ struct CgColFusedEpi {
           sc[SC_BETA] = b;
           if (!fin) atomicOr(status, kStatCgNan);
           if (!go) {
-            sc[SC_ACTIVE] = 0.0;
+            sc[acol] = 0.0;  // not SC_ACTIVE: the other CTAs of this launch may still read it
             if (cond) cudaGraphSetConditional(cond, 0);
           }
         }
@@ -612,7 +613,7 @@ template <class T>
 __global__ void cg_init_fused_kernel(int64_t n, const double* rP, const double* rPs, const double* rt,
                                      const double* diag, const double* rowfac, double* M, double* x, double* res,
                                      double* z, double* p, double* Yx, T* xw, double* sc, double* part,
-                                     cudaGraphConditionalHandle cond) {
+                                     int acol, cudaGraphConditionalHandle cond) {
   pdl_wait();
   const double rho = sc[SC_RHO];
   double a = 0.0, b1 = 0.0;
@@ -642,6 +643,7 @@ __global__ void cg_init_fused_kernel(int64_t n, const double* rP, const double* 
     sc[SC_ITERS] = 0.0;
     sc[SC_BETA] = 0.0;
     sc[SC_ACTIVE] = 1.0;
+    sc[acol] = 1.0;
     if (cond) cudaGraphSetConditional(cond, 1);
   }
 }
@@ -650,14 +652,20 @@ __global__ void cg_init_fused_kernel(int64_t n, const double* rP, const double* 
 // (summed by every CTA in fixed order; <p, F_r p> <= 0 stops CG, reading R21),
 // x += alpha p, res -= alpha q, Yx += alpha y, z = Minv res, the next column
 // half's row weights rowfac z, and one (<res, z>, ||res||_1) partial per CTA.
+// A stop that this iteration's column half decided (slot acol) becomes the
+// loop's stop flag SC_ACTIVE here, after every column CTA has read that flag.
 template <class T>
 __global__ void cg_update_fused_kernel(int64_t n, const double* p, const double* q, const double* y,
                                        const double* Minv, const double* rowfac, double* x, double* res,
                                        double* Yx, double* z, T* xw, double* sc, const double* rowpart,
-                                       int nrow, double* part, int* status, cudaGraphConditionalHandle cond) {
+                                       int nrow, double* part, int* status, int acol,
+                                       cudaGraphConditionalHandle cond) {
   pdl_wait();
-  if (sc[SC_ACTIVE] == 0.0) {
-    if (cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, 0);
+  if (sc[acol] == 0.0) {  // stopped by this iteration's column half (or earlier): commit it
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      sc[SC_ACTIVE] = 0.0;
+      if (cond) cudaGraphSetConditional(cond, 0);
+    }
     return;
   }
   // the operands of this thread's first element are loaded before the sum of
@@ -674,8 +682,11 @@ __global__ void cg_update_fused_kernel(int64_t n, const double* p, const double*
     r0 = res[i0];
     u0 = Yx[i0];
   }
+  // this lane's partials k = lane, lane + 32, ... in order, their loads in
+  // batches of 16 (one L2 round trip at nrow <= 512)
   double pq = 0.0;
-  for (int k = threadIdx.x; k < nrow; k += 32) pq += __ldcg(rowpart + 2 * k);
+  if ((int)threadIdx.x < nrow)
+    ordered_loads<16>(rowpart + 2 * threadIdx.x, 64, (nrow - (int)threadIdx.x + 31) / 32, [&](double v) { pq += v; });
   pq = warp_sum(pq);
   if (!(pq > 0.0) || !isfinite(pq)) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -683,6 +694,7 @@ __global__ void cg_update_fused_kernel(int64_t n, const double* p, const double*
       sc[SC_PQ] = pq;
       sc[SC_ALPHA] = 0.0;
       sc[SC_ACTIVE] = 0.0;
+      sc[acol] = 0.0;
       if (cond) cudaGraphSetConditional(cond, 0);
     }
     return;

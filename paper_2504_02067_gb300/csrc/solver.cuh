@@ -116,6 +116,8 @@ struct Solver {
   bool plain;
   int vg_n, vg_m, rg;
   ColGeo geo;
+  ColGeo cgeo;              // the CG column half in clusters of its R row blocks
+  bool cluster_on = false;  // FP32 dense costs, unless EOT_CG_CLUSTER=0
   SolveCounters cnt;
   int64_t* sweep_bucket;
 
@@ -158,6 +160,12 @@ struct Solver {
     if (vg_n > kCgMaxParts) throw EotError{EOT_ERR_UNSUPPORTED, "more update partials than the CG sweep stages"};
     rg = row_grid(n);
     geo = col_geo(h, n, m, V);
+    // EOT_CG_CLUSTER: the largest cluster (row blocks of a strip), 0 = off;
+    // default the portable size kColClusterMax, at most 16
+    int cmax = kColClusterMax;
+    if (const char* e = std::getenv("EOT_CG_CLUSTER")) cmax = std::min(16, std::max(0, std::atoi(e)));
+    cgeo = col_geo(h, n, m, V, std::max(1, cmax));
+    if constexpr (sizeof(T) == 4) cluster_on = !points && cmax > 0;
     sweep_bucket = &cnt.sweeps_other;
   }
 
@@ -459,6 +467,32 @@ struct Solver {
     const dim3 grid((unsigned)geo.S, (unsigned)geo.R);
     if (V == VEC) launch_k(col_sweep_kernel<T, VEC, NC, LSE, 0, Epi>, grid, dim3(kThreads), s, a, e);
     else launch_k(col_sweep_kernel<T, 1, NC, LSE, 0, Epi>, grid, dim3(kThreads), s, a, e);
+  }
+  // The dense CG column half. FP32 costs: clusters of a strip's row blocks
+  // combine their column sums in distributed shared memory and share the
+  // strip's epilogue (no partials in global memory, no ticket, no finishing
+  // CTA); otherwise the ticketed column sweep.
+  void launch_cg_col(cudaStream_t s, SweepArgs<T> a, const CgColFusedEpi<T>& e) {
+    if constexpr (sizeof(T) == 4) {
+      if (cluster_on) {
+        a.rows_per_block = cgeo.BR;
+        a.nrowblk = cgeo.R;
+        const dim3 grid((unsigned)cgeo.S, (unsigned)cgeo.R);
+        auto kv = col_sweep_kernel<T, VEC, 1, false, 0, CgColFusedEpi<T>, true>;
+        auto k1 = col_sweep_kernel<T, 1, 1, false, 0, CgColFusedEpi<T>, true>;
+        if (cgeo.R > 8) {  // above the portable cluster size
+          static bool done = false;
+          if (!done) {
+            EOT_CUDA(cudaFuncSetAttribute(kv, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+            EOT_CUDA(cudaFuncSetAttribute(k1, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+            done = true;
+          }
+        }
+        launch_kc(V == VEC ? kv : k1, grid, dim3(kThreads), (unsigned)cgeo.R, s, a, e);
+        return;
+      }
+    }
+    launch_col_dense<1, false>(s, a, e);
   }
   template <int NR, bool LSE, int SQM, class Epi>
   void row(const SweepArgs<T>& a, const Epi& e) {
@@ -813,7 +847,8 @@ struct Solver {
                    h->M, h->x, h->res, h->z, h->p, h->Yx, xw0(), h->sc, h->dotpart, h->cnt_dot, cond(F_CG));
         else
           launch_k(cg_init_fused_kernel<T>, dim3(vg_n), dim3(kOnThreads), st, n, h->rP, h->rPs, rt, h->diag,
-                   h->rowfac, h->M, h->x, h->res, h->z, h->p, h->Yx, xw0(), h->sc, h->cgpart, cond(F_CG));
+                   h->rowfac, h->M, h->x, h->res, h->z, h->p, h->Yx, xw0(), h->sc, h->cgpart, (int)SC_ACTIVE_COL,
+                   cond(F_CG));
         EOT_LAUNCH_CHECK();
         h->launches++;
         loop_while(F_CG, [&] {
@@ -898,8 +933,9 @@ struct Solver {
   // One CG iteration, each kernel a no-op once the device stop flag SC_ACTIVE
   // is clear. Dense costs: the column half (which also takes beta and the stop
   // test), the row half (which forms p) and the update (CgColFusedEpi,
-  // CgRowFusedEpi, cg_update_fused_kernel). Point costs: column half, row half,
-  // update, p update.
+  // CgRowFusedEpi, cg_update_fused_kernel); the column half's stop goes to
+  // SC_ACTIVE_COL, which the row half reads and the update commits to
+  // SC_ACTIVE. Point costs: column half, row half, update, p update.
   void cg_iteration() {
     if (!points) {
       {
@@ -907,19 +943,20 @@ struct Solver {
         a.wr[0] = xw0();
         a.active = h->sc + SC_ACTIVE;
         CgColFusedEpi<T> e{h->colfac, h->cP, zf(), h->wprev, h->cgpart, vg_n, h->sc, h->status, cond(F_CG), 0.0,
-                           false, 0};
-        launch_col_dense<1, false>(st, a, e);
+                           false, 0, (int)SC_ACTIVE_COL};
+        launch_cg_col(st, a, e);
       }
       {
         SweepArgs<T> a = args();
         a.wc[0] = zf();
-        a.active = h->sc + SC_ACTIVE;
+        a.active = h->sc + SC_ACTIVE_COL;
         CgRowFusedEpi e{h->rowfac, h->rPs, h->z, h->p, h->y, h->q, h->sc};
         launch_row_dense<1, false, 0>(st, a, e);
       }
       launch_k(cg_update_fused_kernel<T>, dim3(vg_n), dim3(kOnThreads), st, n, (const double*)h->p,
                (const double*)h->q, (const double*)h->y, (const double*)h->M, (const double*)h->rowfac, h->x, h->res,
-               h->Yx, h->z, xw0(), h->sc, (const double*)h->dotpart, rg, h->cgpart, h->status, cond(F_CG));
+               h->Yx, h->z, xw0(), h->sc, (const double*)h->dotpart, rg, h->cgpart, h->status, (int)SC_ACTIVE_COL,
+               cond(F_CG));
       EOT_LAUNCH_CHECK();
       h->launches += 3;
       return;

@@ -355,7 +355,8 @@ double run_sweep_bench(eot_handle h, const eot_problem* P, const double* u, cons
     // the dense CG kernels read the update kernel's partials: start them as cg_init does
     launch_k(cg_init_fused_kernel<T>, dim3(S.vg_n), dim3(kOnThreads), st, P->n, (const double*)h->rP,
              (const double*)h->rPs, (const double*)h->rt, (const double*)h->diag, (const double*)h->rowfac, h->M,
-             h->x, h->res, h->z, h->p, h->Yx, S.xw0(), h->sc, h->cgpart, (cudaGraphConditionalHandle)0);
+             h->x, h->res, h->z, h->p, h->Yx, S.xw0(), h->sc, h->cgpart, (int)SC_ACTIVE_COL,
+             (cudaGraphConditionalHandle)0);
     EOT_LAUNCH_CHECK();
   }
   EOT_LAUNCH_CHECK();
@@ -383,9 +384,9 @@ double run_sweep_bench(eot_handle h, const eot_problem* P, const double* u, cons
       if (S.points)
         S.template col<1, false, 0>(a, CgColEpi<T>{h->colfac, h->cP, S.zf()});
       else
-        S.template launch_col_dense<1, false>(st, a, CgColFusedEpi<T>{h->colfac, h->cP, S.zf(), h->wprev, h->cgpart,
-                                                                       S.vg_n, h->sc, h->status,
-                                                                       (cudaGraphConditionalHandle)0, 0.0, false, 0});
+        S.launch_cg_col(st, a, CgColFusedEpi<T>{h->colfac, h->cP, S.zf(), h->wprev, h->cgpart, S.vg_n, h->sc,
+                                                h->status, (cudaGraphConditionalHandle)0, 0.0, false, 0,
+                                                (int)SC_ACTIVE_COL});
     } else if (kind == 1) {
       a.wc[0] = S.zf();
       if (S.points)

@@ -421,9 +421,18 @@ __global__ void __launch_bounds__(kThreads, 4) row_sweep_kernel(SweepArgs<T> a, 
 // of (t_ij + log wr_0[i]). Optional NR row reductions (with column weights wc_k)
 // give the fused two-sided sweep of the Hessian-vector product.
 // grid = (S strips of 32*V columns, R row blocks of BR rows).
+// CL (FP32, NC = 1, no LSE, no row reductions): launched as clusters of the R
+// CTAs of a strip (R <= 8). Instead of global partials and a ticket, the CTAs
+// of a strip combine their column sums through distributed shared memory and
+// each finishes a share of the strip's columns: no CTA waits for the last one
+// of its strip, which was this sweep's tail. Every CTA of a cluster must take
+// the same path through both cluster barriers, so *a.active must not change
+// while the kernel runs (its epilogue publishes stops elsewhere).
 // ----------------------------------------------------------------------------
-template <class T, int V, int NC, bool LSE, int NR, class Epi>
+template <class T, int V, int NC, bool LSE, int NR, class Epi, bool CL = false>
 __global__ void __launch_bounds__(kThreads, kColCtasPerSm) col_sweep_kernel(SweepArgs<T> a, Epi epi) {
+  static_assert(!CL || (sizeof(T) == 4 && NC == 1 && !LSE && NR == 0 && Epi::kDot == 0),
+                "cluster finish: FP32 column sums without dots or row reductions");
   constexpr int U = 4;  // rows per batch (two batches in flight)
   constexpr int SW = 32 * V;
   constexpr int ND = Epi::kDot;
@@ -589,6 +598,7 @@ __global__ void __launch_bounds__(kThreads, kColCtasPerSm) col_sweep_kernel(Swee
 
   pdl_trigger();
   // ---- combine the 8 warps of this CTA and write the [R][m] partials ----
+  __shared__ float2 ccol[CL ? SW : 1];  // CL: this CTA's column sums, read by its cluster
   // FP32 path: compensated FP32 pairs (the FP64 pipe is narrow), stored as a
   // float2 (sum, compensation) per partial slot; LSE: (max, 0) in slot 0 and the
   // pair in slot 1. FP64 path: FP64 partials.
@@ -611,7 +621,14 @@ __global__ void __launch_bounds__(kThreads, kColCtasPerSm) col_sweep_kernel(Swee
     for (int cc = threadIdx.x; cc < SW; cc += kThreads) {
       const int64_t jj = strip * SW + cc;
       if (jj >= a.m) continue;
-      if constexpr (!LSE) {
+      if constexpr (CL) {
+        float s0 = 0.f, c0 = 0.f;
+        for (int w = 0; w < kWarps; ++w) {
+          kadd(s0, c0, fsum[0][w][cc]);
+          c0 += fcmp[0][w][cc];
+        }
+        ccol[cc] = make_float2(s0, c0);
+      } else if constexpr (!LSE) {
 #pragma unroll
         for (int k = 0; k < NP; ++k) {
           float s0 = 0.f, c0 = 0.f;
@@ -667,6 +684,32 @@ __global__ void __launch_bounds__(kThreads, kColCtasPerSm) col_sweep_kernel(Swee
     }
   }
 
+  if constexpr (CL) {
+    // ---- the strip's CTAs combine through distributed shared memory ----
+    const uint32_t rank = cluster_rank();
+    if constexpr (HasPrefetch<Epi>::value) {  // (before the barrier: it needs no column sums)
+      epi.drain();
+      epi.prepare(strip == 0 && rank == 0);
+    }
+    cluster_sync();  // every CTA's column sums are visible to the cluster
+    const int per = (SW + R - 1) / R;  // columns this CTA finishes
+    const int lo = (int)rank * per, hi = min(SW, lo + per);
+    for (int cc = lo + threadIdx.x; cc < hi; cc += kThreads) {
+      const int64_t jj = strip * SW + cc;
+      if (jj >= a.m) continue;
+      float s0 = 0.f, c0 = 0.f;
+      for (int r = 0; r < R; ++r) {  // in rank order, as the ticketed combine adds row blocks
+        const float2 q = ld_cluster_f2(&ccol[cc], (uint32_t)r);
+        kadd(s0, c0, q.x);
+        c0 += q.y;
+      }
+      double s[1] = {(double)s0 + (double)c0};
+      double d[1];
+      epi.col(jj, s, d);
+    }
+    cluster_sync();  // no CTA leaves while another reads its shared memory
+    return;
+  }
   // ---- tickets: the last CTA of the strip combines the R partials ----
   __shared__ int last_strip, last_rows;
   if constexpr (HasPrefetch<Epi>::value) epi.drain();
