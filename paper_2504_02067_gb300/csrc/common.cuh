@@ -90,6 +90,22 @@ __device__ __forceinline__ void ld_stream(const double* p, double (&c)[1], uint6
   asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(c[0]) : "l"(p), "l"(pol));
 }
 
+// Asynchronous global -> shared copies (cg: L2 only; ca: through L1), completed
+// by cp.async.wait_all of the issuing thread.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16_ca(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Thread-block clusters: a barrier over the cluster's CTAs (every thread of
 // every CTA arrives; writes before it are visible to reads after it), the CTA's
 // rank in its cluster, and a read of another CTA's shared memory.

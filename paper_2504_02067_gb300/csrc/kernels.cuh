@@ -168,14 +168,6 @@ __device__ __forceinline__ CgStage& cg_stage_smem() {
   __shared__ __align__(16) CgStage st;
   return st;
 }
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
-}
 
 // Column half: w_j = (P^T (rowfac z))_j + beta w_prev_j; zf_j = colfac_j^2 w_j / c(P)_j,
 // with beta = <res, z> / <res, z>_prev (0 on the first iteration). begin(): warp 0

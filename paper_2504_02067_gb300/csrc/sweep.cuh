@@ -322,11 +322,23 @@ __global__ void __launch_bounds__(kThreads, 4) row_sweep_kernel(SweepArgs<T> a, 
   if (rv && lane * V < tw0) row_load<T, V, U>(crow, lane * V, tw0, cA, pol);
   pdl_wait();
   if (a.active && *a.active == 0.0) return;
+  const T g = a.gamma_dev ? (T)*a.gamma_dev : a.gamma;
+  const T ah = rv ? a.Ah[i] : T(0);
+  // 16-byte rows (V > 1): t0, tw and the workspace vectors are 16-byte aligned;
+  // the tile is staged by asynchronous copies (through L1, which the CTAs of an
+  // SM share), all of a thread's in flight at once
+  auto stage = [&](int64_t t0, int tw) {
+    for (int q = threadIdx.x * V; q < tw; q += kThreads * V) {
+      cp_async16_ca(&sv[0][q], a.Bh + t0 + q);
+#pragma unroll
+      for (int k = 0; k < NV - 1; ++k) cp_async16_ca(&sv[1 + k][q], a.wc[k] + t0 + q);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  if constexpr (V > 1) stage(0, tw0);
   double wd[ND > 0 ? ND : 1];
 #pragma unroll
   for (int k = 0; k < (ND > 0 ? ND : 1); ++k) wd[k] = 0.0;
-  const T g = a.gamma_dev ? (T)*a.gamma_dev : a.gamma;
-  const T ah = rv ? a.Ah[i] : T(0);
   T S[NA], Cc[NA];
 #pragma unroll
   for (int k = 0; k < NA; ++k) { S[k] = T(0); Cc[k] = T(0); }
@@ -335,21 +347,14 @@ __global__ void __launch_bounds__(kThreads, 4) row_sweep_kernel(SweepArgs<T> a, 
 
   for (int64_t t0 = 0; t0 < a.m; t0 += TW) {
     const int tw = (int)min((int64_t)TW, a.m - t0);
-    __syncthreads();
     if constexpr (V > 1) {
-      // 16-byte rows (V > 1): t0, tw and the workspace vectors are 16-byte aligned
-#pragma unroll 1
-      for (int q = threadIdx.x * V; q < tw; q += kThreads * V) {
-        T x[V];
-        ld_vec<V>(a.Bh + t0 + q, x);
-        *reinterpret_cast<typename VecOf<T>::type*>(&sv[0][q]) = pack<T>(x);
-#pragma unroll
-        for (int k = 0; k < NV - 1; ++k) {
-          ld_vec<V>(a.wc[k] + t0 + q, x);
-          *reinterpret_cast<typename VecOf<T>::type*>(&sv[1 + k][q]) = pack<T>(x);
-        }
+      if (t0 > 0) {
+        __syncthreads();  // every warp is done with the previous tile
+        stage(t0, tw);
       }
+      cp_async_wait_all();
     } else {
+      __syncthreads();
       for (int q = threadIdx.x; q < tw; q += kThreads) {
         sv[0][q] = a.Bh[t0 + q];
 #pragma unroll
