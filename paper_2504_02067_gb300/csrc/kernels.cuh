@@ -268,16 +268,40 @@ struct CgColFusedEpi {
 
 // Row half: p = z + beta p_prev (in place), y = P (w / c(P)), q = r(P) p - rho y;
 // one partial of <p, q> per CTA.
+// The row's operands (z, p, rowfac, r(P)) and beta, rho are copied into the
+// warp's shared-memory slot by cp.async when the sweep starts (prefetch, lane 0),
+// so the epilogue does not wait for a memory round trip at the end of the row.
+struct CgRowStage {
+  double z, p, rowfac, rP, beta, rho;
+};
+__device__ __forceinline__ CgRowStage* cg_row_stage() {
+  __shared__ __align__(16) CgRowStage st[kWarps];
+  return st;
+}
 struct CgRowFusedEpi {
   static constexpr int kDot = 1;
   static constexpr bool kNoTicket = true;
+  static constexpr bool kRowPrefetch = true;
   const double *rowfac, *rP, *z;
   double *p, *y, *q, *sc;
+  __device__ void prefetch(int64_t i) {
+    CgRowStage& s = cg_row_stage()[threadIdx.x >> 5];
+    cp_async8(&s.z, z + i);
+    cp_async8(&s.p, p + i);
+    cp_async8(&s.rowfac, rowfac + i);
+    cp_async8(&s.rP, rP + i);
+    cp_async8(&s.beta, sc + SC_BETA);
+    cp_async8(&s.rho, sc + SC_RHO);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  }
+  // called by the lane that issued prefetch(i)
   __device__ void row(int64_t i, const double* s, double* d) {
-    const double pi = z[i] + sc[SC_BETA] * p[i];
+    cp_async_wait_all();
+    const CgRowStage& st = cg_row_stage()[threadIdx.x >> 5];
+    const double pi = st.z + st.beta * st.p;
     p[i] = pi;
-    const double yi = rowfac[i] * s[0];
-    const double qi = rP[i] * pi - sc[SC_RHO] * yi;
+    const double yi = st.rowfac * s[0];
+    const double qi = st.rP * pi - st.rho * yi;
     y[i] = yi;
     q[i] = qi;
     d[0] = pi * qi;

@@ -67,6 +67,12 @@ template <class E, class = void>
 struct NoTicket : std::false_type {};
 template <class E>
 struct NoTicket<E, std::void_t<decltype(E::kNoTicket)>> : std::bool_constant<E::kNoTicket> {};
+// row sweeps whose epilogue copies a row's operands ahead (Epi::prefetch(i), by
+// the lane that later calls Epi::row(i))
+template <class E, class = void>
+struct HasRowPrefetch : std::false_type {};
+template <class E>
+struct HasRowPrefetch<E, std::void_t<decltype(E::kRowPrefetch)>> : std::bool_constant<E::kRowPrefetch> {};
 template <class E, class = void>
 struct HasPrefetch : std::false_type {};
 template <class E>
@@ -336,6 +342,9 @@ __global__ void __launch_bounds__(kThreads, 4) row_sweep_kernel(SweepArgs<T> a, 
     asm volatile("cp.async.commit_group;" ::: "memory");
   };
   if constexpr (V > 1) stage(0, tw0);
+  if constexpr (HasRowPrefetch<Epi>::value) {
+    if (rv && lane == 0) epi.prefetch(i);
+  }
   double wd[ND > 0 ? ND : 1];
 #pragma unroll
   for (int k = 0; k < (ND > 0 ? ND : 1); ++k) wd[k] = 0.0;
