@@ -21,7 +21,7 @@ enum Flag : int { F_NEWTON = 0, F_SK, F_GO, F_CGOUT, F_CG, F_DEC, F_LS, F_UPD, F
 
 // device scalars of the stage control (continuing the Sc enum of kernels.cuh)
 enum ScCtl : int {
-  SC_EPS = 23,      // tolerance eps of the projection (Alg. 4)
+  SC_EPS = SC_CTL_BEGIN,  // tolerance eps of the projection (Alg. 4)
   SC_EPSCHI,        // eps^(2/5), ChiSinkhorn's tolerance (Alg. 3)
   SC_ETA,           // forcing parameter of the Newton step
   SC_GL1K,          // ||grad g||_1 at the start of the Newton step

@@ -16,6 +16,7 @@ enum Sc : int {
   SC_CHECK, SC_GL1, SC_CHI2, SC_LHS, SC_SLOPE, SC_MASS, SC_CHK, SC_GAMMA, SC_AUX0, SC_AUX1,
   SC_GRD, SC_GMASS,  // <r(P), d_u> and sum r(P): the gauge component of d_u
   SC_RZPREV,         // <res, z> of the previous CG iteration (dense CG: beta's denominator)
+  SC_CTL_BEGIN,      // the stage control's slots follow (control.cuh)
   SC_COUNT = 32,     // the slots the sweeps and O(n) kernels use (eot_marginals_noalloc keeps these)
   SC_TOTAL = 64      // with the stage control's slots (control.cuh): the handle's array
 };
