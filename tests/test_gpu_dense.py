@@ -397,3 +397,53 @@ def test_plain_fp32_solve_floor_on_the_grid_workload(H):
     st = H.eot_solve(prob, default_params(gamma_i=16.0, gamma_f=256.0, tol_final=1e-4), u, v).as_dict()
     err = O.marginal_l1_error(u.cpu().numpy(), v.cpu().numpy(), 256.0, C64, p["r"], p["c"])
     assert err <= 2e-4, (err, st["marg_err_l1"])
+
+
+def test_cluster_and_ticketed_column_half_agree(monkeypatch):
+    """The CG column half of FP32 dense costs runs as thread-block clusters whose
+    CTAs combine their column sums in distributed shared memory; EOT_CG_CLUSTER=0
+    selects the ticketed combine through global partials. Both take the same
+    Alg. 2 / Alg. 1 path: the same rho and CG count (within one) for a Newton
+    step whose row-block counts differ (600 x 512: R = 8 clustered, more
+    ticketed), and on the 64 x 64 grid workload the same stages and potentials
+    to rounding, both at marginal L1 <= 1e-6 as the oracle measures it."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2504_02067_gb300 import Handle, Problem, default_params
+    n, m = 600, 512
+    rng = np.random.default_rng(43)
+    C = rng.uniform(0, 1, size=(n, m)).astype(np.float32)
+    C64 = C.astype(np.float64)
+    gamma = 64.0
+    u, v, r, c = near_feasible(44, n, m, gamma, C64)
+    rP = O.row_sum(O.plan(u, v, gamma, C64))
+    rt = rP * (1 + 0.02 * rng.normal(size=n))
+    rt /= rt.sum()
+    gl1 = np.abs(rP - rt).sum()
+    eta = max(gl1, 0.8 * 1e-4 / gl1)
+    p = W.grid_problem_4096(0, "sqeuclid")
+    g = float(np.float32(16384.0))
+    out = {}
+    for mode in ("8", "0"):
+        monkeypatch.setenv("EOT_CG_CLUSTER", mode)
+        h = Handle(0, 64, 64)
+        try:
+            prob = Problem(t(C, torch.float32), r=t(r), c=t(c), precision="mixed")
+            du, dv, rho, it = h.newton_solve(prob, t(u), t(v), gamma, t(rt), eta, 0.0)
+            gp = Problem(t(p["C"], torch.float32), t(p["r"]), t(p["c"]))
+            uu, vv, st = h.solve(gp, default_params(gamma_i=16.0, gamma_f=16384.0))
+            out[mode] = (du.cpu().numpy(), rho, it, uu.cpu().numpy(), vv.cpu().numpy(), st)
+        finally:
+            h.close()
+    a, b = out["8"], out["0"]
+    assert a[1] == b[1] and abs(a[2] - b[2]) <= 1
+    d = a[0] - b[0]
+    assert np.abs(d - d.mean()).sum() <= 1e-5 * np.abs(b[0]).sum()
+    for k in (3, 4):
+        e = a[k] - b[k]
+        assert np.abs(e - e.mean()).max() <= 1e-9 * (1.0 + np.abs(b[k]).max()), k
+    assert a[5]["stages"] == b[5]["stages"]
+    assert abs(a[5]["cg_iters"] - b[5]["cg_iters"]) <= 0.01 * b[5]["cg_iters"]
+    for x in (a, b):
+        err = O.marginal_l1_error(x[3], x[4], g, p["C"].astype(np.float64), p["r"], p["c"])
+        assert err <= 1e-6, err
